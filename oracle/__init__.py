@@ -1,0 +1,239 @@
+"""CPU oracle of the FFA periodogram (Morello et al. 2020) -- TEST INFRASTRUCTURE.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never imports, links or
+calls it, and it shares no code with the CUDA library.
+
+The arithmetic lives in ``ffa_oracle.c`` (plain C, FP64 except for the FP32
+instantiation of the FFA, which fixes the exact sequence of float additions of the
+paper's recursion).  This module only compiles it with gcc and marshals numpy
+arrays through ctypes.
+
+Paper passages followed (sections and equations of the paper):
+  * plan ............ Sec. 5.3 (pseudo-octaves), Sec. 5.6 (initial tau = Pmin/bmin)
+  * downsample ...... Sec. 5.3, App. A.4 (overlap-weighted real-factor windows)
+  * ffa ............. Sec. 2.2, Eq. ffa_merge_rule (depth-first, m_h = floor(m/2))
+  * trial periods ... Sec. 2.3 (P_s = p^2 tau / (p - s/(m-1)); redundant rows)
+  * boxcar S/N ...... Sec. 5.4, Sec. 3.3 (Z = x.s, unit square sum), App. A.3
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ffa_oracle.c")
+_LIB = os.path.join(_HERE, "libffa_oracle.so")
+_lib = None
+
+_i64 = ctypes.c_int64
+_dbl = ctypes.c_double
+_int = ctypes.c_int
+_p = ctypes.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no contraction into FMA, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "ffa_oracle_api.h"))
+    ):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+             "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"],
+            cwd=_HERE,
+        )
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    lib.oracle_plan.restype = _int
+    lib.oracle_plan.argtypes = [_i64, _dbl, _dbl, _dbl, _int, _int, _int, _p, _p, _int,
+                                _p, _p, _p, _p, _p, _p, _p, _p]
+    lib.oracle_downsampled_length.restype = _i64
+    lib.oracle_downsampled_length.argtypes = [_i64, _dbl]
+    lib.oracle_downsample.restype = _int
+    lib.oracle_downsample.argtypes = [_p, _i64, _dbl, _p, _i64]
+    lib.oracle_downsampled_variance.restype = _dbl
+    lib.oracle_downsampled_variance.argtypes = [_dbl]
+    lib.oracle_ffa_split.restype = None
+    lib.oracle_ffa_split.argtypes = [_i64, _i64, _p, _p, _p]
+    lib.oracle_ffa_f64.restype = _int
+    lib.oracle_ffa_f64.argtypes = [_p, _i64, _i64, _p]
+    lib.oracle_ffa_f32.restype = _int
+    lib.oracle_ffa_f32.argtypes = [_p, _i64, _i64, _p]
+    lib.oracle_trial_period.restype = _dbl
+    lib.oracle_trial_period.argtypes = [_dbl, _i64, _i64, _i64]
+    lib.oracle_boxcar_snr.restype = _int
+    lib.oracle_boxcar_snr.argtypes = [_p, _i64, _i64, _p, _int, _dbl, _p]
+    lib.oracle_periodogram.restype = _i64
+    lib.oracle_periodogram.argtypes = [_p, _i64, _dbl, _dbl, _dbl, _int, _int, _p, _int,
+                                       _p, _p, _p, _p, _i64]
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Plan:
+    """Search plan: octaves (factor, length) and transforms in (octave, p) order."""
+    oct_factor: np.ndarray     # float64 [n_octaves]
+    oct_len: np.ndarray        # int64   [n_octaves]
+    tr_octave: np.ndarray      # int32   [n_transforms]
+    tr_p: np.ndarray           # int32
+    tr_m: np.ndarray           # int64
+    tr_kept: np.ndarray        # int64
+    tr_first_trial: np.ndarray # int64
+    n_trials: int
+
+    @property
+    def n_octaves(self) -> int:
+        return len(self.oct_factor)
+
+    @property
+    def n_transforms(self) -> int:
+        return len(self.tr_p)
+
+
+def plan(n, tsamp, pmin, pmax, bmin, bmax) -> Plan:
+    """Sec. 5.3 search plan.  Raises ValueError on invalid parameters."""
+    lib = _load()
+    no = ctypes.c_int(0)
+    nt = ctypes.c_int(0)
+    ntr = ctypes.c_int64(0)
+    z = np.zeros(1)
+    rc = lib.oracle_plan(n, tsamp, pmin, pmax, bmin, bmax, 0, _ptr(z), _ptr(z), 0,
+                         _ptr(z), _ptr(z), _ptr(z), _ptr(z), _ptr(z),
+                         ctypes.byref(no), ctypes.byref(nt), ctypes.byref(ntr))
+    if rc != 0:
+        raise ValueError("invalid search parameters")
+    O, T = no.value, nt.value
+    of = np.zeros(O, np.float64)
+    ol = np.zeros(O, np.int64)
+    to = np.zeros(T, np.int32)
+    tp = np.zeros(T, np.int32)
+    tm = np.zeros(T, np.int64)
+    tk = np.zeros(T, np.int64)
+    tf = np.zeros(T, np.int64)
+    lib.oracle_plan(n, tsamp, pmin, pmax, bmin, bmax, O, _ptr(of), _ptr(ol), T,
+                    _ptr(to), _ptr(tp), _ptr(tm), _ptr(tk), _ptr(tf),
+                    ctypes.byref(no), ctypes.byref(nt), ctypes.byref(ntr))
+    return Plan(of, ol, to, tp, tm, tk, tf, int(ntr.value))
+
+
+def downsampled_length(n: int, f: float) -> int:
+    return int(_load().oracle_downsampled_length(n, f))
+
+
+def downsample(x: np.ndarray, f: float) -> np.ndarray:
+    """App. A.4 downsampling of a float32 series by real factor f >= 1 (FP64 out)."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    nout = lib.oracle_downsampled_length(len(x), f)
+    if nout < 0:
+        raise ValueError("invalid downsampling factor")
+    out = np.zeros(nout, np.float64)
+    if lib.oracle_downsample(_ptr(x), len(x), f, _ptr(out), nout) != 0:
+        raise ValueError("downsample failed")
+    return out
+
+
+def downsampled_variance(f: float) -> float:
+    return float(_load().oracle_downsampled_variance(f))
+
+
+def ffa_split(m: int, s: int):
+    """(i, j, b) of the merge rule for output row s of an m-row transform."""
+    i, j, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _load().oracle_ffa_split(m, s, ctypes.byref(i), ctypes.byref(j), ctypes.byref(b))
+    return i.value, j.value, b.value
+
+
+def ffa(block: np.ndarray) -> np.ndarray:
+    """Folding transform of an m x p block by the depth-first FFA (Sec. 2.2).
+
+    float32 input -> float32 output with the paper's exact sequence of float adds;
+    float64 input -> float64 output.
+    """
+    lib = _load()
+    if block.ndim != 2:
+        raise ValueError("block must be 2-D")
+    m, p = block.shape
+    if block.dtype == np.float32:
+        a = np.ascontiguousarray(block)
+        out = np.empty_like(a)
+        rc = lib.oracle_ffa_f32(_ptr(a), m, p, _ptr(out))
+    else:
+        a = np.ascontiguousarray(block, dtype=np.float64)
+        out = np.empty_like(a)
+        rc = lib.oracle_ffa_f64(_ptr(a), m, p, _ptr(out))
+    if rc != 0:
+        raise ValueError("invalid FFA shape")
+    return out
+
+
+def trial_period(tau: float, p: int, m: int, s: int) -> float:
+    return float(_load().oracle_trial_period(tau, p, m, s))
+
+
+def boxcar_snr(prof: np.ndarray, widths, stdnoise: float) -> np.ndarray:
+    """Boxcar S/N of every row of a profile array (Sec. 5.4), FP64, direct sums."""
+    lib = _load()
+    P = np.ascontiguousarray(prof, dtype=np.float64)
+    if P.ndim == 1:
+        P = P[None, :]
+    rows, p = P.shape
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    out = np.zeros((rows, len(w)), np.float64)
+    if lib.oracle_boxcar_snr(_ptr(P), rows, p, _ptr(w), len(w), stdnoise, _ptr(out)) != 0:
+        raise ValueError("invalid boxcar arguments")
+    return out
+
+
+@dataclass
+class Periodogram:
+    periods: np.ndarray   # float64 [ntrials]
+    foldbins: np.ndarray  # int32   [ntrials]
+    snr: np.ndarray       # float64 [ntrials, nw]
+
+
+def periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths, select=None) -> Periodogram:
+    """Sec. 5.3 periodogram of a float32 series, FP64 throughout.
+
+    ``select``: optional boolean mask over the plan's transforms; only those are
+    computed and their trials are returned compactly in plan order.
+    """
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    pl = plan(len(x), tsamp, pmin, pmax, bmin, bmax)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    if select is None:
+        cap = pl.n_trials
+        sel_ptr = None
+    else:
+        sel = np.ascontiguousarray(select, dtype=np.uint8)
+        if len(sel) != pl.n_transforms:
+            raise ValueError("select mask has the wrong length")
+        cap = int(pl.tr_kept[sel.astype(bool)].sum())
+        sel_ptr = _ptr(sel)
+    periods = np.zeros(cap, np.float64)
+    fb = np.zeros(cap, np.int32)
+    snr = np.zeros((cap, len(w)), np.float64)
+    got = lib.oracle_periodogram(_ptr(x), len(x), tsamp, pmin, pmax, bmin, bmax, _ptr(w),
+                                 len(w), sel_ptr, _ptr(periods), _ptr(fb), _ptr(snr), cap)
+    if got != cap:
+        raise ValueError("oracle periodogram failed (%d)" % got)
+    return Periodogram(periods, fb, snr)
