@@ -1,0 +1,181 @@
+/*
+ * ffa.h -- C ABI of libffa, a GB300 (sm_103a) implementation of the FFA periodogram
+ * of Morello et al. 2020 ("Optimal periodicity searching: revisiting the Fast Folding
+ * Algorithm for large scale pulsar surveys", arXiv:2004.03701).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers named d_* are DEVICE pointers, h_* are HOST pointers.  All memory is
+ *    owned by the caller; libffa never allocates or frees device memory.  Scratch
+ *    memory comes from a caller-provided workspace (d_ws, ws_bytes) whose size is
+ *    queried first.  The workspace must be 256-byte aligned.
+ *  - `stream` is a cudaStream_t passed as an opaque pointer (NULL = legacy default
+ *    stream).  Calls that take a stream are asynchronous on it unless stated.
+ *  - Every call returns an ffa_status.  Argument errors are detected on the host
+ *    before anything is launched.  ffa_last_error() returns a thread-local message
+ *    for the last failing call of the calling thread.  No exception and no process
+ *    exit crosses this ABI.
+ *  - Device-side failures (a bounded wait that ran out) set a status word inside
+ *    the workspace; ffa_check() reads it.
+ *  - All arrays are dense and row-major.  float is IEEE binary32, double binary64.
+ */
+#ifndef FFA_H
+#define FFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ffa_status;
+#define FFA_OK 0
+#define FFA_ERR_ARG 1         /* invalid argument (null pointer, bad size, bad range) */
+#define FFA_ERR_CAPACITY 2    /* output or workspace too small                        */
+#define FFA_ERR_CUDA 3        /* a CUDA runtime call failed                           */
+#define FFA_ERR_TIMEOUT 4     /* a bounded device-side wait ran out                   */
+#define FFA_ERR_UNSUPPORTED 5 /* size outside what this build supports                */
+#define FFA_ERR_DEVICE 6      /* another device-side check failed                     */
+
+typedef int32_t ffa_dtype;
+#define FFA_F32 0 /* float                                                   */
+#define FFA_F16 1 /* IEEE binary16                                           */
+#define FFA_I8 2  /* int8 q, value q / 16 (normalised data clipped to +-8 sigma) */
+
+/* Thread-local text of the last error of this thread ("" if none). */
+const char* ffa_last_error(void);
+/* Library version string. */
+const char* ffa_version(void);
+
+/* ------------------------------------------------------------------------------
+ * Real-factor downsampling (paper Sec. 5.3 and App. A.4).
+ *   out[i] = sum_j x[j] * |[j, j+1) intersect [i f, (i+1) f)|,   0 <= i < n_out,
+ *   n_out = floor(n / f).  Input samples that overlap the window partially are
+ *   weighted by their overlap fraction.  factor >= 1.
+ * d_x:     n floats (device).   d_out: out_cap floats (device).
+ * n_out:   host pointer, receives floor(n / factor) (set even on FFA_ERR_CAPACITY).
+ * Workspace: ffa_downsample_workspace(n) bytes (a prefix-sum of the input).
+ * Accuracy: within 1e-6 of sum_j |w_j x_j| per output sample.
+ * Errors: FFA_ERR_ARG (null pointers, n <= 0, factor < 1 or not finite),
+ *         FFA_ERR_CAPACITY (out_cap < n_out or workspace too small).
+ * ---------------------------------------------------------------------------- */
+ffa_status ffa_downsample_workspace(int64_t n, size_t* bytes);
+ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_out,
+                          int64_t out_cap, int64_t* n_out, void* d_ws, size_t ws_bytes,
+                          void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Folding transform of an m x p block by the depth-first FFA (paper Sec. 2.1-2.2,
+ * Eq. ffa_merge_rule).  d_in and d_out are rows x cols floats (device, row-major,
+ * row r = samples [r*cols, (r+1)*cols)); out row s is the profile folded along the
+ * integration path drifting s bins over the block, 0 <= s < rows.  The head of an
+ * n-row block is its first floor(n/2) rows; nearest-integer rounding of the split
+ * is half-up; (T << k)[x] = T[(x + k) mod cols].  The result is bit-identical to
+ * the recursion evaluated with one float add per element.
+ * rows >= 1, cols >= 1, rows * cols < 2^31.  d_in and d_out must not overlap.
+ * Workspace: ffa_transform_workspace(rows, cols) bytes.
+ * Errors: FFA_ERR_ARG, FFA_ERR_CAPACITY, FFA_ERR_UNSUPPORTED (cols > 4096).
+ * ---------------------------------------------------------------------------- */
+ffa_status ffa_transform_workspace(int32_t rows, int32_t cols, size_t* bytes);
+ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d_out,
+                         void* d_ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Boxcar matched filter S/N (paper Sec. 5.4, with the Z-statistic normalisation of
+ * Sec. 3.3 and App. A.3).  For each profile row r and width w = h_widths[iw]:
+ *   d_snr[r * nw + iw] = max_{0<=k<cols} C_k(w) / (stdnoise * sqrt(w)),
+ *   C_k(w) = sum_{q<w} prof[r][(k + q) mod cols],
+ * where stdnoise is the noise standard deviation of one profile bin (for an
+ * m-row transform of a series downsampled by f: sqrt(m * V_f)).
+ * d_prof: rows x cols floats (device).  h_widths: nw ints (host), 1 <= w <= cols.
+ * d_snr: rows x nw floats (device).  Sums are accumulated in float.
+ * Errors: FFA_ERR_ARG (null pointers, rows < 0, cols < 1, nw < 1 or > 64,
+ *         bad width, stdnoise <= 0), FFA_ERR_UNSUPPORTED (cols > 4096).
+ * ---------------------------------------------------------------------------- */
+ffa_status ffa_boxcar_snr(const float* d_prof, int32_t rows, int32_t cols,
+                          const int32_t* h_widths, int32_t nw, double stdnoise,
+                          float* d_snr, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Periodogram search plan (paper Sec. 5.3, Fig. 4; Sec. 5.6 for the first factor).
+ *   f0 = pmin / (bmin * tsamp) (must be >= 1), fg = (bmax + 1) / bmin,
+ *   octave k: factor F_k = f0 * fg^k while bmin * tsamp * F_k <= pmax,
+ *             N_k = floor(n / F_k) samples of length tau_k = tsamp * F_k;
+ *   base periods p = bmin..bmax, m = floor(N_k / p) rows (transforms with m < 2
+ *   skipped); row s is kept iff P_s < (p + 1) tau_k, i.e. s (p + 1) < p (m - 1)
+ *   (Sec. 2.3); P_s = tau_k p^2 / (p - s / (m - 1)).
+ * Host only.  Widths: 1 <= w < bmin, strictly increasing, at most 64.
+ * ---------------------------------------------------------------------------- */
+typedef struct ffa_plan_info {
+    int64_t ntrials;                  /* rows of the periodogram                     */
+    int32_t noctaves;                 /* pseudo-octaves                              */
+    int32_t ntransforms;              /* FFA transforms (octave, p)                  */
+    int32_t nwidths;                  /* boxcar widths                               */
+    int32_t max_rows;                 /* largest m                                   */
+    int64_t downsampled_samples;      /* sum over octaves of N_k                     */
+    int64_t folded_samples;           /* sum over transforms of m * p                */
+    size_t workspace_bytes;           /* for ffa_periodogram                         */
+    size_t host_workspace_bytes;      /* for ffa_periodogram_host (includes I/O)     */
+} ffa_plan_info;
+
+ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pmax,
+                                int32_t bmin, int32_t bmax, const int32_t* h_widths,
+                                int32_t nw, ffa_plan_info* out);
+
+/* ------------------------------------------------------------------------------
+ * FFA periodogram (paper Sec. 5.3, Fig. 4; Sec. 5.5 for the two-dimensional output).
+ * d_x: n samples (device) of a normalised series (zero mean, unit variance, Sec. 3.1
+ *      and Sec. 5.2), stored as `dtype`.
+ * Outputs (device), trials in (octave, p, s) order, periods strictly increasing:
+ *   d_periods[t]            trial period in seconds (double)
+ *   d_foldbins[t]           base period p in samples of its octave (int32)
+ *   d_snr[t * nw + iw]      boxcar S/N of width h_widths[iw] (float), normalised by
+ *                           sqrt(m * w * V_f), V_f = F_k if F_k is an integer else
+ *                           F_k - 1/3 (App. A.4)
+ * ntrials_cap >= ffa_plan_info.ntrials.  Workspace: ffa_plan_info.workspace_bytes.
+ * The plan's tables are copied into the workspace on every call (from page-locked
+ * host memory owned by libffa).
+ * Errors: FFA_ERR_ARG, FFA_ERR_CAPACITY, FFA_ERR_UNSUPPORTED, FFA_ERR_CUDA.
+ * ---------------------------------------------------------------------------- */
+ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp,
+                           double pmin, double pmax, int32_t bmin, int32_t bmax,
+                           const int32_t* h_widths, int32_t nw, double* d_periods,
+                           int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
+                           void* d_ws, size_t ws_bytes, void* stream);
+
+/* Same search, end to end from and to HOST buffers: copies h_x (n floats) to the
+ * device, runs the periodogram, copies the three outputs back, and synchronises
+ * `stream` before returning.  Host buffers should be page-locked for speed.
+ * Workspace: ffa_plan_info.host_workspace_bytes. */
+ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, double pmin,
+                                double pmax, int32_t bmin, int32_t bmax,
+                                const int32_t* h_widths, int32_t nw, double* h_periods,
+                                int32_t* h_foldbins, float* h_snr, int64_t ntrials_cap,
+                                void* d_ws, size_t ws_bytes, void* stream);
+
+/* Synchronises `stream`, reads and clears the device status word of a workspace used
+ * by ffa_periodogram / ffa_transform / ffa_downsample.  FFA_OK if no device-side
+ * check failed, else FFA_ERR_TIMEOUT or FFA_ERR_DEVICE. */
+ffa_status ffa_check(void* d_ws, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Launch accounting and per-kernel timing (for benchmarks).  When enabled, every
+ * kernel launch of this library is bracketed by CUDA events on its stream.
+ * Not to be enabled while a stream is being captured into a graph.
+ * ---------------------------------------------------------------------------- */
+int64_t ffa_launch_count(void);          /* kernels launched by this process so far */
+int32_t ffa_kernel_kinds(void);          /* number of kernel kinds                  */
+const char* ffa_kernel_name(int32_t kind);
+ffa_status ffa_profile_enable(int32_t on);
+ffa_status ffa_profile_reset(void);
+/* Synchronises the recorded events; returns launches, summed device time (ms) and
+ * summed algorithmic bytes (reads + writes of the data the method must touch) of
+ * one kernel kind since the last reset. */
+ffa_status ffa_profile_query(int32_t kind, int64_t* launches, double* total_ms,
+                             double* alg_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFA_H */

@@ -1,0 +1,320 @@
+"""GB300 (sm_103a) FFA periodogram -- thin Python binding of libffa's C ABI.
+
+Every step of the search (prefix sums, real-factor downsampling, FFA merges, boxcar
+S/N) runs in the CUDA kernels of ``libffa.so``; this module only marshals arguments:
+torch tensors supply device memory and the current CUDA stream.  There is no CPU
+fallback: if the library is missing, every call raises.
+
+Calls (names follow include/ffa.h and the paper, Morello et al. 2020):
+  downsample(x, factor)                         Sec. 5.3, App. A.4
+  ffa_transform(block)                          Sec. 2.2, Eq. ffa_merge_rule
+  boxcar_snr(prof, widths, stdnoise)            Sec. 5.4
+  periodogram_plan(n, tsamp, pmin, pmax, bmin, bmax, widths)
+  periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths)        Sec. 5.3, Fig. 4
+  periodogram_host(x_host, ...)                 same, host buffers in and out
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+__all__ = [
+    "FFAError", "library", "build", "downsample", "ffa_transform", "boxcar_snr",
+    "PlanInfo", "periodogram_plan", "periodogram", "periodogram_host", "Searcher",
+    "check", "launch_count", "kernel_names", "profile_enable", "profile_reset",
+    "profile_query",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libffa.so")
+
+FFA_F32, FFA_F16, FFA_I8 = 0, 1, 2
+_STATUS = {0: "FFA_OK", 1: "FFA_ERR_ARG", 2: "FFA_ERR_CAPACITY", 3: "FFA_ERR_CUDA",
+           4: "FFA_ERR_TIMEOUT", 5: "FFA_ERR_UNSUPPORTED", 6: "FFA_ERR_DEVICE"}
+
+
+class FFAError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), message))
+        self.status = status
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("ntrials", ctypes.c_int64), ("noctaves", ctypes.c_int32),
+                ("ntransforms", ctypes.c_int32), ("nwidths", ctypes.c_int32),
+                ("max_rows", ctypes.c_int32), ("downsampled_samples", ctypes.c_int64),
+                ("folded_samples", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
+                ("host_workspace_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+    return _build.build(force=force)
+
+
+def library() -> ctypes.CDLL:
+    """The loaded libffa.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libffa.so is not built (run __graft_entry__.build()); "
+                           "there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, dbl, vp, sz = (ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
+                             ctypes.c_size_t)
+    L.ffa_last_error.restype = ctypes.c_char_p
+    L.ffa_version.restype = ctypes.c_char_p
+    L.ffa_downsample_workspace.argtypes = [i64, ctypes.POINTER(sz)]
+    L.ffa_downsample.argtypes = [vp, i64, dbl, vp, i64, ctypes.POINTER(i64), vp, sz, vp]
+    L.ffa_transform_workspace.argtypes = [i32, i32, ctypes.POINTER(sz)]
+    L.ffa_transform.argtypes = [vp, i32, i32, vp, vp, sz, vp]
+    L.ffa_boxcar_snr.argtypes = [vp, i32, i32, vp, i32, dbl, vp, vp]
+    L.ffa_periodogram_plan.argtypes = [i64, dbl, dbl, dbl, i32, i32, vp, i32,
+                                       ctypes.POINTER(_PlanInfo)]
+    L.ffa_periodogram.argtypes = [vp, i32, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
+                                  i64, vp, sz, vp]
+    L.ffa_periodogram_host.argtypes = [vp, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
+                                       i64, vp, sz, vp]
+    L.ffa_check.argtypes = [vp, vp]
+    L.ffa_launch_count.restype = i64
+    L.ffa_kernel_kinds.restype = i32
+    L.ffa_kernel_name.restype = ctypes.c_char_p
+    L.ffa_kernel_name.argtypes = [i32]
+    L.ffa_profile_enable.argtypes = [i32]
+    L.ffa_profile_query.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
+                                    ctypes.POINTER(dbl)]
+    for f in ("ffa_downsample_workspace", "ffa_downsample", "ffa_transform_workspace",
+              "ffa_transform", "ffa_boxcar_snr", "ffa_periodogram_plan", "ffa_periodogram",
+              "ffa_periodogram_host", "ffa_check", "ffa_profile_enable", "ffa_profile_reset",
+              "ffa_profile_query"):
+        getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise FFAError(status, library().ffa_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> ctypes.c_void_p:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_tensor(t, name: str):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+def _workspace(nbytes: int, device):
+    torch = _torch()
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _widths_array(widths: Sequence[int]) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+
+
+def _vp(a) -> ctypes.c_void_p:
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+# ----------------------------------------------------------------------------------
+def downsample(x, factor: float, stream=None):
+    """Real-factor downsampling of a float32 CUDA series (Sec. 5.3, App. A.4)."""
+    torch = _torch()
+    _dev_tensor(x, "x")
+    if x.dtype != torch.float32 or x.dim() != 1:
+        raise TypeError("x must be a 1-D float32 tensor")
+    L = library()
+    n = x.numel()
+    need = ctypes.c_size_t()
+    _check(L.ffa_downsample_workspace(n, ctypes.byref(need)))
+    ws = _workspace(need.value, x.device)
+    nout = int(np.floor(n / factor)) if factor >= 1 else 0
+    out = torch.empty(max(nout, 1), dtype=torch.float32, device=x.device)
+    got = ctypes.c_int64()
+    _check(L.ffa_downsample(_vp(x), n, float(factor), _vp(out), out.numel(), ctypes.byref(got),
+                            _vp(ws), ws.numel(), _stream_handle(stream)))
+    return out[: got.value]
+
+
+def ffa_transform(block, stream=None):
+    """Folding transform of a (rows, cols) float32 CUDA block (Sec. 2.2)."""
+    torch = _torch()
+    _dev_tensor(block, "block")
+    if block.dtype != torch.float32 or block.dim() != 2:
+        raise TypeError("block must be a 2-D float32 tensor")
+    L = library()
+    m, p = block.shape
+    need = ctypes.c_size_t()
+    _check(L.ffa_transform_workspace(m, p, ctypes.byref(need)))
+    ws = _workspace(need.value, block.device)
+    out = torch.empty_like(block)
+    _check(L.ffa_transform(_vp(block), m, p, _vp(out), _vp(ws), ws.numel(),
+                           _stream_handle(stream)))
+    return out
+
+
+def boxcar_snr(prof, widths: Sequence[int], stdnoise: float, stream=None):
+    """Boxcar S/N (rows, nw) of a (rows, cols) float32 CUDA profile array (Sec. 5.4)."""
+    torch = _torch()
+    _dev_tensor(prof, "prof")
+    if prof.dtype != torch.float32 or prof.dim() != 2:
+        raise TypeError("prof must be a 2-D float32 tensor")
+    w = _widths_array(widths)
+    rows, cols = prof.shape
+    out = torch.empty((rows, len(w)), dtype=torch.float32, device=prof.device)
+    _check(library().ffa_boxcar_snr(_vp(prof), rows, cols, _vp(w), len(w), float(stdnoise),
+                                    _vp(out), _stream_handle(stream)))
+    return out
+
+
+@dataclass
+class PlanInfo:
+    ntrials: int
+    noctaves: int
+    ntransforms: int
+    nwidths: int
+    max_rows: int
+    downsampled_samples: int
+    folded_samples: int
+    workspace_bytes: int
+    host_workspace_bytes: int
+
+
+def periodogram_plan(n: int, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,
+                     widths: Sequence[int]) -> PlanInfo:
+    w = _widths_array(widths)
+    info = _PlanInfo()
+    _check(library().ffa_periodogram_plan(n, tsamp, pmin, pmax, bmin, bmax, _vp(w), len(w),
+                                          ctypes.byref(info)))
+    return PlanInfo(*(getattr(info, f) for f, _ in _PlanInfo._fields_))
+
+
+def _dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return FFA_F32
+    if t.dtype == torch.float16:
+        return FFA_F16
+    if t.dtype == torch.int8:
+        return FFA_I8
+    raise TypeError("series dtype must be float32, float16 or int8 (value q/16)")
+
+
+class Searcher:
+    """Holds the workspace and outputs of one search configuration for repeated calls."""
+
+    def __init__(self, n, tsamp, pmin, pmax, bmin, bmax, widths, device="cuda"):
+        torch = _torch()
+        self.args = (int(n), float(tsamp), float(pmin), float(pmax), int(bmin), int(bmax))
+        self.widths = _widths_array(widths)
+        self.info = periodogram_plan(*self.args, self.widths)
+        T, nw = self.info.ntrials, len(self.widths)
+        self.device = torch.device(device)
+        self.ws = _workspace(self.info.workspace_bytes, self.device)
+        self.periods = torch.empty(T, dtype=torch.float64, device=self.device)
+        self.foldbins = torch.empty(T, dtype=torch.int32, device=self.device)
+        self.snr = torch.empty((T, nw), dtype=torch.float32, device=self.device)
+        self._host_ws = None
+
+    def __call__(self, x, stream=None):
+        _dev_tensor(x, "x")
+        if x.numel() != self.args[0]:
+            raise ValueError("series length differs from the plan")
+        n, tsamp, pmin, pmax, bmin, bmax = self.args
+        _check(library().ffa_periodogram(
+            _vp(x), _dtype_code(x), n, tsamp, pmin, pmax, bmin, bmax, _vp(self.widths),
+            len(self.widths), _vp(self.periods), _vp(self.foldbins), _vp(self.snr),
+            self.periods.numel(), _vp(self.ws), self.ws.numel(), _stream_handle(stream)))
+        return self.periods, self.foldbins, self.snr
+
+    def run_host(self, x_host, periods_h, foldbins_h, snr_h, stream=None):
+        """End to end from host memory: copies in, searches, copies out, synchronises."""
+        if self._host_ws is None:
+            self._host_ws = _workspace(self.info.host_workspace_bytes, self.device)
+        n, tsamp, pmin, pmax, bmin, bmax = self.args
+        _check(library().ffa_periodogram_host(
+            _vp(x_host), n, tsamp, pmin, pmax, bmin, bmax, _vp(self.widths), len(self.widths),
+            _vp(periods_h), _vp(foldbins_h), _vp(snr_h), len(periods_h), _vp(self._host_ws),
+            self._host_ws.numel(), _stream_handle(stream)))
+
+    def check(self, stream=None):
+        check(self.ws, stream)
+
+
+def periodogram(x, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,
+                widths: Sequence[int], stream=None):
+    """FFA periodogram of a normalised CUDA series (float32, float16 or int8 as q/16).
+
+    Returns (periods float64 [T], foldbins int32 [T], snr float32 [T, nw]) on the device.
+    """
+    s = Searcher(x.numel(), tsamp, pmin, pmax, bmin, bmax, widths, device=x.device)
+    return s(x, stream)
+
+
+def periodogram_host(x: np.ndarray, tsamp, pmin, pmax, bmin, bmax, widths, device="cuda"):
+    """Same search from and to host numpy arrays (copies inside the call)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    s = Searcher(len(x), tsamp, pmin, pmax, bmin, bmax, widths, device=device)
+    T, nw = s.info.ntrials, len(s.widths)
+    per = np.empty(T, np.float64)
+    fb = np.empty(T, np.int32)
+    snr = np.empty((T, nw), np.float32)
+    s.run_host(x, per, fb, snr)
+    return per, fb, snr
+
+
+def check(ws, stream=None) -> None:
+    """Raises FFAError if a device-side check of the last calls on `ws` failed."""
+    _check(library().ffa_check(_vp(ws), _stream_handle(stream)))
+
+
+def launch_count() -> int:
+    return int(library().ffa_launch_count())
+
+
+def kernel_names() -> Tuple[str, ...]:
+    L = library()
+    return tuple(L.ffa_kernel_name(k).decode() for k in range(L.ffa_kernel_kinds()))
+
+
+def profile_enable(on: bool = True) -> None:
+    _check(library().ffa_profile_enable(1 if on else 0))
+
+
+def profile_reset() -> None:
+    _check(library().ffa_profile_reset())
+
+
+def profile_query(kind) -> dict:
+    L = library()
+    if isinstance(kind, str):
+        kind = kernel_names().index(kind)
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    b = ctypes.c_double()
+    _check(L.ffa_profile_query(kind, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
+    return {"launches": n.value, "ms": ms.value, "alg_bytes": b.value}

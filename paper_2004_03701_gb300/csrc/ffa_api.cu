@@ -1,0 +1,803 @@
+// ffa_api.cu -- host side of libffa: argument checking, the search plan (Sec. 5.3 of
+// Morello et al. 2020), workspace layout, launch sequencing and launch accounting,
+// behind the C ABI declared in include/ffa.h.
+#include "ffa.h"
+#include "ffa_internal.h"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+namespace ffa {
+namespace {
+
+// ---------------------------------------------------------------------------------
+// Errors.
+// ---------------------------------------------------------------------------------
+thread_local std::string g_err;
+
+ffa_status fail(ffa_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+ffa_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(FFA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FFA_CUDA(call, what)                      \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------------------
+// Launch accounting.
+// ---------------------------------------------------------------------------------
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double bytes;
+};
+struct ProfAcc {
+    int64_t launches = 0;
+    double ms = 0.0;
+    double bytes = 0.0;
+};
+
+std::atomic<int64_t> g_launches{0};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_pending;
+std::vector<cudaEvent_t> g_pool;
+ProfAcc g_acc[kNumKinds];
+
+const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top",    "prefix_final",
+                                     "downsample",     "ffa_bottom",    "ffa_bottom_snr",
+                                     "ffa_level",      "ffa_final_snr", "boxcar_snr"};
+
+cudaEvent_t pool_get() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void drain_pending() {
+    for (auto& r : g_pending) {
+        float ms = 0.f;
+        cudaEventSynchronize(r.b);
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        g_acc[r.kind].launches += 1;
+        g_acc[r.kind].ms += ms;
+        g_acc[r.kind].bytes += r.bytes;
+        g_pool.push_back(r.a);
+        g_pool.push_back(r.b);
+    }
+    g_pending.clear();
+}
+
+// ---------------------------------------------------------------------------------
+// Search plan.
+// ---------------------------------------------------------------------------------
+struct Group {
+    int64_t bottom_off = 0, bottom_cnt = 0;
+    int bottom_smem = 0, bottom_buf = 0;
+    double bottom_bytes = 0;
+    int max_depth = 0;
+    std::vector<int64_t> level_off, level_cnt;  // index = depth d (1..max_depth-1)
+    std::vector<double> level_bytes;
+    int64_t final_off = 0, final_cnt = 0;
+    double final_bytes = 0;
+};
+
+struct Plan {
+    // parameters
+    int64_t n = 0;
+    double tsamp = 0, pmin = 0, pmax = 0;
+    int bmin = 0, bmax = 0;
+    std::vector<int> widths;
+    // derived
+    Widths W{};
+    std::vector<OctaveDesc> oct;
+    std::vector<TransformDesc> trs;
+    std::vector<WorkItem> items;
+    int64_t bottom0_off = 0, bottom0_cnt = 0;
+    int bottom0_smem = 0, bottom0_buf = 0, bottom0_snr_warps = 0;
+    double bottom0_bytes = 0;
+    std::vector<Group> groups;
+    int final_smem = 0, final_warp_floats = 0;
+    int64_t ntrials = 0, ds_total = 0, ds_floats = 0, scratch_floats = 0, folded = 0;
+    int max_rows = 0, max_p = 0;
+    int64_t nchunks = 0;
+    // workspace layout (bytes)
+    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, tables_bytes = 0;
+    size_t o_prefix = 0, o_partial = 0, o_ds = 0, o_s0 = 0, o_s1 = 0, ws_bytes = 0;
+    size_t o_hx = 0, o_hper = 0, o_hfb = 0, o_hsnr = 0, ws_host_bytes = 0;
+    void* pinned = nullptr;
+    ~Plan() {
+        if (pinned) cudaFreeHost(pinned);
+    }
+};
+
+constexpr size_t kStatusBytes = 256;
+std::mutex g_plan_mu;
+constexpr int64_t kGroupFloats = int64_t(16) << 20;  // 64 MB per scratch buffer
+
+// Rows of one shared-memory sub-tree: two buffers of n * p + 4 floats.
+int max_subtree_rows(int p) {
+    const int buf = (kSmemBytes - 16) / 8;
+    return std::max(1, (buf - 4) / p);
+}
+int bottom_buf_floats(int64_t elems, int snr_need) {
+    int need = (int)elems + 4;
+    if (snr_need > need) need = snr_need;
+    return (int)align_up((size_t)need, 4);
+}
+int depth_for(int m, int p) {
+    const int R = max_subtree_rows(p);
+    int d = 0;
+    while (((int64_t)m + (int64_t(1) << d) - 1) >> d > R) ++d;
+    return d;
+}
+
+ffa_status make_widths(const int32_t* h_widths, int32_t nw, int limit, Widths* W) {
+    if (!h_widths) return fail(FFA_ERR_ARG, "widths is null");
+    if (nw < 1 || nw > kMaxWidths) return fail(FFA_ERR_ARG, "nw must be in [1, %d]", kMaxWidths);
+    std::memset(W, 0, sizeof(*W));
+    W->nw = nw;
+    for (int i = 0; i < nw; ++i) {
+        const int w = h_widths[i];
+        if (w < 1 || w > limit) return fail(FFA_ERR_ARG, "width %d outside [1, %d]", w, limit);
+        if (i && w <= h_widths[i - 1]) return fail(FFA_ERR_ARG, "widths must increase strictly");
+        W->w[i] = w;
+        W->inv_sqrt_w[i] = (float)(1.0 / std::sqrt((double)w));
+        if (w > W->wmax) W->wmax = w;
+    }
+    return FFA_OK;
+}
+
+ffa_status check_search(int64_t n, double tsamp, double pmin, double pmax, int bmin, int bmax) {
+    if (n <= 0) return fail(FFA_ERR_ARG, "n must be positive");
+    if (!(tsamp > 0.0) || !std::isfinite(tsamp)) return fail(FFA_ERR_ARG, "tsamp must be > 0");
+    if (!(pmin > 0.0) || !(pmax > pmin) || !std::isfinite(pmax))
+        return fail(FFA_ERR_ARG, "need 0 < pmin < pmax");
+    if (bmin < 2 || bmax < bmin) return fail(FFA_ERR_ARG, "need 2 <= bmin <= bmax");
+    if (bmax > kMaxCols) return fail(FFA_ERR_UNSUPPORTED, "bmax above %d", kMaxCols);
+    if (pmin / ((double)bmin * tsamp) < 1.0)
+        return fail(FFA_ERR_ARG, "pmin / (bmin tsamp) < 1: first downsampling factor below 1");
+    if (n > (int64_t(1) << 40)) return fail(FFA_ERR_UNSUPPORTED, "n too large");
+    return FFA_OK;
+}
+
+void fixed_point(double f, uint64_t* fi, uint64_t* ff) {
+    const double fl = std::floor(f);
+    *fi = (uint64_t)fl;
+    // f - floor(f) is exact in double; scale by 2^64 exactly via ldexp
+    *ff = (uint64_t)std::ldexp(f - fl, 64);
+}
+
+ffa_status build_plan(Plan& pl) {
+    const double tsamp = pl.tsamp;
+    const double f0 = pl.pmin / ((double)pl.bmin * tsamp);     // Sec. 5.6: tau = Pmin / bmin
+    const double fg = ((double)pl.bmax + 1.0) / (double)pl.bmin;  // Sec. 5.3
+    int64_t ds_off = 0, first = 0;
+    std::vector<double> fac;
+    for (int k = 0;; ++k) {
+        const double f = f0 * std::pow(fg, (double)k);
+        if ((double)pl.bmin * tsamp * f > pl.pmax) break;
+        if (k > 4096) return fail(FFA_ERR_UNSUPPORTED, "too many octaves");
+        OctaveDesc od{};
+        od.nk = (int64_t)std::floor((double)pl.n / f);
+        od.out_off = ds_off;
+        od.first = first;
+        fixed_point(f, &od.f_int, &od.f_frac);
+        pl.oct.push_back(od);
+        fac.push_back(f);
+        ds_off += (int64_t)align_up((size_t)std::max<int64_t>(od.nk, 0), 4) + 4;
+        first += od.nk;
+    }
+    pl.ds_total = first;
+    pl.ds_floats = ds_off;
+    // Transforms in (octave, p) order (Sec. 5.3, Fig. 4).
+    int64_t trial = 0;
+    for (size_t k = 0; k < pl.oct.size(); ++k) {
+        const double f = fac[k];
+        const double var = (f == std::floor(f)) ? f : f - 1.0 / 3.0;  // App. A.4
+        for (int p = pl.bmin; p <= pl.bmax; ++p) {
+            const int64_t m64 = pl.oct[k].nk / p;
+            if (m64 < 2) continue;
+            if (m64 * p >= (int64_t(1) << 31)) return fail(FFA_ERR_UNSUPPORTED, "transform too large");
+            const int m = (int)m64;
+            int64_t kept = 0;  // rows with s (p + 1) < p (m - 1)  (Sec. 2.3)
+            kept = (int64_t)p * (m - 1) > 0 ? ((int64_t)p * (m - 1) - 1) / (p + 1) + 1 : 0;
+            if (kept > m) kept = m;
+            TransformDesc t{};
+            t.src_off = pl.oct[k].out_off;
+            t.scratch_off = 0;
+            t.trial0 = trial;
+            t.tau = tsamp * f;
+            t.p = p;
+            t.m = m;
+            t.kept = (int)kept;
+            t.depth = depth_for(m, p);
+            t.inv_std = (float)(1.0 / std::sqrt((double)m * var));
+            pl.trs.push_back(t);
+            trial += kept;
+            pl.folded += (int64_t)m * p;
+            pl.max_rows = std::max(pl.max_rows, m);
+            pl.max_p = std::max(pl.max_p, p);
+        }
+    }
+    pl.ntrials = trial;
+    const int wmax = pl.W.wmax;
+    const int nw = pl.W.nw;
+    const double out_row_bytes = 4.0 * nw + 12.0;
+
+    // Whole-tree-in-shared-memory transforms: one launch, fused S/N.
+    pl.bottom0_off = (int64_t)pl.items.size();
+    int64_t elems0 = 0;
+    int p0 = 0;
+    for (size_t t = 0; t < pl.trs.size(); ++t) {
+        const TransformDesc& d = pl.trs[t];
+        if (d.depth != 0) continue;
+        pl.items.push_back(WorkItem{(int32_t)t, 0});
+        elems0 = std::max<int64_t>(elems0, (int64_t)d.m * d.p);
+        p0 = std::max(p0, d.p);
+        pl.bottom0_bytes += 4.0 * d.m * d.p + out_row_bytes * d.kept;
+    }
+    pl.bottom0_cnt = (int64_t)pl.items.size() - pl.bottom0_off;
+    if (pl.bottom0_cnt) {
+        const int per_warp = p0 + wmax + 1;
+        int buf = bottom_buf_floats(elems0, 0);
+        pl.bottom0_snr_warps = std::min(kBottomThreads / 32, buf / per_warp);
+        if (pl.bottom0_snr_warps < 1) {
+            buf = bottom_buf_floats(elems0, per_warp);
+            pl.bottom0_snr_warps = 1;
+        }
+        pl.bottom0_buf = buf;
+        pl.bottom0_smem = 16 + 8 * buf;
+        if (pl.bottom0_smem > kSmemBytes) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+    }
+
+    // Deeper transforms: groups of consecutive transforms sharing the scratch buffers.
+    int64_t gfloats = 0;
+    Group cur;
+    bool open = false;
+    std::vector<int> members;
+    auto close_group = [&]() {
+        if (!open) return;
+        Group g = cur;
+        // bottom items
+        g.bottom_off = (int64_t)pl.items.size();
+        int64_t elems = 0;
+        for (int t : members) {
+            const TransformDesc& d = pl.trs[t];
+            for (int c = 0; c < (1 << d.depth); ++c) pl.items.push_back(WorkItem{t, c});
+            const int64_t rows = (d.m + (1 << d.depth) - 1) >> d.depth;
+            elems = std::max<int64_t>(elems, rows * d.p);
+            g.max_depth = std::max(g.max_depth, d.depth);
+            g.bottom_bytes += 8.0 * d.m * d.p;
+        }
+        g.bottom_cnt = (int64_t)pl.items.size() - g.bottom_off;
+        g.bottom_buf = bottom_buf_floats(elems, 0);
+        g.bottom_smem = 16 + 8 * g.bottom_buf;
+        // merge levels d = max_depth-1 .. 1
+        g.level_off.assign(g.max_depth, 0);
+        g.level_cnt.assign(g.max_depth, 0);
+        g.level_bytes.assign(g.max_depth, 0.0);
+        for (int d = g.max_depth - 1; d >= 1; --d) {
+            g.level_off[d] = (int64_t)pl.items.size();
+            for (int t : members) {
+                const TransformDesc& td = pl.trs[t];
+                if (td.depth <= d) continue;
+                const int nb = (td.m + kLevelRows - 1) / kLevelRows;
+                for (int b = 0; b < nb; ++b) pl.items.push_back(WorkItem{t, b});
+                g.level_bytes[d] += 8.0 * td.m * td.p;
+            }
+            g.level_cnt[d] = (int64_t)pl.items.size() - g.level_off[d];
+        }
+        g.final_off = (int64_t)pl.items.size();
+        for (int t : members) {
+            const TransformDesc& td = pl.trs[t];
+            const int nb = (td.kept + kFinalRows - 1) / kFinalRows;
+            for (int b = 0; b < nb; ++b) pl.items.push_back(WorkItem{t, b});
+            g.final_bytes += 4.0 * td.m * td.p + out_row_bytes * td.kept;
+        }
+        g.final_cnt = (int64_t)pl.items.size() - g.final_off;
+        pl.groups.push_back(g);
+        members.clear();
+        cur = Group();
+        open = false;
+        gfloats = 0;
+    };
+    for (size_t t = 0; t < pl.trs.size(); ++t) {
+        TransformDesc& d = pl.trs[t];
+        if (d.depth == 0) continue;
+        const int64_t need = (int64_t)d.m * d.p;
+        if (open && gfloats + need > kGroupFloats) close_group();
+        d.scratch_off = gfloats;
+        gfloats += (int64_t)align_up((size_t)need, 4);
+        pl.scratch_floats = std::max(pl.scratch_floats, gfloats);
+        members.push_back((int)t);
+        open = true;
+    }
+    close_group();
+    for (const Group& g : pl.groups)
+        if (g.bottom_smem > kSmemBytes) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+
+    // Last-level + S/N kernel: per warp p + (p + wmax + 1) floats.
+    pl.final_warp_floats = (int)align_up((size_t)(2 * pl.max_p + wmax + 1), 4);
+    pl.final_smem = (kFinalThreads / 32) * pl.final_warp_floats * 4;
+    if (pl.final_smem > kSmemBytes) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+
+    // Tables: octaves | transforms | items, each 256-byte aligned.
+    size_t o = 0;
+    pl.o_oct = o;
+    o = align_up(o + pl.oct.size() * sizeof(OctaveDesc), 256);
+    pl.o_trs = o;
+    o = align_up(o + pl.trs.size() * sizeof(TransformDesc), 256);
+    pl.o_items = o;
+    o = align_up(o + pl.items.size() * sizeof(WorkItem), 256);
+    pl.tables_bytes = std::max<size_t>(o, 256);
+
+    // Workspace: status | tables | prefix | chunk sums | series | scratch 0 | scratch 1
+    pl.nchunks = (pl.n + prefix_chunk() - 1) / prefix_chunk();
+    size_t w = kStatusBytes;
+    pl.o_tables = w;
+    w = align_up(w + pl.tables_bytes, 256);
+    pl.o_prefix = w;
+    w = align_up(w + (size_t)(pl.n + 1) * sizeof(float2), 256);
+    pl.o_partial = w;
+    w = align_up(w + (size_t)pl.nchunks * sizeof(float2), 256);
+    pl.o_ds = w;
+    w = align_up(w + (size_t)pl.ds_floats * 4, 256);
+    pl.o_s0 = w;
+    w = align_up(w + (size_t)pl.scratch_floats * 4, 256);
+    pl.o_s1 = w;
+    w = align_up(w + (size_t)pl.scratch_floats * 4, 256);
+    pl.ws_bytes = w;
+    // host-buffer variant: + input and outputs
+    pl.o_hx = w;
+    w = align_up(w + (size_t)pl.n * 4, 256);
+    pl.o_hper = w;
+    w = align_up(w + (size_t)pl.ntrials * 8, 256);
+    pl.o_hfb = w;
+    w = align_up(w + (size_t)pl.ntrials * 4, 256);
+    pl.o_hsnr = w;
+    w = align_up(w + (size_t)pl.ntrials * nw * 4, 256);
+    pl.ws_host_bytes = w;
+
+    return FFA_OK;
+}
+
+// Page-locked copy of the plan's tables, made on first execution (planning alone needs
+// no CUDA device).  Copied into the workspace on every call.
+ffa_status ensure_pinned(Plan& pl) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    if (pl.pinned) return FFA_OK;
+    void* p = nullptr;
+    FFA_CUDA(cudaHostAlloc(&p, pl.tables_bytes, cudaHostAllocDefault), "cudaHostAlloc");
+    char* h = static_cast<char*>(p);
+    std::memset(h, 0, pl.tables_bytes);
+    std::memcpy(h + pl.o_oct, pl.oct.data(), pl.oct.size() * sizeof(OctaveDesc));
+    std::memcpy(h + pl.o_trs, pl.trs.data(), pl.trs.size() * sizeof(TransformDesc));
+    std::memcpy(h + pl.o_items, pl.items.data(), pl.items.size() * sizeof(WorkItem));
+    pl.pinned = p;
+    return FFA_OK;
+}
+
+using PlanKey = std::tuple<int64_t, double, double, double, int, int, std::vector<int>>;
+std::map<PlanKey, std::unique_ptr<Plan>> g_plans;
+
+ffa_status get_plan(int64_t n, double tsamp, double pmin, double pmax, int bmin, int bmax,
+                    const int32_t* h_widths, int32_t nw, Plan** out) {
+    ffa_status st = check_search(n, tsamp, pmin, pmax, bmin, bmax);
+    if (st != FFA_OK) return st;
+    Widths W;
+    st = make_widths(h_widths, nw, bmin - 1, &W);  // widths below the smallest base period
+    if (st != FFA_OK) return st;
+    PlanKey key{n, tsamp, pmin, pmax, bmin, bmax, std::vector<int>(h_widths, h_widths + nw)};
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plans.find(key);
+    if (it != g_plans.end()) {
+        *out = it->second.get();
+        return FFA_OK;
+    }
+    auto pl = std::make_unique<Plan>();
+    pl->n = n;
+    pl->tsamp = tsamp;
+    pl->pmin = pmin;
+    pl->pmax = pmax;
+    pl->bmin = bmin;
+    pl->bmax = bmax;
+    pl->widths.assign(h_widths, h_widths + nw);
+    pl->W = W;
+    st = build_plan(*pl);
+    if (st != FFA_OK) return st;
+    if (g_plans.size() > 64) g_plans.clear();
+    *out = pl.get();
+    g_plans[key] = std::move(pl);
+    return FFA_OK;
+}
+
+// Issues the whole periodogram on `st`: tables upload, prefix, downsampling, then
+// the FFA + S/N launches group by group.
+ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d_periods,
+                           int32_t* d_foldbins, float* d_snr, char* ws, cudaStream_t st) {
+    unsigned* status = reinterpret_cast<unsigned*>(ws);
+    FFA_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st), "cudaMemsetAsync");
+    FFA_CUDA(cudaMemcpyAsync(ws + pl.o_tables, pl.pinned, pl.tables_bytes, cudaMemcpyHostToDevice,
+                             st),
+             "cudaMemcpyAsync(tables)");
+    const OctaveDesc* d_oct = reinterpret_cast<const OctaveDesc*>(ws + pl.o_tables + pl.o_oct);
+    const TransformDesc* d_trs =
+        reinterpret_cast<const TransformDesc*>(ws + pl.o_tables + pl.o_trs);
+    const WorkItem* d_items = reinterpret_cast<const WorkItem*>(ws + pl.o_tables + pl.o_items);
+    float2* prefix = reinterpret_cast<float2*>(ws + pl.o_prefix);
+    float* ds = reinterpret_cast<float*>(ws + pl.o_ds);
+    float* s0 = reinterpret_cast<float*>(ws + pl.o_s0);
+    float* s1 = reinterpret_cast<float*>(ws + pl.o_s1);
+
+    PrefixParams pp{d_x, dtype, pl.n, reinterpret_cast<float2*>(ws + pl.o_partial), prefix,
+                    pl.nchunks};
+    FFA_CUDA(launch_prefix(pp, st), "prefix launch");
+    DownsampleParams dp{};
+    dp.x = d_x;
+    dp.dtype = dtype;
+    dp.n = pl.n;
+    dp.prefix = prefix;
+    dp.oct = d_oct;
+    dp.noct = (int)pl.oct.size();
+    dp.total = pl.ds_total;
+    dp.out = ds;
+    FFA_CUDA(launch_downsample(dp, st), "downsample launch");
+
+    BottomParams bp{};
+    bp.src = ds;
+    bp.trs = d_trs;
+    bp.widths = pl.W;
+    bp.periods = d_periods;
+    bp.foldbins = d_foldbins;
+    bp.snr = d_snr;
+    bp.status = status;
+    if (pl.bottom0_cnt) {
+        bp.items = d_items + pl.bottom0_off;
+        bp.buf_floats = pl.bottom0_buf;
+        bp.snr_warps = pl.bottom0_snr_warps;
+        LaunchScope ls(kFfaBottomSnr, pl.bottom0_bytes, st);
+        FFA_CUDA(launch_bottom(bp, (int)pl.bottom0_cnt, pl.bottom0_smem, true, st),
+                 "ffa_bottom_snr launch");
+    }
+    for (const Group& g : pl.groups) {
+        bp.items = d_items + g.bottom_off;
+        bp.dst = s0;      // depth-D sub-trees land in buffer D % 2
+        bp.dst_odd = s1;
+        bp.buf_floats = g.bottom_buf;
+        bp.snr_warps = 0;
+        {
+            LaunchScope ls(kFfaBottom, g.bottom_bytes, st);
+            FFA_CUDA(launch_bottom(bp, (int)g.bottom_cnt, g.bottom_smem, false, st),
+                     "ffa_bottom launch");
+        }
+        for (int d = g.max_depth - 1; d >= 1; --d) {
+            LevelParams lp{};
+            lp.in = ((d + 1) & 1) ? s1 : s0;
+            lp.out = (d & 1) ? s1 : s0;
+            lp.trs = d_trs;
+            lp.items = d_items + g.level_off[d];
+            lp.depth = d;
+            LaunchScope ls(kFfaLevel, g.level_bytes[d], st);
+            FFA_CUDA(launch_level(lp, (int)g.level_cnt[d], st), "ffa_level launch");
+        }
+        FinalParams fp{};
+        fp.in = s1;  // depth 1
+        fp.trs = d_trs;
+        fp.items = d_items + g.final_off;
+        fp.widths = pl.W;
+        fp.periods = d_periods;
+        fp.foldbins = d_foldbins;
+        fp.snr = d_snr;
+        fp.warp_floats = pl.final_warp_floats;
+        LaunchScope ls(kFfaFinalSnr, g.final_bytes, st);
+        FFA_CUDA(launch_final(fp, (int)g.final_cnt, pl.final_smem, st), "ffa_final launch");
+    }
+    return FFA_OK;
+}
+
+bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) == 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+LaunchScope::LaunchScope(int k, double b, cudaStream_t s) : kind(k), bytes(b), stream(s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    ev0 = pool_get();
+    ev1 = pool_get();
+    cudaEventRecord(ev0, s);
+}
+LaunchScope::~LaunchScope() {
+    if (!ev0) return;
+    cudaEventRecord(ev1, stream);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_pending.push_back(ProfRec{kind, ev0, ev1, bytes});
+}
+
+}  // namespace ffa
+
+using namespace ffa;
+
+// =================================================================================
+// C ABI
+// =================================================================================
+extern "C" {
+
+const char* ffa_last_error(void) { return g_err.c_str(); }
+const char* ffa_version(void) { return "libffa 0.1 (sm_103a)"; }
+
+int64_t ffa_launch_count(void) { return g_launches.load(); }
+int32_t ffa_kernel_kinds(void) { return kNumKinds; }
+const char* ffa_kernel_name(int32_t kind) {
+    return (kind >= 0 && kind < kNumKinds) ? kKindNames[kind] : "";
+}
+ffa_status ffa_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return FFA_OK;
+}
+ffa_status ffa_profile_reset(void) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    drain_pending();
+    for (auto& a : g_acc) a = ProfAcc();
+    return FFA_OK;
+}
+ffa_status ffa_profile_query(int32_t kind, int64_t* launches, double* total_ms, double* alg_bytes) {
+    if (kind < 0 || kind >= kNumKinds) return fail(FFA_ERR_ARG, "bad kernel kind");
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    drain_pending();
+    if (launches) *launches = g_acc[kind].launches;
+    if (total_ms) *total_ms = g_acc[kind].ms;
+    if (alg_bytes) *alg_bytes = g_acc[kind].bytes;
+    return FFA_OK;
+}
+
+// ---------------------------------------------------------------------------------
+ffa_status ffa_downsample_workspace(int64_t n, size_t* bytes) {
+    if (!bytes) return fail(FFA_ERR_ARG, "bytes is null");
+    if (n <= 0) return fail(FFA_ERR_ARG, "n must be positive");
+    const int64_t nch = (n + prefix_chunk() - 1) / prefix_chunk();
+    *bytes = kStatusBytes + align_up((size_t)(n + 1) * sizeof(float2), 256) +
+             align_up((size_t)nch * sizeof(float2), 256);
+    return FFA_OK;
+}
+
+ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_out,
+                          int64_t out_cap, int64_t* n_out, void* d_ws, size_t ws_bytes,
+                          void* stream) {
+    if (!d_x || !d_out || !n_out || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
+    if (n <= 0) return fail(FFA_ERR_ARG, "n must be positive");
+    if (!(factor >= 1.0) || !std::isfinite(factor) || factor >= 4294967296.0)
+        return fail(FFA_ERR_ARG, "factor must be a finite number >= 1");
+    if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
+    const int64_t nk = (int64_t)std::floor((double)n / factor);
+    *n_out = nk;
+    if (out_cap < nk) return fail(FFA_ERR_CAPACITY, "out_cap %lld < %lld", (long long)out_cap,
+                                  (long long)nk);
+    size_t need = 0;
+    ffa_downsample_workspace(n, &need);
+    if (ws_bytes < need) return fail(FFA_ERR_CAPACITY, "workspace needs %zu bytes", need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(d_ws);
+    const int64_t nch = (n + prefix_chunk() - 1) / prefix_chunk();
+    float2* prefix = reinterpret_cast<float2*>(ws + kStatusBytes);
+    float2* partial =
+        reinterpret_cast<float2*>(ws + kStatusBytes + align_up((size_t)(n + 1) * sizeof(float2), 256));
+    FFA_CUDA(cudaMemsetAsync(ws, 0, sizeof(unsigned), st), "cudaMemsetAsync");
+    if (nk == 0) return FFA_OK;
+    PrefixParams pp{d_x, FFA_F32, n, partial, prefix, nch};
+    FFA_CUDA(launch_prefix(pp, st), "prefix launch");
+    DownsampleParams dp{};
+    dp.x = d_x;
+    dp.dtype = FFA_F32;
+    dp.n = n;
+    dp.prefix = prefix;
+    dp.oct = nullptr;
+    dp.noct = 1;
+    dp.total = nk;
+    dp.out = d_out;
+    dp.single.nk = nk;
+    fixed_point(factor, &dp.single.f_int, &dp.single.f_frac);
+    FFA_CUDA(launch_downsample(dp, st), "downsample launch");
+    return FFA_OK;
+}
+
+// ---------------------------------------------------------------------------------
+ffa_status ffa_transform_workspace(int32_t rows, int32_t cols, size_t* bytes) {
+    if (!bytes) return fail(FFA_ERR_ARG, "bytes is null");
+    if (rows < 1 || cols < 1) return fail(FFA_ERR_ARG, "rows and cols must be >= 1");
+    if (cols > kMaxCols) return fail(FFA_ERR_UNSUPPORTED, "cols above %d", kMaxCols);
+    if ((int64_t)rows * cols >= (int64_t(1) << 31)) return fail(FFA_ERR_UNSUPPORTED, "block too large");
+    const int D = depth_for(rows, cols);
+    *bytes = kStatusBytes + (D ? align_up((size_t)rows * cols * 4, 256) : 0);
+    return FFA_OK;
+}
+
+ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d_out,
+                         void* d_ws, size_t ws_bytes, void* stream) {
+    if (!d_in || !d_out || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
+    size_t need = 0;
+    ffa_status stt = ffa_transform_workspace(rows, cols, &need);
+    if (stt != FFA_OK) return stt;
+    if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < need) return fail(FFA_ERR_CAPACITY, "workspace needs %zu bytes", need);
+    const char* a0 = reinterpret_cast<const char*>(d_in);
+    const char* b0 = reinterpret_cast<const char*>(d_out);
+    const size_t nbytes = (size_t)rows * cols * 4;
+    if (a0 < b0 + nbytes && b0 < a0 + nbytes) return fail(FFA_ERR_ARG, "d_in and d_out overlap");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(d_ws);
+    unsigned* status = reinterpret_cast<unsigned*>(ws);
+    float* scratch = reinterpret_cast<float*>(ws + kStatusBytes);
+    FFA_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st), "cudaMemsetAsync");
+
+    const int D = depth_for(rows, cols);
+    TransformDesc t{};
+    t.p = cols;
+    t.m = rows;
+    t.kept = rows;
+    t.depth = D;
+    auto buf_of = [&](int d) { return (d & 1) ? scratch : d_out; };  // depth d lives here
+    BottomParams bp{};
+    bp.src = d_in;
+    bp.dst = d_out;
+    bp.dst_odd = scratch;
+    bp.single = t;
+    bp.status = status;
+    const int rows_d = (rows + (1 << D) - 1) >> D;
+    bp.buf_floats = bottom_buf_floats((int64_t)rows_d * cols, 0);
+    const int smem = 16 + 8 * bp.buf_floats;
+    {
+        LaunchScope ls(kFfaBottom, 8.0 * rows * cols, st);
+        FFA_CUDA(launch_bottom(bp, 1 << D, smem, false, st), "ffa_bottom launch");
+    }
+    for (int d = D - 1; d >= 0; --d) {
+        LevelParams lp{};
+        lp.in = buf_of(d + 1);
+        lp.out = buf_of(d);
+        lp.single = t;
+        lp.depth = d;
+        LaunchScope ls(kFfaLevel, 8.0 * rows * cols, st);
+        FFA_CUDA(launch_level(lp, (rows + kLevelRows - 1) / kLevelRows, st), "ffa_level launch");
+    }
+    return FFA_OK;
+}
+
+// ---------------------------------------------------------------------------------
+ffa_status ffa_boxcar_snr(const float* d_prof, int32_t rows, int32_t cols,
+                          const int32_t* h_widths, int32_t nw, double stdnoise, float* d_snr,
+                          void* stream) {
+    if (!d_prof || !d_snr) return fail(FFA_ERR_ARG, "null pointer");
+    if (rows < 0 || cols < 1) return fail(FFA_ERR_ARG, "rows >= 0 and cols >= 1 required");
+    if (cols > kMaxCols) return fail(FFA_ERR_UNSUPPORTED, "cols above %d", kMaxCols);
+    if (!(stdnoise > 0.0) || !std::isfinite(stdnoise)) return fail(FFA_ERR_ARG, "stdnoise must be > 0");
+    SnrParams sp{};
+    ffa_status stt = make_widths(h_widths, nw, cols, &sp.widths);
+    if (stt != FFA_OK) return stt;
+    sp.prof = d_prof;
+    sp.rows = rows;
+    sp.cols = cols;
+    sp.inv_std = (float)(1.0 / stdnoise);
+    sp.snr = d_snr;
+    sp.warp_floats = (int)align_up((size_t)(cols + sp.widths.wmax + 1), 4);
+    if (8 * sp.warp_floats * 4 > kSmemBytes)
+        return fail(FFA_ERR_UNSUPPORTED, "cols + max width too large for shared memory");
+    FFA_CUDA(launch_snr(sp, static_cast<cudaStream_t>(stream)), "boxcar_snr launch");
+    return FFA_OK;
+}
+
+// ---------------------------------------------------------------------------------
+ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pmax, int32_t bmin,
+                                int32_t bmax, const int32_t* h_widths, int32_t nw,
+                                ffa_plan_info* out) {
+    if (!out) return fail(FFA_ERR_ARG, "out is null");
+    Plan* pl = nullptr;
+    ffa_status st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, &pl);
+    if (st != FFA_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    out->ntrials = pl->ntrials;
+    out->noctaves = (int32_t)pl->oct.size();
+    out->ntransforms = (int32_t)pl->trs.size();
+    out->nwidths = nw;
+    out->max_rows = pl->max_rows;
+    out->downsampled_samples = pl->ds_total;
+    out->folded_samples = pl->folded;
+    out->workspace_bytes = pl->ws_bytes;
+    out->host_workspace_bytes = pl->ws_host_bytes;
+    return FFA_OK;
+}
+
+ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp, double pmin,
+                           double pmax, int32_t bmin, int32_t bmax, const int32_t* h_widths,
+                           int32_t nw, double* d_periods, int32_t* d_foldbins, float* d_snr,
+                           int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!d_x || !d_periods || !d_foldbins || !d_snr || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
+    if (dtype != FFA_F32 && dtype != FFA_F16 && dtype != FFA_I8) return fail(FFA_ERR_ARG, "bad dtype");
+    if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
+    Plan* pl = nullptr;
+    ffa_status st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, &pl);
+    if (st != FFA_OK) return st;
+    if (ntrials_cap < pl->ntrials)
+        return fail(FFA_ERR_CAPACITY, "ntrials_cap %lld < %lld", (long long)ntrials_cap,
+                    (long long)pl->ntrials);
+    if (ws_bytes < pl->ws_bytes) return fail(FFA_ERR_CAPACITY, "workspace needs %zu bytes", pl->ws_bytes);
+    st = ensure_pinned(*pl);
+    if (st != FFA_OK) return st;
+    return run_periodogram(*pl, d_x, dtype, d_periods, d_foldbins, d_snr, static_cast<char*>(d_ws),
+                           static_cast<cudaStream_t>(stream));
+}
+
+ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, double pmin,
+                                double pmax, int32_t bmin, int32_t bmax, const int32_t* h_widths,
+                                int32_t nw, double* h_periods, int32_t* h_foldbins, float* h_snr,
+                                int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!h_x || !h_periods || !h_foldbins || !h_snr || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
+    if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
+    Plan* pl = nullptr;
+    ffa_status st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, &pl);
+    if (st != FFA_OK) return st;
+    if (ntrials_cap < pl->ntrials) return fail(FFA_ERR_CAPACITY, "ntrials_cap too small");
+    if (ws_bytes < pl->ws_host_bytes)
+        return fail(FFA_ERR_CAPACITY, "workspace needs %zu bytes", pl->ws_host_bytes);
+    st = ensure_pinned(*pl);
+    if (st != FFA_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(d_ws);
+    float* x = reinterpret_cast<float*>(ws + pl->o_hx);
+    double* per = reinterpret_cast<double*>(ws + pl->o_hper);
+    int32_t* fb = reinterpret_cast<int32_t*>(ws + pl->o_hfb);
+    float* snr = reinterpret_cast<float*>(ws + pl->o_hsnr);
+    FFA_CUDA(cudaMemcpyAsync(x, h_x, (size_t)n * 4, cudaMemcpyHostToDevice, s), "copy in");
+    st = run_periodogram(*pl, x, FFA_F32, per, fb, snr, ws, s);
+    if (st != FFA_OK) return st;
+    const size_t T = (size_t)pl->ntrials;
+    FFA_CUDA(cudaMemcpyAsync(h_periods, per, T * 8, cudaMemcpyDeviceToHost, s), "copy periods");
+    FFA_CUDA(cudaMemcpyAsync(h_foldbins, fb, T * 4, cudaMemcpyDeviceToHost, s), "copy foldbins");
+    FFA_CUDA(cudaMemcpyAsync(h_snr, snr, T * nw * 4, cudaMemcpyDeviceToHost, s), "copy snr");
+    FFA_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return FFA_OK;
+}
+
+ffa_status ffa_check(void* d_ws, void* stream) {
+    if (!d_ws) return fail(FFA_ERR_ARG, "null workspace");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned v = 0;
+    FFA_CUDA(cudaMemcpyAsync(&v, d_ws, sizeof(v), cudaMemcpyDeviceToHost, s), "read status");
+    FFA_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    FFA_CUDA(cudaMemsetAsync(d_ws, 0, sizeof(v), s), "clear status");
+    if (v & kDevTimeout) return fail(FFA_ERR_TIMEOUT, "a device-side wait ran out of time");
+    if (v) return fail(FFA_ERR_DEVICE, "device status 0x%x", v);
+    return FFA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+"""Host-side checks of libffa that need no GPU: the library loads, exports every
+symbol include/ffa.h declares, plans searches exactly like the oracle's reading of
+Sec. 5.3, and rejects bad arguments before launching anything."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2004_03701_gb300 as ffa
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ffa.build()
+    return ffa.library()
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(ffa_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_symbols_exported(lib):
+    names = declared_functions()
+    assert "ffa_periodogram" in names and "ffa_transform" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.ffa_version()
+
+
+@pytest.mark.parametrize("args", [
+    (262144, 1e-3, 1.0, 10.0, 240, 260),
+    (2 ** 23, 64e-6, 0.2, 20.0, 240, 260),
+    (2 ** 21, 64e-6, 0.1, 10.0, 480, 520),
+    (100_000, 1e-3, 0.5, 3.0, 40, 44),
+    (5000, 1e-3, 0.5, 3.0, 40, 44),
+    (2 ** 23, 64e-6, 1.0, 120.0, 983, 1065),
+])
+def test_plan_matches_oracle(lib, args):
+    widths = (1, 2, 3, 4, 6, 9, 13, 19, 28)
+    info = ffa.periodogram_plan(*args, widths)
+    pl = oracle.plan(*args)
+    assert info.ntrials == pl.n_trials
+    assert info.noctaves == pl.n_octaves
+    assert info.ntransforms == pl.n_transforms
+    assert info.downsampled_samples == int(pl.oct_len.sum())
+    assert info.folded_samples == int((pl.tr_m * pl.tr_p).sum())
+    assert info.max_rows == (int(pl.tr_m.max()) if pl.n_transforms else 0)
+    assert info.workspace_bytes > 0 and info.host_workspace_bytes >= info.workspace_bytes
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=0), dict(tsamp=0.0), dict(pmin=20.0), dict(bmin=1), dict(bmax=200),
+    dict(pmin=0.1),                     # first downsampling factor below 1
+    dict(widths=(1, 1)), dict(widths=(0, 2)), dict(widths=(1, 240)), dict(widths=()),
+])
+def test_plan_rejects_bad_arguments(lib, bad):
+    a = dict(n=262144, tsamp=1e-3, pmin=1.0, pmax=10.0, bmin=240, bmax=260, widths=(1, 2, 4))
+    a.update(bad)
+    with pytest.raises(ffa.FFAError) as e:
+        ffa.periodogram_plan(a["n"], a["tsamp"], a["pmin"], a["pmax"], a["bmin"], a["bmax"],
+                             a["widths"])
+    assert e.value.status == 1
+
+
+def test_other_calls_reject_bad_arguments(lib):
+    sz = ctypes.c_size_t()
+    assert lib.ffa_transform_workspace(0, 5, ctypes.byref(sz)) == 1
+    assert lib.ffa_transform_workspace(5, 5000, ctypes.byref(sz)) == 5
+    assert lib.ffa_transform_workspace(5, 5, None) == 1
+    assert lib.ffa_downsample_workspace(0, ctypes.byref(sz)) == 1
+    n_out = ctypes.c_int64()
+    assert lib.ffa_downsample(None, 10, 2.0, None, 5, ctypes.byref(n_out), None, 0, None) == 1
+    fake = ctypes.c_void_p(256)   # never dereferenced: rejected on the host first
+    assert lib.ffa_downsample(fake, 10, 0.5, fake, 5, ctypes.byref(n_out), fake, 1 << 20,
+                              None) == 1
+    assert lib.ffa_downsample(fake, 100, 3.0, fake, 5, ctypes.byref(n_out), fake, 1 << 20,
+                              None) == 2
+    assert n_out.value == 33
+    w = np.array([1, 2], np.int32)
+    assert lib.ffa_boxcar_snr(fake, 4, 8, w.ctypes.data, 2, 0.0, fake, None) == 1
+    assert lib.ffa_boxcar_snr(fake, 4, 8, w.ctypes.data, 0, 1.0, fake, None) == 1
+    assert lib.ffa_transform(fake, 4, 8, fake, fake, 1 << 20, None) == 1  # in/out overlap
+    assert len(lib.ffa_last_error()) > 0
+    assert lib.ffa_check(None, None) == 1
+
+
+def test_kernel_kinds(lib):
+    names = ffa.kernel_names()
+    assert "ffa_bottom" in names and "ffa_final_snr" in names and "downsample" in names
+
+
+def test_width_sets_fit_the_plan(lib):
+    for wl in (synth.WIDTHS_11, synth.WIDTHS_16):
+        info = ffa.periodogram_plan(2 ** 21, 64e-6, 0.1, 10.0, 480, 520, wl)
+        assert info.nwidths == len(wl)
