@@ -235,9 +235,11 @@ class Searcher:
         T, nw = self.info.ntrials, len(self.widths)
         self.device = torch.device(device)
         self.ws = _workspace(self.info.workspace_bytes, self.device)
-        self.periods = torch.empty(T, dtype=torch.float64, device=self.device)
-        self.foldbins = torch.empty(T, dtype=torch.int32, device=self.device)
-        self.snr = torch.empty((T, nw), dtype=torch.float32, device=self.device)
+        # at least one element each, so that the device pointers are never null
+        self._per = torch.empty(max(T, 1), dtype=torch.float64, device=self.device)
+        self._fb = torch.empty(max(T, 1), dtype=torch.int32, device=self.device)
+        self._snr = torch.empty((max(T, 1), nw), dtype=torch.float32, device=self.device)
+        self.periods, self.foldbins, self.snr = self._per[:T], self._fb[:T], self._snr[:T]
         self._host_ws = None
 
     def __call__(self, x, stream=None):
@@ -247,7 +249,7 @@ class Searcher:
         n, tsamp, pmin, pmax, bmin, bmax = self.args
         _check(library().ffa_periodogram(
             _vp(x), _dtype_code(x), n, tsamp, pmin, pmax, bmin, bmax, _vp(self.widths),
-            len(self.widths), _vp(self.periods), _vp(self.foldbins), _vp(self.snr),
+            len(self.widths), _vp(self._per), _vp(self._fb), _vp(self._snr),
             self.periods.numel(), _vp(self.ws), self.ws.numel(), _stream_handle(stream)))
         return self.periods, self.foldbins, self.snr
 
@@ -258,7 +260,8 @@ class Searcher:
         n, tsamp, pmin, pmax, bmin, bmax = self.args
         _check(library().ffa_periodogram_host(
             _vp(x_host), n, tsamp, pmin, pmax, bmin, bmax, _vp(self.widths), len(self.widths),
-            _vp(periods_h), _vp(foldbins_h), _vp(snr_h), len(periods_h), _vp(self._host_ws),
+            _vp(periods_h), _vp(foldbins_h), _vp(snr_h), max(len(periods_h), self.info.ntrials),
+            _vp(self._host_ws),
             self._host_ws.numel(), _stream_handle(stream)))
 
     def check(self, stream=None):
@@ -280,11 +283,11 @@ def periodogram_host(x: np.ndarray, tsamp, pmin, pmax, bmin, bmax, widths, devic
     x = np.ascontiguousarray(x, dtype=np.float32)
     s = Searcher(len(x), tsamp, pmin, pmax, bmin, bmax, widths, device=device)
     T, nw = s.info.ntrials, len(s.widths)
-    per = np.empty(T, np.float64)
-    fb = np.empty(T, np.int32)
-    snr = np.empty((T, nw), np.float32)
+    per = np.empty(max(T, 1), np.float64)
+    fb = np.empty(max(T, 1), np.int32)
+    snr = np.empty((max(T, 1), nw), np.float32)
     s.run_host(x, per, fb, snr)
-    return per, fb, snr
+    return per[:T], fb[:T], snr[:T]
 
 
 def check(ws, stream=None) -> None:

@@ -67,9 +67,9 @@ std::vector<ProfRec> g_pending;
 std::vector<cudaEvent_t> g_pool;
 ProfAcc g_acc[kNumKinds];
 
-const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top",    "prefix_final",
-                                     "downsample",     "ffa_bottom",    "ffa_bottom_snr",
-                                     "ffa_level",      "ffa_final_snr", "boxcar_snr"};
+const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top", "prefix_final",
+                                     "downsample",     "ffa_bottom", "ffa_bottom_snr",
+                                     "ffa_top",        "ffa_top_snr", "boxcar_snr"};
 
 cudaEvent_t pool_get() {
     if (!g_pool.empty()) {
@@ -99,15 +99,16 @@ void drain_pending() {
 // ---------------------------------------------------------------------------------
 // Search plan.
 // ---------------------------------------------------------------------------------
+struct Stage {              // one top-kernel launch: pass j of every transform that has it
+    int64_t off = 0, cnt = 0;
+    int smem = 0;
+    double bytes = 0;
+};
 struct Group {
     int64_t bottom_off = 0, bottom_cnt = 0;
     int bottom_smem = 0, bottom_buf = 0;
     double bottom_bytes = 0;
-    int max_depth = 0;
-    std::vector<int64_t> level_off, level_cnt;  // index = depth d (1..max_depth-1)
-    std::vector<double> level_bytes;
-    int64_t final_off = 0, final_cnt = 0;
-    double final_bytes = 0;
+    std::vector<Stage> stages;
 };
 
 struct Plan {
@@ -125,7 +126,6 @@ struct Plan {
     int bottom0_smem = 0, bottom0_buf = 0, bottom0_snr_warps = 0;
     double bottom0_bytes = 0;
     std::vector<Group> groups;
-    int final_smem = 0, final_warp_floats = 0;
     int64_t ntrials = 0, ds_total = 0, ds_floats = 0, scratch_floats = 0, folded = 0;
     int max_rows = 0, max_p = 0;
     int64_t nchunks = 0;
@@ -143,10 +143,11 @@ constexpr size_t kStatusBytes = 256;
 std::mutex g_plan_mu;
 constexpr int64_t kGroupFloats = int64_t(16) << 20;  // 64 MB per scratch buffer
 
-// Rows of one shared-memory sub-tree: two buffers of n * p + 4 floats.
+// Rows of one shared-memory sub-tree: two buffers of round4(n * p + 4) floats after a
+// 16-byte barrier slot, within kSmemBytes.
 int max_subtree_rows(int p) {
-    const int buf = (kSmemBytes - 16) / 8;
-    return std::max(1, (buf - 4) / p);
+    const int cap = ((kSmemBytes - 16) / 8) & ~3;
+    return std::max(1, (cap - 4) / p);
 }
 int bottom_buf_floats(int64_t elems, int snr_need) {
     int need = (int)elems + 4;
@@ -158,6 +159,22 @@ int depth_for(int m, int p) {
     int d = 0;
     while (((int64_t)m + (int64_t(1) << d) - 1) >> d > R) ++d;
     return d;
+}
+
+// Rows per top-kernel CTA: the most that fit in shared memory (at most kTopMaxRows).
+int top_rows(int p, int L, bool score, int wmax) {
+    for (int K = kTopMaxRows; K >= 1; --K)
+        if (top_layout(K, L, p, wmax, score).total * 4 <= kSmemBytes) return K;
+    return 0;
+}
+
+// Merge levels per top pass for base period p: the most (up to kTopMaxLevels) for which
+// at least one row per CTA fits when stored and, if `score`, when scored.
+int top_chunk(int p, int wmax, bool score) {
+    for (int c = kTopMaxLevels; c >= 1; --c)
+        if (top_rows(p, c, false, wmax) >= 1 && (!score || top_rows(p, c, true, wmax) >= 1))
+            return c;
+    return 0;
 }
 
 ffa_status make_widths(const int32_t* h_widths, int32_t nw, int limit, Widths* W) {
@@ -240,6 +257,8 @@ ffa_status build_plan(Plan& pl) {
             t.m = m;
             t.kept = (int)kept;
             t.depth = depth_for(m, p);
+            t.chunk = top_chunk(p, pl.W.wmax, true);
+            if (t.chunk < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
             t.inv_std = (float)(1.0 / std::sqrt((double)m * var));
             pl.trs.push_back(t);
             trial += kept;
@@ -281,52 +300,52 @@ ffa_status build_plan(Plan& pl) {
 
     // Deeper transforms: groups of consecutive transforms sharing the scratch buffers.
     int64_t gfloats = 0;
-    Group cur;
     bool open = false;
     std::vector<int> members;
+    ffa_status kerr = FFA_OK;
     auto close_group = [&]() {
         if (!open) return;
-        Group g = cur;
-        // bottom items
+        Group g;
         g.bottom_off = (int64_t)pl.items.size();
         int64_t elems = 0;
+        int maxpass = 0;
         for (int t : members) {
             const TransformDesc& d = pl.trs[t];
-            for (int c = 0; c < (1 << d.depth); ++c) pl.items.push_back(WorkItem{t, c});
+            for (int c = 0; c < (1 << d.depth); ++c) pl.items.push_back(WorkItem{t, c, 0, 0, 0});
             const int64_t rows = (d.m + (1 << d.depth) - 1) >> d.depth;
             elems = std::max<int64_t>(elems, rows * d.p);
-            g.max_depth = std::max(g.max_depth, d.depth);
+            maxpass = std::max(maxpass, top_passes(d.depth, d.chunk));
             g.bottom_bytes += 8.0 * d.m * d.p;
         }
         g.bottom_cnt = (int64_t)pl.items.size() - g.bottom_off;
         g.bottom_buf = bottom_buf_floats(elems, 0);
         g.bottom_smem = 16 + 8 * g.bottom_buf;
-        // merge levels d = max_depth-1 .. 1
-        g.level_off.assign(g.max_depth, 0);
-        g.level_cnt.assign(g.max_depth, 0);
-        g.level_bytes.assign(g.max_depth, 0.0);
-        for (int d = g.max_depth - 1; d >= 1; --d) {
-            g.level_off[d] = (int64_t)pl.items.size();
+        for (int j = 0; j < maxpass; ++j) {
+            Stage s;
+            s.off = (int64_t)pl.items.size();
             for (int t : members) {
-                const TransformDesc& td = pl.trs[t];
-                if (td.depth <= d) continue;
-                const int nb = (td.m + kLevelRows - 1) / kLevelRows;
-                for (int b = 0; b < nb; ++b) pl.items.push_back(WorkItem{t, b});
-                g.level_bytes[d] += 8.0 * td.m * td.p;
+                const TransformDesc& d = pl.trs[t];
+                const int np = top_passes(d.depth, d.chunk);
+                if (j >= np) continue;
+                const int dout = top_pass_out_depth(d.depth, d.chunk, j);
+                const int L = top_pass_in_depth(d.depth, d.chunk, j) - dout;
+                const bool score = j == np - 1;
+                const int K = top_rows(d.p, L, score, wmax);
+                if (K < 1) { kerr = fail(FFA_ERR_UNSUPPORTED, "profile too long"); return; }
+                s.smem = std::max(s.smem, top_layout(K, L, d.p, wmax, score).total * 4);
+                const int nmax = (d.m + (1 << dout) - 1) >> dout;
+                const int lim = score ? d.kept : nmax;
+                const int nb = (lim + K - 1) / K;
+                const int cnt = score ? nb : (1 << dout) * nb;
+                for (int i = 0; i < cnt; ++i)
+                    pl.items.push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, 0});
+                s.bytes += 4.0 * d.m * d.p + (score ? out_row_bytes * d.kept : 4.0 * d.m * d.p);
             }
-            g.level_cnt[d] = (int64_t)pl.items.size() - g.level_off[d];
+            s.cnt = (int64_t)pl.items.size() - s.off;
+            g.stages.push_back(s);
         }
-        g.final_off = (int64_t)pl.items.size();
-        for (int t : members) {
-            const TransformDesc& td = pl.trs[t];
-            const int nb = (td.kept + kFinalRows - 1) / kFinalRows;
-            for (int b = 0; b < nb; ++b) pl.items.push_back(WorkItem{t, b});
-            g.final_bytes += 4.0 * td.m * td.p + out_row_bytes * td.kept;
-        }
-        g.final_cnt = (int64_t)pl.items.size() - g.final_off;
         pl.groups.push_back(g);
         members.clear();
-        cur = Group();
         open = false;
         gfloats = 0;
     };
@@ -342,13 +361,9 @@ ffa_status build_plan(Plan& pl) {
         open = true;
     }
     close_group();
+    if (kerr != FFA_OK) return kerr;
     for (const Group& g : pl.groups)
         if (g.bottom_smem > kSmemBytes) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
-
-    // Last-level + S/N kernel: per warp p + (p + wmax + 1) floats.
-    pl.final_warp_floats = (int)align_up((size_t)(2 * pl.max_p + wmax + 1), 4);
-    pl.final_smem = (kFinalThreads / 32) * pl.final_warp_floats * 4;
-    if (pl.final_smem > kSmemBytes) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
 
     // Tables: octaves | transforms | items, each 256-byte aligned.
     size_t o = 0;
@@ -490,7 +505,7 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     }
     for (const Group& g : pl.groups) {
         bp.items = d_items + g.bottom_off;
-        bp.dst = s0;      // depth-D sub-trees land in buffer D % 2
+        bp.dst = s0;      // sub-trees of a transform with P top passes land in buffer P % 2
         bp.dst_odd = s1;
         bp.buf_floats = g.bottom_buf;
         bp.snr_warps = 0;
@@ -499,27 +514,21 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
             FFA_CUDA(launch_bottom(bp, (int)g.bottom_cnt, g.bottom_smem, false, st),
                      "ffa_bottom launch");
         }
-        for (int d = g.max_depth - 1; d >= 1; --d) {
-            LevelParams lp{};
-            lp.in = ((d + 1) & 1) ? s1 : s0;
-            lp.out = (d & 1) ? s1 : s0;
-            lp.trs = d_trs;
-            lp.items = d_items + g.level_off[d];
-            lp.depth = d;
-            LaunchScope ls(kFfaLevel, g.level_bytes[d], st);
-            FFA_CUDA(launch_level(lp, (int)g.level_cnt[d], st), "ffa_level launch");
+        for (size_t j = 0; j < g.stages.size(); ++j) {
+            const Stage& sg = g.stages[j];
+            TopParams tp{};
+            tp.buf0 = s0;
+            tp.buf1 = s1;
+            tp.trs = d_trs;
+            tp.items = d_items + sg.off;
+            tp.widths = pl.W;
+            tp.periods = d_periods;
+            tp.foldbins = d_foldbins;
+            tp.snr = d_snr;
+            tp.status = status;
+            LaunchScope ls(kFfaTopSnr, sg.bytes, st);
+            FFA_CUDA(launch_top(tp, (int)sg.cnt, sg.smem, st), "ffa_top launch");
         }
-        FinalParams fp{};
-        fp.in = s1;  // depth 1
-        fp.trs = d_trs;
-        fp.items = d_items + g.final_off;
-        fp.widths = pl.W;
-        fp.periods = d_periods;
-        fp.foldbins = d_foldbins;
-        fp.snr = d_snr;
-        fp.warp_floats = pl.final_warp_floats;
-        LaunchScope ls(kFfaFinalSnr, g.final_bytes, st);
-        FFA_CUDA(launch_final(fp, (int)g.final_cnt, pl.final_smem, st), "ffa_final launch");
     }
     return FFA_OK;
 }
@@ -667,10 +676,12 @@ ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d
     t.m = rows;
     t.kept = rows;
     t.depth = D;
-    auto buf_of = [&](int d) { return (d & 1) ? scratch : d_out; };  // depth d lives here
+    t.chunk = top_chunk(cols, 0, false);
+    if (t.chunk < 1) return fail(FFA_ERR_UNSUPPORTED, "cols too large for the top kernel");
+    const int npass = top_passes(D, t.chunk);
     BottomParams bp{};
     bp.src = d_in;
-    bp.dst = d_out;
+    bp.dst = d_out;     // with P top passes the sub-trees go to buffer P % 2: d_out or scratch
     bp.dst_odd = scratch;
     bp.single = t;
     bp.status = status;
@@ -681,14 +692,23 @@ ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d
         LaunchScope ls(kFfaBottom, 8.0 * rows * cols, st);
         FFA_CUDA(launch_bottom(bp, 1 << D, smem, false, st), "ffa_bottom launch");
     }
-    for (int d = D - 1; d >= 0; --d) {
-        LevelParams lp{};
-        lp.in = buf_of(d + 1);
-        lp.out = buf_of(d);
-        lp.single = t;
-        lp.depth = d;
-        LaunchScope ls(kFfaLevel, 8.0 * rows * cols, st);
-        FFA_CUDA(launch_level(lp, (rows + kLevelRows - 1) / kLevelRows, st), "ffa_level launch");
+    for (int j = 0; j < npass; ++j) {
+        const int dout = top_pass_out_depth(D, t.chunk, j);
+        const int L = top_pass_in_depth(D, t.chunk, j) - dout;
+        const int K = top_rows(cols, L, false, 0);
+        if (K < 1) return fail(FFA_ERR_UNSUPPORTED, "cols too large for the top kernel");
+        const int nmax = (rows + (1 << dout) - 1) >> dout;
+        const int nb = (nmax + K - 1) / K;
+        TopParams tp{};
+        tp.buf0 = d_out;
+        tp.buf1 = scratch;
+        tp.single = t;
+        tp.status = status;
+        tp.single_pass = j;
+        tp.single_rows = K;
+        LaunchScope ls(kFfaTop, 8.0 * rows * cols, st);
+        FFA_CUDA(launch_top(tp, (1 << dout) * nb, top_layout(K, L, cols, 0, false).total * 4, st),
+                 "ffa_top launch");
     }
     return FFA_OK;
 }

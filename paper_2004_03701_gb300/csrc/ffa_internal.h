@@ -12,11 +12,10 @@ namespace ffa {
 constexpr int kMaxWidths = 64;       // boxcar widths per search
 constexpr int kMaxCols = 4096;       // base period (bins) limit of this build
 constexpr int kSmemBytes = 232448;   // dynamic shared memory per CTA on sm_103 (227 KB)
-constexpr int kBottomThreads = 512;  // CTA of the shared-memory FFA kernel
-constexpr int kLevelThreads = 256;   // CTA of the global merge-level kernel
-constexpr int kLevelRows = 32;       // output rows per CTA of a merge level
-constexpr int kFinalThreads = 256;   // CTA of the last-level + S/N kernel
-constexpr int kFinalRows = 32;       // output rows per CTA of that kernel
+constexpr int kBottomThreads = 512;  // CTA of the shared-memory sub-tree kernel
+constexpr int kTopThreads = 512;     // CTA of the gathered top-level kernel
+constexpr int kTopMaxLevels = 3;     // merge levels per top pass
+constexpr int kTopMaxRows = 128;     // output rows per top CTA
 
 // Device status word bits (first word of every workspace).
 constexpr unsigned kDevTimeout = 1u;
@@ -33,15 +32,71 @@ struct TransformDesc {
     int32_t kept;         // rows s with P_s < (p + 1) tau  (Sec. 2.3)
     int32_t depth;        // depth of the shared-memory sub-trees (0 = whole tree)
     float inv_std;        // 1 / sqrt(m V_f): noise std of one folded bin, inverted
-    int32_t pad;
+    int32_t chunk;        // merge levels per top pass (1..kTopMaxLevels)
 };
 static_assert(sizeof(TransformDesc) == 56, "TransformDesc layout");
 
-// A CTA's share of a launch: transform index and node / row-block index.
+// A CTA's share of a launch: transform index, node / row-block index, and for the
+// top kernel the pass index and the rows per block.
 struct WorkItem {
     int32_t tr;
     int32_t idx;
+    int16_t pass;
+    int16_t rows;
+    int32_t pad;
 };
+static_assert(sizeof(WorkItem) == 16, "WorkItem layout");
+
+// Passes of the top of an FFA tree whose shared-memory sub-trees sit at depth D:
+// chunks of `chunk` levels from the bottom, the last one reaching the root.
+__host__ __device__ inline int top_passes(int depth, int chunk) {
+    return (depth + chunk - 1) / chunk;
+}
+__host__ __device__ inline int top_pass_in_depth(int depth, int chunk, int pass) {
+    return depth - chunk * pass;
+}
+__host__ __device__ inline int top_pass_out_depth(int depth, int chunk, int pass) {
+    const int d = depth - chunk * (pass + 1);
+    return d > 0 ? d : 0;
+}
+
+// Shared-memory layout (in floats) of a top-kernel CTA merging L levels for K output
+// rows of p bins.  Rows of level l (0 = output) number at most K + 3 (2^l - 1).
+struct TopLayout {
+    int table;      // interval table (ints): 15 nodes x 8 ints
+    int desc;       // row descriptors (int4), desc_cap of them
+    int desc_cap;
+    int buf_a;      // levels L, L-2, ...   (level L with per-interval alignment slack)
+    int buf_b;      // levels L-1, L-3, ...
+    int sbuf;       // per-warp prefix-sum rows of the boxcar S/N
+    int sbuf_warp;  // floats per warp
+    int total;      // floats
+};
+__host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
+__host__ __device__ inline TopLayout top_layout(int K, int L, int p, int wmax, bool snr) {
+    TopLayout t;
+    int off = 4;  // mbarrier
+    t.table = off;
+    off += 128;
+    t.desc = off;
+    t.desc_cap = L * K + 3 * (1 << L) + 8;
+    off += 4 * t.desc_cap;
+    int cap_a = 0, cap_b = 0;
+    for (int l = 0; l <= L; ++l) {
+        int sz = (K + 3 * ((1 << l) - 1)) * p + (l == L ? 8 * (1 << L) : 0);
+        if (((L - l) & 1) == 0) cap_a = cap_a > sz ? cap_a : sz;
+        else cap_b = cap_b > sz ? cap_b : sz;
+    }
+    t.buf_a = off;
+    off += round4(cap_a);
+    t.buf_b = off;
+    off += round4(cap_b);
+    t.sbuf = off;
+    t.sbuf_warp = snr ? round4(p + wmax + 1) : 0;
+    off += (kTopThreads / 32) * t.sbuf_warp;
+    t.total = off;
+    return t;
+}
 
 // Downsampling of one octave: factor f in 64.64 fixed point (exact for a double).
 struct OctaveDesc {
@@ -67,8 +122,8 @@ enum KernelKind : int {
     kDownsample,
     kFfaBottom,
     kFfaBottomSnr,
-    kFfaLevel,
-    kFfaFinalSnr,
+    kFfaTop,
+    kFfaTopSnr,
     kBoxcarSnr,
     kNumKinds
 };
@@ -99,8 +154,8 @@ struct DownsampleParams {
 
 struct BottomParams {
     const float* src;               // octave series buffer or the caller's block
-    float* dst;                     // where sub-trees of even depth are written
-    float* dst_odd;                 // where sub-trees of odd depth are written
+    float* dst;                     // sub-trees of transforms with an even number of top
+    float* dst_odd;                 // passes go to dst, the others to dst_odd
     const TransformDesc* trs;       // null: use `single`
     const WorkItem* items;          // null: item = {0, blockIdx.x}
     TransformDesc single;
@@ -113,25 +168,19 @@ struct BottomParams {
     int snr_warps;                  // warps that score rows (fused S/N mode)
 };
 
-struct LevelParams {
-    const float* in;
-    float* out;
+struct TopParams {
+    float* buf0;                    // the two scratch buffers: pass j of a transform with
+    float* buf1;                    // P passes reads buf[(P-j)&1], writes buf[(P-j-1)&1]
     const TransformDesc* trs;
     const WorkItem* items;
-    TransformDesc single;
-    int depth;                      // depth of the nodes this launch computes
-};
-
-struct FinalParams {
-    const float* in;                // depth-1 transforms
-    const TransformDesc* trs;
-    const WorkItem* items;
-    TransformDesc single;
+    TransformDesc single;           // used when trs is null
     Widths widths;
     double* periods;
     int32_t* foldbins;
-    float* snr;
-    int warp_floats;                // shared floats per warp
+    float* snr;                     // null: the last pass stores the transform instead
+    unsigned* status;
+    int single_pass;                // pass and rows per block when items is null
+    int single_rows;
 };
 
 struct SnrParams {
@@ -149,8 +198,7 @@ cudaError_t launch_prefix(const PrefixParams& P, cudaStream_t s);
 cudaError_t launch_downsample(const DownsampleParams& P, cudaStream_t s);
 cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bool snr_mode,
                           cudaStream_t s);
-cudaError_t launch_level(const LevelParams& P, int nblocks, cudaStream_t s);
-cudaError_t launch_final(const FinalParams& P, int nblocks, int smem_bytes, cudaStream_t s);
+cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s);
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s);
 
 // Launch accounting (ffa_api.cu): brackets one launch with profiling events.

@@ -10,9 +10,11 @@
 //                 merge level of the sub-tree (Eq. ffa_merge_rule) runs in shared
 //                 memory; either writes the sub-tree's transform or, when the sub-tree
 //                 is the whole transform, scores its rows directly (fused S/N).
-//   ffa_level     one merge level of the top of the tree, through L2.
-//   ffa_final_snr the last merge level fused with the boxcar S/N (Sec. 5.4): the final
-//                 folded profiles are built in shared memory and never stored.
+//   ffa_top       the levels above the sub-trees, up to three per pass: a CTA gathers
+//                 only the rows its block of outputs depends on (one interval per
+//                 descendant, one bulk copy each) and merges them in shared memory;
+//                 the last pass of a periodogram scores its rows with the boxcar
+//                 filters (Sec. 5.4), so final profiles are never stored.
 //   boxcar_snr    standalone S/N of stored profiles.
 //
 // Every floating-point add of the FFA is the same single float add of H_i[x] and
@@ -262,16 +264,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 // Boxcar S/N of one profile by one warp (Sec. 5.4).  S = exclusive prefix sum over
 // two concatenated repeats (length p + wmax + 1, in shared memory), then for each
 // width w the largest S[k + w] - S[k], scaled by 1 / (stdnoise sqrt(w)).
+// T = ceil(p / 32): each lane keeps S[lane + 32 t] in registers.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ void warp_snr(const float* prof, int p, float* S, const Widths& W,
-                                         float inv_std, float* out, int lane) {
-    const int L = p + W.wmax;
+__device__ __forceinline__ void warp_prefix(const float* prof, int p, int L, float* S, int lane) {
     const int c = (L + 31) >> 5;
     const int i0 = lane * c;
     const int i1 = min(i0 + c, L);
     float acc = 0.f;
     for (int i = i0; i < i1; ++i) acc += prof[i < p ? i : i - p];
     float inc = acc;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         float v = __shfl_up_sync(kFull, inc, o);
         if (lane >= o) inc += v;
@@ -286,6 +288,36 @@ __device__ __forceinline__ void warp_snr(const float* prof, int p, float* S, con
         S[i + 1] = run;
     }
     __syncwarp();
+}
+
+template <int T>
+__device__ __forceinline__ void warp_snr_t(const float* prof, int p, float* S, const Widths& W,
+                                           float inv_std, float* out, int lane) {
+    warp_prefix(prof, p, p + W.wmax, S, lane);
+    float sk[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int k = lane + 32 * t;
+        sk[t] = k < p ? S[k] : 0.f;
+    }
+    for (int iw = 0; iw < W.nw; ++iw) {
+        const float* Sw = S + W.w[iw];
+        float best = -INFINITY;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int k = lane + 32 * t;
+            if (k < p) best = fmaxf(best, Sw[k] - sk[t]);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
+        if (lane == 0) out[iw] = best * inv_std * W.inv_sqrt_w[iw];
+    }
+    __syncwarp();
+}
+
+__device__ __noinline__ void warp_snr_any(const float* prof, int p, float* S, const Widths& W,
+                                          float inv_std, float* out, int lane) {
+    warp_prefix(prof, p, p + W.wmax, S, lane);
     for (int iw = 0; iw < W.nw; ++iw) {
         const int w = W.w[iw];
         float best = -INFINITY;
@@ -296,24 +328,94 @@ __device__ __forceinline__ void warp_snr(const float* prof, int p, float* S, con
     __syncwarp();
 }
 
+__device__ __forceinline__ void warp_snr(const float* prof, int p, float* S, const Widths& W,
+                                         float inv_std, float* out, int lane) {
+    switch ((p + 31) >> 5) {
+        case 1: warp_snr_t<1>(prof, p, S, W, inv_std, out, lane); break;
+        case 2: warp_snr_t<2>(prof, p, S, W, inv_std, out, lane); break;
+        case 3: warp_snr_t<3>(prof, p, S, W, inv_std, out, lane); break;
+        case 4: warp_snr_t<4>(prof, p, S, W, inv_std, out, lane); break;
+        case 5: warp_snr_t<5>(prof, p, S, W, inv_std, out, lane); break;
+        case 6: warp_snr_t<6>(prof, p, S, W, inv_std, out, lane); break;
+        case 7: warp_snr_t<7>(prof, p, S, W, inv_std, out, lane); break;
+        case 8: warp_snr_t<8>(prof, p, S, W, inv_std, out, lane); break;
+        case 9: warp_snr_t<9>(prof, p, S, W, inv_std, out, lane); break;
+        case 10: warp_snr_t<10>(prof, p, S, W, inv_std, out, lane); break;
+        case 11: warp_snr_t<11>(prof, p, S, W, inv_std, out, lane); break;
+        case 12: warp_snr_t<12>(prof, p, S, W, inv_std, out, lane); break;
+        case 13: warp_snr_t<13>(prof, p, S, W, inv_std, out, lane); break;
+        case 14: warp_snr_t<14>(prof, p, S, W, inv_std, out, lane); break;
+        case 15: warp_snr_t<15>(prof, p, S, W, inv_std, out, lane); break;
+        case 16: warp_snr_t<16>(prof, p, S, W, inv_std, out, lane); break;
+        case 17: warp_snr_t<17>(prof, p, S, W, inv_std, out, lane); break;
+        default: warp_snr_any(prof, p, S, W, inv_std, out, lane); break;
+    }
+}
+
 __device__ __forceinline__ double trial_period(double tau, int p, int m, int s) {
     // P_s = tau p^2 / (p - s / (m - 1))  (Sec. 2.3), same operation order as the oracle
     return tau * (double)p * (double)p / ((double)p - (double)s / (double)(m - 1));
 }
 
+// One merge (Eq. ffa_merge_rule) of shared-memory rows by one warp:
+//   sm[o + x] = sm[a + x] + sm[b + (x + k) mod p],   0 <= k < p.
+// Offsets are in floats from the shared-memory base; lanes take consecutive columns.
+__device__ __forceinline__ void merge_row(float* sm, int o, int a, int b, int k, int p, int lane) {
+    int y = lane + k;
+    if (y >= p) y -= p;
+#pragma unroll 4
+    for (int x = lane; x < p; x += 32) {
+        sm[o + x] = __fadd_rn(sm[a + x], sm[b + y]);
+        y += 32;
+        if (y >= p) y -= p;
+    }
+}
+__device__ __forceinline__ void copy_row(float* sm, int o, int a, int p, int lane) {
+#pragma unroll 4
+    for (int x = lane; x < p; x += 32) sm[o + x] = sm[a + x];
+}
+
+// Rows [0, total) of `src` (global) into shared memory at sm + dst (a float offset whose
+// alignment mod 4 matches src's): one bulk copy of the 16-byte-aligned interior, plain
+// loads for up to 3 floats at either end.  bulk_bytes() is what the copy moves; every
+// thread can evaluate it, so all agree on whether to wait.
+__device__ __forceinline__ int bulk_lead(const float* src) {
+    const int h = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+    return h ? 4 - h : 0;
+}
+__device__ __forceinline__ unsigned bulk_bytes(const float* src, int total) {
+    const int lead = bulk_lead(src);
+    return total > lead ? (unsigned)(((total - lead) & ~3) * 4) : 0u;
+}
+__device__ __forceinline__ void issue_rows_copy(float* sm, int dst, const float* src, int total,
+                                                uint64_t* bar) {
+    const int lead = bulk_lead(src);
+    const unsigned bytes = bulk_bytes(src, total);
+    if (bytes) bulk_g2s(sm + dst + lead, src + lead, bytes, bar);
+}
+__device__ __forceinline__ void load_row_ends(float* sm, int dst, const float* src, int total,
+                                              int tid, int nthreads) {
+    const int lead = bulk_lead(src);
+    const int body = (int)(bulk_bytes(src, total) / 4);
+    const int tail0 = lead + body;
+    const int nends = lead + (total - tail0);
+    for (int e = tid; e < nends; e += nthreads) {
+        const int q = e < lead ? e : tail0 + (e - lead);
+        sm[dst + q] = src[q];
+    }
+}
+
 // ---------------------------------------------------------------------------------
-// Shared-memory FFA of one sub-tree.
+// Shared-memory FFA of one sub-tree (all of its levels, breadth-first by height).
 // ---------------------------------------------------------------------------------
 template <bool kSnr>
 __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams P) {
     extern __shared__ __align__(16) float smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    float* bufA = smem + 4;
-    float* bufB = bufA + P.buf_floats;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kBottomThreads / 32;
 
-    const WorkItem item = P.items ? P.items[blockIdx.x] : WorkItem{0, (int)blockIdx.x};
+    const WorkItem item = P.items ? P.items[blockIdx.x] : WorkItem{0, (int)blockIdx.x, 0, 0, 0};
     const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
     const int p = tr.p;
 
@@ -324,24 +426,20 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
         if ((item.idx >> b) & 1) { start += nh; n -= nh; } else { n = nh; }
     }
 
-    // ---- load rows [start, start + n): bulk copy of the 16-byte-aligned interior,
-    //      plain loads for up to 3 floats at either end.
+    // ---- rows [start, start + n) -> buffer A (row 0 at float offset a0)
     const float* src = P.src + tr.src_off + (int64_t)start * p;
-    const int64_t total = (int64_t)n * p;
-    const int h = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);  // row 0 at bufA + h
-    float* in = bufA + h;
-    const int lead = h ? 4 - h : 0;                // floats before the aligned interior
-    const int64_t body = total > lead ? ((total - lead) & ~(int64_t)3) : 0;
+    const int total = n * p;
+    const int bufA = 4, bufB = 4 + P.buf_floats;
+    const int a0 = bufA + (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
     if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
-    if (body > 0 && tid == 0) {
-        mbar_expect_tx(bar, (unsigned)(body * 4));
-        bulk_g2s(in + lead, src + lead, (unsigned)(body * 4), bar);
+    const unsigned bytes = bulk_bytes(src, total);
+    if (tid == 0 && bytes) {
+        mbar_expect_tx(bar, bytes);  // the single arrival of this barrier phase
+        issue_rows_copy(smem, a0, src, total, bar);
     }
-    for (int64_t e = tid; e < total; e += kBottomThreads) {
-        if (e < lead || e >= lead + body) in[e] = src[e];
-    }
-    const bool landed = body == 0 || mbar_wait_bounded(bar, 0);
+    load_row_ends(smem, a0, src, total, tid, kBottomThreads);
+    const bool landed = bytes == 0 || mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
             atomicOr(P.status, kDevTimeout);
@@ -350,10 +448,10 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
         return;
     }
 
-    // ---- merge levels 1..H of the sub-tree, breadth-first by node height.  At level
-    //      `lev` every row belongs to one node of height <= lev whose parent is higher:
-    //      nodes of height lev merge (Eq. ffa_merge_rule), lower ones are carried.
-    float* out = bufB;
+    // ---- merge levels 1..H.  At level `lev` every row belongs to one node of height
+    //      <= lev whose parent is higher: nodes of height lev merge, lower ones are
+    //      carried over unchanged.
+    int in = a0, out = bufB;
     const int H = tree_height(n);
     for (int lev = 1; lev <= H; ++lev) {
         for (int r = warp; r < n; r += nwarps) {
@@ -362,37 +460,30 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
                 const int nh = sz >> 1;
                 if (r - st >= nh) { st += nh; sz -= nh; } else { sz = nh; }
             }
-            float* o = out + (int64_t)r * p;
             if (tree_height(sz) == lev) {
                 const Split sp = merge_split(sz, r - st);
-                const float* ra = in + (int64_t)(st + sp.i) * p;
-                const float* rb = in + (int64_t)(st + (sz >> 1) + sp.j) * p;
-                const int k = sp.shift % p;
-                for (int x = lane; x < p; x += 32) {
-                    int y = x + k;
-                    if (y >= p) y -= p;
-                    o[x] = __fadd_rn(ra[x], rb[y]);
-                }
+                merge_row(smem, out + r * p, in + (st + sp.i) * p, in + (st + (sz >> 1) + sp.j) * p,
+                          sp.shift % p, p, lane);
             } else {
-                const float* ra = in + (int64_t)r * p;
-                for (int x = lane; x < p; x += 32) o[x] = ra[x];
+                copy_row(smem, out + r * p, in + r * p, p, lane);
             }
         }
         __syncthreads();
-        float* t = in;
+        const int t = in;
         in = out;
-        out = (t == bufA + h) ? bufA : t;
+        out = (t == a0) ? bufA : t;
     }
 
     if constexpr (!kSnr) {
-        float* dst = ((tr.depth & 1) ? P.dst_odd : P.dst) + tr.scratch_off + (int64_t)start * p;
-        for (int64_t e = tid; e < total; e += kBottomThreads) dst[e] = in[e];
+        float* dst = ((top_passes(tr.depth, tr.chunk) & 1) ? P.dst_odd : P.dst) + tr.scratch_off +
+                     (int64_t)start * p;
+        for (int e = tid; e < total; e += kBottomThreads) dst[e] = smem[in + e];
     } else {
         // The sub-tree is the whole transform: score rows s < kept (Sec. 2.3).
-        float* S = out + warp * (p + P.widths.wmax + 1);
+        float* S = smem + out + warp * (p + P.widths.wmax + 1);
         for (int s = warp; warp < P.snr_warps && s < tr.kept; s += P.snr_warps) {
             const int64_t t = tr.trial0 + s;
-            warp_snr(in + (int64_t)s * p, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw,
+            warp_snr(smem + in + s * p, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw,
                      lane);
             if (lane == 0) {
                 P.periods[t] = trial_period(tr.tau, p, tr.m, s);
@@ -405,68 +496,178 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
 }
 
 // ---------------------------------------------------------------------------------
-// One merge level of the top of the tree: rows of the depth-d nodes from the complete
-// transforms of their depth-(d+1) children, through L2.
+// Top of the tree: up to three merge levels per pass, gathered.  A CTA computes rows
+// [lo, hi] of one node at depth d_out from the complete transforms of its descendants
+// at depth d_in = d_out + L.  Because the merge indices i(s), j(s) grow with s, the rows
+// needed from each descendant form one interval; only those are loaded (one bulk copy
+// per interval) and merged in shared memory.  The last pass of a periodogram scores
+// its rows with the boxcar filters instead of storing them.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kLevelThreads) ffa_level_kernel(LevelParams P) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const WorkItem item = P.items ? P.items[blockIdx.x] : WorkItem{0, (int)blockIdx.x};
-    const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
-    const int p = tr.p, m = tr.m;
-    const float* in = P.in + tr.scratch_off;
-    float* out = P.out + tr.scratch_off;
-    const int r1 = min(m, (item.idx + 1) * kLevelRows);
-    for (int r = item.idx * kLevelRows + warp; r < r1; r += kLevelThreads / 32) {
-        int st = 0, sz = m;
-        for (int b = 0; b < P.depth; ++b) {
-            const int nh = sz >> 1;
-            if (r - st >= nh) { st += nh; sz -= nh; } else { sz = nh; }
-        }
-        const Split sp = merge_split(sz, r - st);
-        const float* ra = in + (int64_t)(st + sp.i) * p;
-        const float* rb = in + (int64_t)(st + (sz >> 1) + sp.j) * p;
-        const int k = sp.shift % p;
-        float* o = out + (int64_t)r * p;
-        for (int x = lane; x < p; x += 32) {
-            int y = x + k;
-            if (y >= p) y -= p;
-            o[x] = __fadd_rn(ra[x], rb[y]);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------
-// Root merge level fused with the boxcar S/N: each warp builds F_s in shared memory
-// from the two depth-1 transforms and scores it.
-// ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kFinalThreads) ffa_final_snr_kernel(FinalParams P) {
+__global__ void __launch_bounds__(kTopThreads) ffa_top_kernel(TopParams P) {
     extern __shared__ __align__(16) float smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const WorkItem item = P.items ? P.items[blockIdx.x] : WorkItem{0, (int)blockIdx.x};
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = kTopThreads / 32;
+
+    const WorkItem item = P.items ? P.items[blockIdx.x]
+                                  : WorkItem{0, (int)blockIdx.x, (int16_t)P.single_pass,
+                                             (int16_t)P.single_rows, 0};
     const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
     const int p = tr.p, m = tr.m;
-    const float* in = P.in + tr.scratch_off;
-    float* prof = smem + warp * P.warp_floats;
-    float* S = prof + p;
-    const int s1 = min(tr.kept, (item.idx + 1) * kFinalRows);
-    for (int s = item.idx * kFinalRows + warp; s < s1; s += kFinalThreads / 32) {
-        const Split sp = merge_split(m, s);
-        const float* ra = in + (int64_t)sp.i * p;
-        const float* rb = in + (int64_t)((m >> 1) + sp.j) * p;
-        const int k = sp.shift % p;
-        for (int x = lane; x < p; x += 32) {
-            int y = x + k;
-            if (y >= p) y -= p;
-            prof[x] = __fadd_rn(ra[x], rb[y]);
+    const int npass = top_passes(tr.depth, tr.chunk);
+    const int pass = item.pass;
+    const int d_in = top_pass_in_depth(tr.depth, tr.chunk, pass);
+    const int d_out = top_pass_out_depth(tr.depth, tr.chunk, pass);
+    const int L = d_in - d_out;
+    const int K = item.rows;
+    const bool last = pass == npass - 1;
+    const bool score = last && P.snr != nullptr;
+    const float* in = ((npass - pass) & 1 ? P.buf1 : P.buf0) + tr.scratch_off;
+    float* out = ((npass - pass - 1) & 1 ? P.buf1 : P.buf0) + tr.scratch_off;
+    const TopLayout lay = top_layout(K, L, p, P.widths.wmax, score);
+
+    // target node (depth d_out) and its row block
+    const int nmax = (m + (1 << d_out) - 1) >> d_out;
+    const int limit_rows = score ? tr.kept : nmax;
+    const int nb = (limit_rows + K - 1) / K;
+    const int node = item.idx / nb, blk = item.idx - node * nb;
+    int st0 = 0, n0 = m;
+    for (int b = d_out - 1; b >= 0; --b) {
+        const int nh = n0 >> 1;
+        if ((node >> b) & 1) { st0 += nh; n0 -= nh; } else { n0 = nh; }
+    }
+    const int lo0 = blk * K;
+    const int hi0 = min(lo0 + K, score ? tr.kept : n0) - 1;
+    if (lo0 > hi0) return;  // uniform: block past the end of a smaller node
+
+    // ---- interval table, heap order: node e at level l is e = 2^l - 1 + j.
+    //      per node: [0] abs start row, [1] size, [2] lo, [3] hi, [4] smem offset of row lo
+    int* tab = reinterpret_cast<int*>(smem + lay.table);
+    int* lvl_desc = tab + 120;  // first descriptor of each level, levels L-1..0, + end
+    if (tid == 0) {
+        tab[0] = st0; tab[1] = n0; tab[2] = lo0; tab[3] = hi0;
+        for (int l = 0; l < L; ++l) {
+            for (int j = 0; j < (1 << l); ++j) {
+                const int e = (1 << l) - 1 + j;
+                const int st = tab[8 * e], n = tab[8 * e + 1], lo = tab[8 * e + 2], hi = tab[8 * e + 3];
+                const int nh = n >> 1;
+                const Split a = merge_split(n, lo), z = merge_split(n, hi);
+                const int eh = 2 * e + 1, et = 2 * e + 2;
+                tab[8 * eh] = st; tab[8 * eh + 1] = nh; tab[8 * eh + 2] = a.i; tab[8 * eh + 3] = z.i;
+                tab[8 * et] = st + nh; tab[8 * et + 1] = n - nh; tab[8 * et + 2] = a.j;
+                tab[8 * et + 3] = z.j;
+            }
         }
-        __syncwarp();
-        const int64_t t = tr.trial0 + s;
-        warp_snr(prof, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw, lane);
-        if (lane == 0) {
-            P.periods[t] = trial_period(tr.tau, p, m, s);
-            P.foldbins[t] = p;
+        // offsets: level L with alignment slack (buffer A), the others compact
+        int off = lay.buf_a;
+        for (int j = 0; j < (1 << L); ++j) {
+            const int e = (1 << L) - 1 + j;
+            const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
+            const int h = (int)((reinterpret_cast<uintptr_t>(g) >> 2) & 3);
+            tab[8 * e + 4] = off + h;
+            off = round4(off + h + (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p);
+        }
+        int nd = 0;
+        for (int l = L - 1; l >= 0; --l) {
+            int o = (((L - l) & 1) == 0) ? lay.buf_a : lay.buf_b;
+            lvl_desc[L - 1 - l] = nd;
+            for (int j = 0; j < (1 << l); ++j) {
+                const int e = (1 << l) - 1 + j;
+                tab[8 * e + 4] = o;
+                const int rows = tab[8 * e + 3] - tab[8 * e + 2] + 1;
+                o += rows * p;
+                nd += rows;
+            }
+        }
+        lvl_desc[L] = nd;
+        mbar_init(bar, 1);
+    }
+    __syncthreads();
+
+    // ---- row descriptors {out, head row, tail row, shift} for levels L-1 .. 0
+    int4* desc = reinterpret_cast<int4*>(smem + lay.desc);
+    const int ndesc = lvl_desc[L];
+    for (int q = tid; q < ndesc; q += kTopThreads) {
+        int l = L - 1;
+        while (q >= lvl_desc[L - l]) --l;  // level of descriptor q
+        int r = q - lvl_desc[L - 1 - l];
+        int e = (1 << l) - 1;
+        while (r > tab[8 * e + 3] - tab[8 * e + 2]) {
+            r -= tab[8 * e + 3] - tab[8 * e + 2] + 1;
+            ++e;
+        }
+        const int s = tab[8 * e + 2] + r;
+        const Split sp = merge_split(tab[8 * e + 1], s);
+        const int eh = 2 * e + 1, et = 2 * e + 2;
+        int4 d;
+        d.x = tab[8 * e + 4] + r * p;
+        d.y = tab[8 * eh + 4] + (sp.i - tab[8 * eh + 2]) * p;
+        d.z = tab[8 * et + 4] + (sp.j - tab[8 * et + 2]) * p;
+        d.w = sp.shift % p;
+        desc[q] = d;
+    }
+
+    // ---- gather the needed rows of the depth-d_in transforms: one bulk copy per interval,
+    //      all counted by a single arrival on the barrier
+    unsigned bytes = 0;
+    for (int j = 0; j < (1 << L); ++j) {
+        const int e = (1 << L) - 1 + j;
+        const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
+        bytes += bulk_bytes(g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p);
+    }
+    if (tid == 0 && bytes) {
+        mbar_expect_tx(bar, bytes);
+        for (int j = 0; j < (1 << L); ++j) {
+            const int e = (1 << L) - 1 + j;
+            const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
+            issue_rows_copy(smem, tab[8 * e + 4], g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p, bar);
         }
     }
+    for (int j = 0; j < (1 << L); ++j) {
+        const int e = (1 << L) - 1 + j;
+        const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
+        load_row_ends(smem, tab[8 * e + 4], g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p, tid,
+                      kTopThreads);
+    }
+    const bool landed = bytes == 0 || mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(!landed)) {
+        if (tid == 0) {
+            atomicOr(P.status, kDevTimeout);
+            mbar_wait_bounded(bar, 0);
+        }
+        return;
+    }
+
+    // ---- merge levels L-1 .. 0
+    for (int l = L - 1; l >= 0; --l) {
+        const int q1 = lvl_desc[L - l];
+        for (int q = lvl_desc[L - 1 - l] + warp; q < q1; q += nwarps) {
+            const int4 d = desc[q];
+            merge_row(smem, d.x, d.y, d.z, d.w, p, lane);
+        }
+        __syncthreads();
+    }
+
+    // ---- level 0: score (last pass of a periodogram) or store
+    const int o0 = tab[4];
+    const int rows0 = hi0 - lo0 + 1;
+    if (score) {
+        float* S = smem + lay.sbuf + warp * lay.sbuf_warp;
+        for (int r = warp; r < rows0; r += nwarps) {
+            const int s = lo0 + r;
+            const int64_t t = tr.trial0 + s;
+            warp_snr(smem + o0 + r * p, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw, lane);
+            if (lane == 0) {
+                P.periods[t] = trial_period(tr.tau, p, m, s);
+                P.foldbins[t] = p;
+            }
+        }
+    } else {
+        float* dst = out + (int64_t)(st0 + lo0) * p;
+        for (int e = tid; e < rows0 * p; e += kTopThreads) dst[e] = smem[o0 + e];
+    }
+    __syncthreads();
+    if (tid == 0) mbar_inval(bar);
 }
 
 // Standalone boxcar S/N of stored profiles: one warp per row.
@@ -538,16 +739,10 @@ cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bo
     return cudaGetLastError();
 }
 
-cudaError_t launch_level(const LevelParams& P, int nblocks, cudaStream_t s) {
+cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s) {
     if (nblocks <= 0) return cudaSuccess;
-    ffa_level_kernel<<<nblocks, kLevelThreads, 0, s>>>(P);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_final(const FinalParams& P, int nblocks, int smem_bytes, cudaStream_t s) {
-    if (nblocks <= 0) return cudaSuccess;
-    allow_max_smem((const void*)ffa_final_snr_kernel, 2);
-    ffa_final_snr_kernel<<<nblocks, kFinalThreads, smem_bytes, s>>>(P);
+    allow_max_smem((const void*)ffa_top_kernel, 2);
+    ffa_top_kernel<<<nblocks, kTopThreads, smem_bytes, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -37,7 +37,7 @@ TRANSFORM_SHAPES = [
     (1, 1), (1, 7), (2, 1), (2, 5), (3, 2), (5, 3), (7, 31), (8, 33), (13, 240), (64, 260),
     (100, 250), (111, 260), (112, 260), (127, 240), (128, 260), (129, 33), (257, 257),
     (1000, 240), (2684, 240), (5368, 250), (300, 1024), (17, 4096), (40000, 3), (2, 4096),
-    (9683, 3), (4097, 7),
+    (9683, 3), (4097, 7), (50, 4096), (100, 2048), (223, 260), (3000, 31), (1342, 520),
 ]
 
 
