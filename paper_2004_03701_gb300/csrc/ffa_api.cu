@@ -106,7 +106,7 @@ struct Stage {              // one top-kernel launch: pass j of every transform 
 };
 struct Group {
     int64_t bottom_off = 0, bottom_cnt = 0;
-    int bottom_smem = 0, bottom_buf = 0;
+    int bottom_smem = 0, bottom_nmax = 0, bottom_elems = 0;
     double bottom_bytes = 0;
     std::vector<Stage> stages;
 };
@@ -123,7 +123,9 @@ struct Plan {
     std::vector<TransformDesc> trs;
     std::vector<WorkItem> items;
     int64_t bottom0_off = 0, bottom0_cnt = 0;
-    int bottom0_smem = 0, bottom0_buf = 0, bottom0_snr_warps = 0;
+    int bottom0_smem = 0, bottom0_nmax = 0, bottom0_elems = 0, bottom0_snr_warps = 0;
+    int bottom0_snr_floats = 0;
+    int row_cap = kBottomMaxRows;  // sub-tree row limit (lowered if a launch's mix overflows)
     double bottom0_bytes = 0;
     std::vector<Group> groups;
     int64_t ntrials = 0, ds_total = 0, ds_floats = 0, scratch_floats = 0, folded = 0;
@@ -140,22 +142,19 @@ struct Plan {
 };
 
 constexpr size_t kStatusBytes = 256;
+constexpr ffa_status kRetrySmaller = -1;  // internal: a launch's sub-tree mix overflows
 std::mutex g_plan_mu;
-constexpr int64_t kGroupFloats = int64_t(16) << 20;  // 64 MB per scratch buffer
+constexpr int64_t kGroupFloats = int64_t(6) << 20;  // 24 MB per scratch buffer (L2-resident)
 
-// Rows of one shared-memory sub-tree: two buffers of round4(n * p + 4) floats after a
-// 16-byte barrier slot, within kSmemBytes.
-int max_subtree_rows(int p) {
-    const int cap = ((kSmemBytes - 16) / 8) & ~3;
-    return std::max(1, (cap - 4) / p);
+// Rows of one shared-memory sub-tree of p bins: the most (at most row_cap) whose
+// layout fits in shared memory.
+int max_subtree_rows(int p, int row_cap) {
+    int n = std::min(row_cap, kBottomMaxRows);
+    while (n > 1 && bottom_layout(n, n * p, 0).total * 4 > kSmemBytes) --n;
+    return std::max(n, 1);
 }
-int bottom_buf_floats(int64_t elems, int snr_need) {
-    int need = (int)elems + 4;
-    if (snr_need > need) need = snr_need;
-    return (int)align_up((size_t)need, 4);
-}
-int depth_for(int m, int p) {
-    const int R = max_subtree_rows(p);
+int depth_for(int m, int p, int row_cap = kBottomMaxRows) {
+    const int R = max_subtree_rows(p, row_cap);
     int d = 0;
     while (((int64_t)m + (int64_t(1) << d) - 1) >> d > R) ++d;
     return d;
@@ -256,7 +255,7 @@ ffa_status build_plan(Plan& pl) {
             t.p = p;
             t.m = m;
             t.kept = (int)kept;
-            t.depth = depth_for(m, p);
+            t.depth = depth_for(m, p, pl.row_cap);
             t.chunk = top_chunk(p, pl.W.wmax, true);
             if (t.chunk < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
             t.inv_std = (float)(1.0 / std::sqrt((double)m * var));
@@ -274,28 +273,26 @@ ffa_status build_plan(Plan& pl) {
 
     // Whole-tree-in-shared-memory transforms: one launch, fused S/N.
     pl.bottom0_off = (int64_t)pl.items.size();
-    int64_t elems0 = 0;
     int p0 = 0;
     for (size_t t = 0; t < pl.trs.size(); ++t) {
         const TransformDesc& d = pl.trs[t];
         if (d.depth != 0) continue;
-        pl.items.push_back(WorkItem{(int32_t)t, 0});
-        elems0 = std::max<int64_t>(elems0, (int64_t)d.m * d.p);
+        pl.items.push_back(WorkItem{(int32_t)t, 0, 0, 0, 0});
+        pl.bottom0_nmax = std::max(pl.bottom0_nmax, d.m);
+        pl.bottom0_elems = std::max(pl.bottom0_elems, d.m * d.p);
         p0 = std::max(p0, d.p);
         pl.bottom0_bytes += 4.0 * d.m * d.p + out_row_bytes * d.kept;
     }
     pl.bottom0_cnt = (int64_t)pl.items.size() - pl.bottom0_off;
     if (pl.bottom0_cnt) {
-        const int per_warp = p0 + wmax + 1;
-        int buf = bottom_buf_floats(elems0, 0);
-        pl.bottom0_snr_warps = std::min(kBottomThreads / 32, buf / per_warp);
-        if (pl.bottom0_snr_warps < 1) {
-            buf = bottom_buf_floats(elems0, per_warp);
-            pl.bottom0_snr_warps = 1;
-        }
-        pl.bottom0_buf = buf;
-        pl.bottom0_smem = 16 + 8 * buf;
-        if (pl.bottom0_smem > kSmemBytes) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+        const int per_warp = snr_warp_floats(p0, wmax);
+        const BottomLayout l0 = bottom_layout(pl.bottom0_nmax, pl.bottom0_elems, 0);
+        pl.bottom0_snr_warps = std::min(kBottomThreads / 32, l0.buf_floats / per_warp);
+        if (pl.bottom0_snr_warps < 1) pl.bottom0_snr_warps = 1;
+        pl.bottom0_snr_floats = pl.bottom0_snr_warps * per_warp;
+        pl.bottom0_smem =
+            bottom_layout(pl.bottom0_nmax, pl.bottom0_elems, pl.bottom0_snr_floats).total * 4;
+        if (pl.bottom0_smem > kSmemBytes) return kRetrySmaller;
     }
 
     // Deeper transforms: groups of consecutive transforms sharing the scratch buffers.
@@ -307,19 +304,18 @@ ffa_status build_plan(Plan& pl) {
         if (!open) return;
         Group g;
         g.bottom_off = (int64_t)pl.items.size();
-        int64_t elems = 0;
         int maxpass = 0;
         for (int t : members) {
             const TransformDesc& d = pl.trs[t];
             for (int c = 0; c < (1 << d.depth); ++c) pl.items.push_back(WorkItem{t, c, 0, 0, 0});
-            const int64_t rows = (d.m + (1 << d.depth) - 1) >> d.depth;
-            elems = std::max<int64_t>(elems, rows * d.p);
+            const int rows = (d.m + (1 << d.depth) - 1) >> d.depth;
+            g.bottom_nmax = std::max(g.bottom_nmax, rows);
+            g.bottom_elems = std::max(g.bottom_elems, rows * d.p);
             maxpass = std::max(maxpass, top_passes(d.depth, d.chunk));
             g.bottom_bytes += 8.0 * d.m * d.p;
         }
         g.bottom_cnt = (int64_t)pl.items.size() - g.bottom_off;
-        g.bottom_buf = bottom_buf_floats(elems, 0);
-        g.bottom_smem = 16 + 8 * g.bottom_buf;
+        g.bottom_smem = bottom_layout(g.bottom_nmax, g.bottom_elems, 0).total * 4;
         for (int j = 0; j < maxpass; ++j) {
             Stage s;
             s.off = (int64_t)pl.items.size();
@@ -363,7 +359,7 @@ ffa_status build_plan(Plan& pl) {
     close_group();
     if (kerr != FFA_OK) return kerr;
     for (const Group& g : pl.groups)
-        if (g.bottom_smem > kSmemBytes) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+        if (g.bottom_smem > kSmemBytes) return kRetrySmaller;
 
     // Tables: octaves | transforms | items, each 256-byte aligned.
     size_t o = 0;
@@ -447,7 +443,18 @@ ffa_status get_plan(int64_t n, double tsamp, double pmin, double pmax, int bmin,
     pl->bmax = bmax;
     pl->widths.assign(h_widths, h_widths + nw);
     pl->W = W;
-    st = build_plan(*pl);
+    for (int cap = kBottomMaxRows;;) {
+        st = build_plan(*pl);
+        if (st != kRetrySmaller) break;
+        // sub-trees of different widths share one launch: lower the row limit and replan
+        cap = std::min(cap, pl->row_cap) - 1;
+        if (cap < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+        auto fresh = std::make_unique<Plan>();
+        fresh->n = n; fresh->tsamp = tsamp; fresh->pmin = pmin; fresh->pmax = pmax;
+        fresh->bmin = bmin; fresh->bmax = bmax; fresh->widths = pl->widths; fresh->W = W;
+        fresh->row_cap = cap;
+        pl = std::move(fresh);
+    }
     if (st != FFA_OK) return st;
     if (g_plans.size() > 64) g_plans.clear();
     *out = pl.get();
@@ -497,8 +504,10 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     bp.status = status;
     if (pl.bottom0_cnt) {
         bp.items = d_items + pl.bottom0_off;
-        bp.buf_floats = pl.bottom0_buf;
+        bp.nmax = pl.bottom0_nmax;
+        bp.elems_max = pl.bottom0_elems;
         bp.snr_warps = pl.bottom0_snr_warps;
+        bp.snr_floats = pl.bottom0_snr_floats;
         LaunchScope ls(kFfaBottomSnr, pl.bottom0_bytes, st);
         FFA_CUDA(launch_bottom(bp, (int)pl.bottom0_cnt, pl.bottom0_smem, true, st),
                  "ffa_bottom_snr launch");
@@ -507,8 +516,10 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
         bp.items = d_items + g.bottom_off;
         bp.dst = s0;      // sub-trees of a transform with P top passes land in buffer P % 2
         bp.dst_odd = s1;
-        bp.buf_floats = g.bottom_buf;
+        bp.nmax = g.bottom_nmax;
+        bp.elems_max = g.bottom_elems;
         bp.snr_warps = 0;
+        bp.snr_floats = 0;
         {
             LaunchScope ls(kFfaBottom, g.bottom_bytes, st);
             FFA_CUDA(launch_bottom(bp, (int)g.bottom_cnt, g.bottom_smem, false, st),
@@ -686,8 +697,9 @@ ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d
     bp.single = t;
     bp.status = status;
     const int rows_d = (rows + (1 << D) - 1) >> D;
-    bp.buf_floats = bottom_buf_floats((int64_t)rows_d * cols, 0);
-    const int smem = 16 + 8 * bp.buf_floats;
+    bp.nmax = rows_d;
+    bp.elems_max = rows_d * cols;
+    const int smem = bottom_layout(bp.nmax, bp.elems_max, 0).total * 4;
     {
         LaunchScope ls(kFfaBottom, 8.0 * rows * cols, st);
         FFA_CUDA(launch_bottom(bp, 1 << D, smem, false, st), "ffa_bottom launch");

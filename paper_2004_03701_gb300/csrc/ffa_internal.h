@@ -73,6 +73,34 @@ struct TopLayout {
     int total;      // floats
 };
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
+
+// Prefix-sum row of the boxcar S/N of a p-bin profile: S[0 .. 32 ceil(p/32) + wmax].
+__host__ __device__ inline int snr_warp_floats(int p, int wmax) {
+    return round4(((p + 31) & ~31) + wmax + 1);
+}
+
+// Shared-memory layout (in floats) of a sub-tree CTA: barrier, two row-descriptor
+// buffers of nmax int2 (merge level l uses one while level l+1's are computed into the
+// other), and two ping-pong row buffers of buf_floats.
+constexpr int kBottomMaxRows = 1024;
+struct BottomLayout {
+    int desc;
+    int buf_a;
+    int buf_b;
+    int buf_floats;
+    int total;
+};
+__host__ __device__ inline BottomLayout bottom_layout(int nmax, int elems_max, int snr_need) {
+    BottomLayout b;
+    b.desc = 4;
+    b.buf_a = round4(b.desc + 4 * nmax);
+    int need = elems_max + 4;
+    if (snr_need > need) need = snr_need;
+    b.buf_floats = round4(need);
+    b.buf_b = b.buf_a + b.buf_floats;
+    b.total = b.buf_b + b.buf_floats;
+    return b;
+}
 __host__ __device__ inline TopLayout top_layout(int K, int L, int p, int wmax, bool snr) {
     TopLayout t;
     int off = 4;  // mbarrier
@@ -92,7 +120,7 @@ __host__ __device__ inline TopLayout top_layout(int K, int L, int p, int wmax, b
     t.buf_b = off;
     off += round4(cap_b);
     t.sbuf = off;
-    t.sbuf_warp = snr ? round4(p + wmax + 1) : 0;
+    t.sbuf_warp = snr ? snr_warp_floats(p, wmax) : 0;
     off += (kTopThreads / 32) * t.sbuf_warp;
     t.total = off;
     return t;
@@ -164,8 +192,10 @@ struct BottomParams {
     int32_t* foldbins;
     float* snr;
     unsigned* status;
-    int buf_floats;                 // floats per shared-memory buffer
+    int nmax;                       // largest sub-tree (rows) of the launch
+    int elems_max;                  // largest sub-tree (floats) of the launch
     int snr_warps;                  // warps that score rows (fused S/N mode)
+    int snr_floats;                 // shared floats those warps need (0 otherwise)
 };
 
 struct TopParams {

@@ -261,22 +261,72 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 }
 
 // ---------------------------------------------------------------------------------
-// Boxcar S/N of one profile by one warp (Sec. 5.4).  S = exclusive prefix sum over
-// two concatenated repeats (length p + wmax + 1, in shared memory), then for each
-// width w the largest S[k + w] - S[k], scaled by 1 / (stdnoise sqrt(w)).
-// T = ceil(p / 32): each lane keeps S[lane + 32 t] in registers.
+// Boxcar S/N of one profile by one warp (Sec. 5.4): S = exclusive prefix sum of the
+// profile over two concatenated repeats, then for each width w the largest
+// C_k = S[k + w] - S[k] over phases k, scaled by 1 / (stdnoise sqrt(w)).
+//
+// Register form (p <= 32 * 17): lane holds v[t] = F[lane + 32 t].  The prefix sums are
+// a warp scan per slot with a running carry; S lives in shared memory (the wmax
+// entries past p are S[p] + S[j]); lanes keep S[k] for their own phases in registers
+// (+inf for k >= p, so that padding phases never win) and read S[k + w] once per width.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ void warp_prefix(const float* prof, int p, int L, float* S, int lane) {
+constexpr int kSnrMaxSlots = 17;
+
+template <int T>
+__device__ __forceinline__ void snr_from_regs(const float (&v)[T], int p, float* S,
+                                              const Widths& W, float inv_std, float* out,
+                                              int lane) {
+    float carry = 0.f;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        float inc = v[t];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float u = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += u;
+        }
+        const int x = lane + 32 * t;
+        if (x < p) S[x + 1] = carry + inc;
+        carry += __shfl_sync(kFull, inc, 31);
+    }
+    if (lane == 0) S[0] = 0.f;
+    __syncwarp();
+    const float total = S[p];
+    const int jmax = 32 * T - 1 + W.wmax - p;  // S is read up to index 32 T - 1 + wmax
+    for (int j = lane + 1; j <= jmax; j += 32)
+        S[p + j] = j <= p ? total + S[j] : 0.f;  // second repeat; finite padding beyond
+    __syncwarp();
+    float sk[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int x = lane + 32 * t;
+        sk[t] = x < p ? S[x] : INFINITY;
+    }
+    for (int iw = 0; iw < W.nw; ++iw) {
+        const float* Sw = S + W.w[iw] + lane;
+        float best = -INFINITY;
+#pragma unroll
+        for (int t = 0; t < T; ++t) best = fmaxf(best, Sw[32 * t] - sk[t]);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
+        if (lane == 0) out[iw] = best * inv_std * W.inv_sqrt_w[iw];
+    }
+    __syncwarp();
+}
+
+// Profiles of more than 32 * kSnrMaxSlots bins: sequential per-lane chunks.
+__device__ __noinline__ void snr_row_any(const float* prof, int p, float* S, const Widths& W,
+                                         float inv_std, float* out, int lane) {
+    const int L = p + W.wmax;
     const int c = (L + 31) >> 5;
     const int i0 = lane * c;
     const int i1 = min(i0 + c, L);
     float acc = 0.f;
     for (int i = i0; i < i1; ++i) acc += prof[i < p ? i : i - p];
     float inc = acc;
-#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        float v = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += v;
+        float u = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += u;
     }
     float run = __shfl_up_sync(kFull, inc, 1);
     if (lane == 0) {
@@ -288,36 +338,6 @@ __device__ __forceinline__ void warp_prefix(const float* prof, int p, int L, flo
         S[i + 1] = run;
     }
     __syncwarp();
-}
-
-template <int T>
-__device__ __forceinline__ void warp_snr_t(const float* prof, int p, float* S, const Widths& W,
-                                           float inv_std, float* out, int lane) {
-    warp_prefix(prof, p, p + W.wmax, S, lane);
-    float sk[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int k = lane + 32 * t;
-        sk[t] = k < p ? S[k] : 0.f;
-    }
-    for (int iw = 0; iw < W.nw; ++iw) {
-        const float* Sw = S + W.w[iw];
-        float best = -INFINITY;
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            const int k = lane + 32 * t;
-            if (k < p) best = fmaxf(best, Sw[k] - sk[t]);
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
-        if (lane == 0) out[iw] = best * inv_std * W.inv_sqrt_w[iw];
-    }
-    __syncwarp();
-}
-
-__device__ __noinline__ void warp_snr_any(const float* prof, int p, float* S, const Widths& W,
-                                          float inv_std, float* out, int lane) {
-    warp_prefix(prof, p, p + W.wmax, S, lane);
     for (int iw = 0; iw < W.nw; ++iw) {
         const int w = W.w[iw];
         float best = -INFINITY;
@@ -328,27 +348,57 @@ __device__ __noinline__ void warp_snr_any(const float* prof, int p, float* S, co
     __syncwarp();
 }
 
-__device__ __forceinline__ void warp_snr(const float* prof, int p, float* S, const Widths& W,
-                                         float inv_std, float* out, int lane) {
+// Scores a stored row (shared or global memory).
+template <int T>
+__device__ __forceinline__ void snr_row_t(const float* prof, int p, float* S, const Widths& W,
+                                          float inv_std, float* out, int lane) {
+    float v[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int x = lane + 32 * t;
+        v[t] = x < p ? prof[x] : 0.f;
+    }
+    snr_from_regs<T>(v, p, S, W, inv_std, out, lane);
+}
+
+// Merges F_s = H + (T << k) straight into registers and scores it (row never stored).
+template <int T>
+__device__ __forceinline__ void snr_merge_t(const float* sm, int a, int b, int k, int p, float* S,
+                                            const Widths& W, float inv_std, float* out, int lane) {
+    float v[T];
+    int y = lane + k;
+    if (y >= p) y -= p;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int x = lane + 32 * t;
+        v[t] = x < p ? __fadd_rn(sm[a + x], sm[b + y]) : 0.f;
+        y += 32;
+        if (y >= p) y -= p;
+    }
+    snr_from_regs<T>(v, p, S, W, inv_std, out, lane);
+}
+
+#define FFA_SNR_SLOTS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) \
+    X(13) X(14) X(15) X(16) X(17)
+
+__device__ __forceinline__ void snr_row(const float* prof, int p, float* S, const Widths& W,
+                                        float inv_std, float* out, int lane) {
     switch ((p + 31) >> 5) {
-        case 1: warp_snr_t<1>(prof, p, S, W, inv_std, out, lane); break;
-        case 2: warp_snr_t<2>(prof, p, S, W, inv_std, out, lane); break;
-        case 3: warp_snr_t<3>(prof, p, S, W, inv_std, out, lane); break;
-        case 4: warp_snr_t<4>(prof, p, S, W, inv_std, out, lane); break;
-        case 5: warp_snr_t<5>(prof, p, S, W, inv_std, out, lane); break;
-        case 6: warp_snr_t<6>(prof, p, S, W, inv_std, out, lane); break;
-        case 7: warp_snr_t<7>(prof, p, S, W, inv_std, out, lane); break;
-        case 8: warp_snr_t<8>(prof, p, S, W, inv_std, out, lane); break;
-        case 9: warp_snr_t<9>(prof, p, S, W, inv_std, out, lane); break;
-        case 10: warp_snr_t<10>(prof, p, S, W, inv_std, out, lane); break;
-        case 11: warp_snr_t<11>(prof, p, S, W, inv_std, out, lane); break;
-        case 12: warp_snr_t<12>(prof, p, S, W, inv_std, out, lane); break;
-        case 13: warp_snr_t<13>(prof, p, S, W, inv_std, out, lane); break;
-        case 14: warp_snr_t<14>(prof, p, S, W, inv_std, out, lane); break;
-        case 15: warp_snr_t<15>(prof, p, S, W, inv_std, out, lane); break;
-        case 16: warp_snr_t<16>(prof, p, S, W, inv_std, out, lane); break;
-        case 17: warp_snr_t<17>(prof, p, S, W, inv_std, out, lane); break;
-        default: warp_snr_any(prof, p, S, W, inv_std, out, lane); break;
+#define FFA_CASE(T) case T: snr_row_t<T>(prof, p, S, W, inv_std, out, lane); return;
+        FFA_SNR_SLOTS(FFA_CASE)
+#undef FFA_CASE
+        default: snr_row_any(prof, p, S, W, inv_std, out, lane); return;
+    }
+}
+
+// Returns false (nothing done) if p needs the generic path.
+__device__ __forceinline__ bool snr_merge(const float* sm, int a, int b, int k, int p, float* S,
+                                          const Widths& W, float inv_std, float* out, int lane) {
+    switch ((p + 31) >> 5) {
+#define FFA_CASE(T) case T: snr_merge_t<T>(sm, a, b, k, p, S, W, inv_std, out, lane); return true;
+        FFA_SNR_SLOTS(FFA_CASE)
+#undef FFA_CASE
+        default: return false;
     }
 }
 
@@ -408,12 +458,30 @@ __device__ __forceinline__ void load_row_ends(float* sm, int dst, const float* s
 // ---------------------------------------------------------------------------------
 // Shared-memory FFA of one sub-tree (all of its levels, breadth-first by height).
 // ---------------------------------------------------------------------------------
+
+// Descriptor of row r of an n-row sub-tree at merge level `lev`: the row belongs to one
+// node of height <= lev whose parent is higher; nodes of height lev merge (Eq.
+// ffa_merge_rule), lower ones are carried unchanged.  Packed: x = head row | tail row
+// << 16 (tail 0xffff = copy), y = shift.
+__device__ __forceinline__ int2 bottom_desc(int n, int lev, int r, int p) {
+    int st = 0, sz = n;
+    while (tree_height(sz) > lev) {
+        const int nh = sz >> 1;
+        if (r - st >= nh) { st += nh; sz -= nh; } else { sz = nh; }
+    }
+    if (tree_height(sz) != lev) return make_int2(r | (0xffff << 16), 0);
+    const Split sp = merge_split(sz, r - st);
+    return make_int2((st + sp.i) | ((st + (sz >> 1) + sp.j) << 16), sp.shift % p);
+}
+
 template <bool kSnr>
 __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams P) {
     extern __shared__ __align__(16) float smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kBottomThreads / 32;
+    const BottomLayout lay = bottom_layout(P.nmax, P.elems_max, P.snr_floats);
+    int2* desc = reinterpret_cast<int2*>(smem + lay.desc);  // 2 x nmax
 
     const WorkItem item = P.items ? P.items[blockIdx.x] : WorkItem{0, (int)blockIdx.x, 0, 0, 0};
     const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
@@ -429,8 +497,7 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
     // ---- rows [start, start + n) -> buffer A (row 0 at float offset a0)
     const float* src = P.src + tr.src_off + (int64_t)start * p;
     const int total = n * p;
-    const int bufA = 4, bufB = 4 + P.buf_floats;
-    const int a0 = bufA + (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+    const int a0 = lay.buf_a + (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
     if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
     const unsigned bytes = bulk_bytes(src, total);
@@ -439,6 +506,9 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
         issue_rows_copy(smem, a0, src, total, bar);
     }
     load_row_ends(smem, a0, src, total, tid, kBottomThreads);
+    const int H = tree_height(n);
+    if (H >= 1)
+        for (int r = tid; r < n; r += kBottomThreads) desc[r] = bottom_desc(n, 1, r, p);
     const bool landed = bytes == 0 || mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
@@ -448,30 +518,24 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
         return;
     }
 
-    // ---- merge levels 1..H.  At level `lev` every row belongs to one node of height
-    //      <= lev whose parent is higher: nodes of height lev merge, lower ones are
-    //      carried over unchanged.
-    int in = a0, out = bufB;
-    const int H = tree_height(n);
+    // ---- merge levels 1..H; level lev+1's descriptors are made while level lev merges
+    int in = a0, out = lay.buf_b;
     for (int lev = 1; lev <= H; ++lev) {
+        const int2* dc = desc + ((lev - 1) & 1) * P.nmax;
+        if (lev < H) {
+            int2* dn = desc + (lev & 1) * P.nmax;
+            for (int r = tid; r < n; r += kBottomThreads) dn[r] = bottom_desc(n, lev + 1, r, p);
+        }
         for (int r = warp; r < n; r += nwarps) {
-            int st = 0, sz = n;
-            while (tree_height(sz) > lev) {
-                const int nh = sz >> 1;
-                if (r - st >= nh) { st += nh; sz -= nh; } else { sz = nh; }
-            }
-            if (tree_height(sz) == lev) {
-                const Split sp = merge_split(sz, r - st);
-                merge_row(smem, out + r * p, in + (st + sp.i) * p, in + (st + (sz >> 1) + sp.j) * p,
-                          sp.shift % p, p, lane);
-            } else {
-                copy_row(smem, out + r * p, in + r * p, p, lane);
-            }
+            const int2 d = dc[r];
+            const int ha = d.x & 0xffff, tb = (d.x >> 16) & 0xffff;
+            if (tb != 0xffff) merge_row(smem, out + r * p, in + ha * p, in + tb * p, d.y, p, lane);
+            else copy_row(smem, out + r * p, in + r * p, p, lane);
         }
         __syncthreads();
         const int t = in;
         in = out;
-        out = (t == a0) ? bufA : t;
+        out = (t == a0) ? lay.buf_a : t;
     }
 
     if constexpr (!kSnr) {
@@ -480,11 +544,10 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
         for (int e = tid; e < total; e += kBottomThreads) dst[e] = smem[in + e];
     } else {
         // The sub-tree is the whole transform: score rows s < kept (Sec. 2.3).
-        float* S = smem + out + warp * (p + P.widths.wmax + 1);
+        float* S = smem + out + warp * snr_warp_floats(p, P.widths.wmax);
         for (int s = warp; warp < P.snr_warps && s < tr.kept; s += P.snr_warps) {
             const int64_t t = tr.trial0 + s;
-            warp_snr(smem + in + s * p, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw,
-                     lane);
+            snr_row(smem + in + s * p, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw, lane);
             if (lane == 0) {
                 P.periods[t] = trial_period(tr.tau, p, tr.m, s);
                 P.foldbins[t] = p;
@@ -542,13 +605,17 @@ __global__ void __launch_bounds__(kTopThreads) ffa_top_kernel(TopParams P) {
 
     // ---- interval table, heap order: node e at level l is e = 2^l - 1 + j.
     //      per node: [0] abs start row, [1] size, [2] lo, [3] hi, [4] smem offset of row lo
+    //      Built by warp 0, one lane per node of a level.
     int* tab = reinterpret_cast<int*>(smem + lay.table);
     int* lvl_desc = tab + 120;  // first descriptor of each level, levels L-1..0, + end
-    if (tid == 0) {
-        tab[0] = st0; tab[1] = n0; tab[2] = lo0; tab[3] = hi0;
+    if (warp == 0) {
+        if (lane == 0) {
+            tab[0] = st0; tab[1] = n0; tab[2] = lo0; tab[3] = hi0;
+        }
+        __syncwarp();
         for (int l = 0; l < L; ++l) {
-            for (int j = 0; j < (1 << l); ++j) {
-                const int e = (1 << l) - 1 + j;
+            if (lane < (1 << l)) {
+                const int e = (1 << l) - 1 + lane;
                 const int st = tab[8 * e], n = tab[8 * e + 1], lo = tab[8 * e + 2], hi = tab[8 * e + 3];
                 const int nh = n >> 1;
                 const Split a = merge_split(n, lo), z = merge_split(n, hi);
@@ -557,30 +624,33 @@ __global__ void __launch_bounds__(kTopThreads) ffa_top_kernel(TopParams P) {
                 tab[8 * et] = st + nh; tab[8 * et + 1] = n - nh; tab[8 * et + 2] = a.j;
                 tab[8 * et + 3] = z.j;
             }
+            __syncwarp();
         }
-        // offsets: level L with alignment slack (buffer A), the others compact
-        int off = lay.buf_a;
-        for (int j = 0; j < (1 << L); ++j) {
-            const int e = (1 << L) - 1 + j;
-            const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
-            const int h = (int)((reinterpret_cast<uintptr_t>(g) >> 2) & 3);
-            tab[8 * e + 4] = off + h;
-            off = round4(off + h + (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p);
-        }
-        int nd = 0;
-        for (int l = L - 1; l >= 0; --l) {
-            int o = (((L - l) & 1) == 0) ? lay.buf_a : lay.buf_b;
-            lvl_desc[L - 1 - l] = nd;
-            for (int j = 0; j < (1 << l); ++j) {
-                const int e = (1 << l) - 1 + j;
-                tab[8 * e + 4] = o;
-                const int rows = tab[8 * e + 3] - tab[8 * e + 2] + 1;
-                o += rows * p;
-                nd += rows;
+        if (lane == 0) {
+            // offsets: level L with alignment slack (buffer A), the others compact
+            int off = lay.buf_a;
+            for (int j = 0; j < (1 << L); ++j) {
+                const int e = (1 << L) - 1 + j;
+                const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
+                const int h = (int)((reinterpret_cast<uintptr_t>(g) >> 2) & 3);
+                tab[8 * e + 4] = off + h;
+                off = round4(off + h + (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p);
             }
+            int nd = 0;
+            for (int l = L - 1; l >= 0; --l) {
+                int o = (((L - l) & 1) == 0) ? lay.buf_a : lay.buf_b;
+                lvl_desc[L - 1 - l] = nd;
+                for (int j = 0; j < (1 << l); ++j) {
+                    const int e = (1 << l) - 1 + j;
+                    tab[8 * e + 4] = o;
+                    const int rows = tab[8 * e + 3] - tab[8 * e + 2] + 1;
+                    o += rows * p;
+                    nd += rows;
+                }
+            }
+            lvl_desc[L] = nd;
+            mbar_init(bar, 1);
         }
-        lvl_desc[L] = nd;
-        mbar_init(bar, 1);
     }
     __syncthreads();
 
@@ -638,8 +708,9 @@ __global__ void __launch_bounds__(kTopThreads) ffa_top_kernel(TopParams P) {
         return;
     }
 
-    // ---- merge levels L-1 .. 0
-    for (int l = L - 1; l >= 0; --l) {
+    // ---- merge levels L-1 .. 1, and level 0 unless it is scored straight from registers
+    const bool fused = score && ((p + 31) >> 5) <= kSnrMaxSlots;
+    for (int l = L - 1; l >= (fused ? 1 : 0); --l) {
         const int q1 = lvl_desc[L - l];
         for (int q = lvl_desc[L - 1 - l] + warp; q < q1; q += nwarps) {
             const int4 d = desc[q];
@@ -653,10 +724,17 @@ __global__ void __launch_bounds__(kTopThreads) ffa_top_kernel(TopParams P) {
     const int rows0 = hi0 - lo0 + 1;
     if (score) {
         float* S = smem + lay.sbuf + warp * lay.sbuf_warp;
+        const int q0 = lvl_desc[L - 1];
         for (int r = warp; r < rows0; r += nwarps) {
             const int s = lo0 + r;
             const int64_t t = tr.trial0 + s;
-            warp_snr(smem + o0 + r * p, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw, lane);
+            float* dst = P.snr + t * P.widths.nw;
+            if (fused) {
+                const int4 d = desc[q0 + r];
+                snr_merge(smem, d.y, d.z, d.w, p, S, P.widths, tr.inv_std, dst, lane);
+            } else {
+                snr_row(smem + o0 + r * p, p, S, P.widths, tr.inv_std, dst, lane);
+            }
             if (lane == 0) {
                 P.periods[t] = trial_period(tr.tau, p, m, s);
                 P.foldbins[t] = p;
@@ -677,8 +755,7 @@ __global__ void __launch_bounds__(256) boxcar_snr_kernel(SnrParams P) {
     float* S = smem + warp * P.warp_floats;
     const int64_t stride = (int64_t)gridDim.x * 8;
     for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < P.rows; r += stride) {
-        warp_snr(P.prof + r * P.cols, P.cols, S, P.widths, P.inv_std, P.snr + r * P.widths.nw,
-                 lane);
+        snr_row(P.prof + r * P.cols, P.cols, S, P.widths, P.inv_std, P.snr + r * P.widths.nw, lane);
     }
 }
 
