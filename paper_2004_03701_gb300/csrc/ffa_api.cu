@@ -741,7 +741,7 @@ ffa_status ffa_boxcar_snr(const float* d_prof, int32_t rows, int32_t cols,
     sp.cols = cols;
     sp.inv_std = (float)(1.0 / stdnoise);
     sp.snr = d_snr;
-    sp.warp_floats = (int)align_up((size_t)(cols + sp.widths.wmax + 1), 4);
+    sp.warp_floats = snr_warp_floats(cols, sp.widths.wmax);
     if (8 * sp.warp_floats * 4 > kSmemBytes)
         return fail(FFA_ERR_UNSUPPORTED, "cols + max width too large for shared memory");
     FFA_CUDA(launch_snr(sp, static_cast<cudaStream_t>(stream)), "boxcar_snr launch");

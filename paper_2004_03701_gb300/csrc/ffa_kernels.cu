@@ -302,14 +302,43 @@ __device__ __forceinline__ void snr_from_regs(const float (&v)[T], int p, float*
         const int x = lane + 32 * t;
         sk[t] = x < p ? S[x] : INFINITY;
     }
-    for (int iw = 0; iw < W.nw; ++iw) {
-        const float* Sw = S + W.w[iw] + lane;
-        float best = -INFINITY;
+    // 16 widths at a time: per-lane maxima, then one transposed butterfly reduction
+    // (16 shuffles for 16 widths); afterwards lane pair (2v, 2v+1) holds width v.
+    for (int w0 = 0; w0 < W.nw; w0 += 16) {
+        float b[16];
 #pragma unroll
-        for (int t = 0; t < T; ++t) best = fmaxf(best, Sw[32 * t] - sk[t]);
+        for (int i = 0; i < 16; ++i) {
+            b[i] = -INFINITY;
+            if (w0 + i < W.nw) {
+                const float* Sw = S + W.w[w0 + i] + lane;
 #pragma unroll
-        for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
-        if (lane == 0) out[iw] = best * inv_std * W.inv_sqrt_w[iw];
+                for (int t = 0; t < T; ++t) b[i] = fmaxf(b[i], Sw[32 * t] - sk[t]);
+            }
+        }
+        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float keep = h16 ? b[i + 8] : b[i], send = h16 ? b[i] : b[i + 8];
+            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 16));
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float keep = h8 ? b[i + 4] : b[i], send = h8 ? b[i] : b[i + 4];
+            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 8));
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float keep = h4 ? b[i + 2] : b[i], send = h4 ? b[i] : b[i + 2];
+            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 4));
+        }
+        {
+            const float keep = h2 ? b[1] : b[0], send = h2 ? b[0] : b[1];
+            b[0] = fmaxf(keep, __shfl_xor_sync(kFull, send, 2));
+        }
+        b[0] = fmaxf(b[0], __shfl_xor_sync(kFull, b[0], 1));
+        const int v = (h16 ? 8 : 0) + (h8 ? 4 : 0) + (h4 ? 2 : 0) + (h2 ? 1 : 0);
+        if ((lane & 1) == 0 && w0 + v < W.nw)
+            out[w0 + v] = b[0] * inv_std * W.inv_sqrt_w[w0 + v];
     }
     __syncwarp();
 }
@@ -474,8 +503,75 @@ __device__ __forceinline__ int2 bottom_desc(int n, int lev, int r, int p) {
     return make_int2((st + sp.i) | ((st + (sz >> 1) + sp.j) << 16), sp.shift % p);
 }
 
+// ---------------------------------------------------------------------------------
+// Register stage: the transform of a node of S <= 16 rows (its whole sub-tree, up to
+// four merge levels) on a strip of 32 consecutive columns held one per lane.  The
+// rotation T[(x + k) mod p] is a shuffle down by k within the strip; an output column
+// depends on input columns x .. x + S - 1 only, so lanes 0 .. 32 - S are exact and the
+// strips advance by 33 - S columns.  The merge schedule of each S is a compile-time
+// table, so every operand is a fixed register.
+// ---------------------------------------------------------------------------------
+template <int S>
+struct RegSched {
+    int i[S], j[S], sh[S];
+    constexpr RegSched() : i(), j(), sh() {
+        constexpr int nh = S / 2, nt = S - S / 2;
+        for (int s = 0; s < S; ++s) {
+            i[s] = S > 1 ? (2 * (nh - 1) * s + (S - 1)) / (2 * (S - 1)) : 0;
+            j[s] = S > 1 ? (2 * (nt - 1) * s + (S - 1)) / (2 * (S - 1)) : 0;
+            sh[s] = s - j[s];
+        }
+    }
+};
+
+template <int OFF, int S, int N>
+__device__ __forceinline__ void reg_ffa(float (&v)[N]) {
+    if constexpr (S > 1) {
+        constexpr int nh = S / 2;
+        reg_ffa<OFF, nh, N>(v);
+        reg_ffa<OFF + nh, S - nh, N>(v);
+        constexpr RegSched<S> sc{};
+        float o[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            o[s] = __fadd_rn(v[OFF + sc.i[s]], __shfl_down_sync(kFull, v[OFF + nh + sc.j[s]], sc.sh[s]));
+#pragma unroll
+        for (int s = 0; s < S; ++s) v[OFF + s] = o[s];
+    }
+}
+
+// One strip of one node: rows [st, st + S) of `in`, columns from c0, into `out`.
+template <int S>
+__device__ __forceinline__ void reg_strip(float* sm, int in, int out, int st, int p, int c0,
+                                          int vstep, int lane) {
+    int x = c0 + lane;
+    if (x >= p) x %= p;
+    float v[S];
+#pragma unroll
+    for (int r = 0; r < S; ++r) v[r] = sm[in + (st + r) * p + x];
+    reg_ffa<0, S, S>(v);
+    if (lane < vstep && c0 + lane < p) {  // vstep <= 33 - S: exact lanes only
+#pragma unroll
+        for (int r = 0; r < S; ++r) sm[out + (st + r) * p + x] = v[r];
+    }
+}
+
+__device__ __forceinline__ void reg_strip_any(float* sm, int in, int out, int st, int sz, int p,
+                                              int c0, int vstep, int lane) {
+    switch (sz) {
+#define FFA_REG(S) case S: reg_strip<S>(sm, in, out, st, p, c0, vstep, lane); break;
+        FFA_REG(1) FFA_REG(2) FFA_REG(3) FFA_REG(4) FFA_REG(5) FFA_REG(6) FFA_REG(7) FFA_REG(8)
+        FFA_REG(9) FFA_REG(10) FFA_REG(11) FFA_REG(12) FFA_REG(13) FFA_REG(14) FFA_REG(15)
+        FFA_REG(16)
+#undef FFA_REG
+        default: break;
+    }
+}
+
+constexpr int kRegLevels = 4;          // levels done in registers: nodes of <= 16 rows
+
 template <bool kSnr>
-__global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams P) {
+__global__ void __launch_bounds__(kBottomThreads, 1) ffa_bottom_kernel(BottomParams P) {
     extern __shared__ __align__(16) float smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -507,8 +603,25 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
     }
     load_row_ends(smem, a0, src, total, tid, kBottomThreads);
     const int H = tree_height(n);
-    if (H >= 1)
-        for (int r = tid; r < n; r += kBottomThreads) desc[r] = bottom_desc(n, 1, r, p);
+    // nodes of the register stage: height <= kRegLevels, parent higher (one per start row)
+    int* rnodes = reinterpret_cast<int*>(desc + P.nmax);  // second descriptor buffer, for now
+    __shared__ int nreg, regmax;
+    if (tid == 0) { nreg = 0; regmax = 1; }
+    __syncthreads();
+    for (int r = tid; r < n; r += kBottomThreads) {
+        int st = 0, sz = n;
+        while (tree_height(sz) > kRegLevels) {
+            const int nh = sz >> 1;
+            if (r - st >= nh) { st += nh; sz -= nh; } else { sz = nh; }
+        }
+        if (r == st) {
+            const int q = atomicAdd(&nreg, 1);
+            rnodes[q] = st | (sz << 16);
+            atomicMax(&regmax, sz);
+        }
+    }
+    if (H > kRegLevels)
+        for (int r = tid; r < n; r += kBottomThreads) desc[r] = bottom_desc(n, kRegLevels + 1, r, p);
     const bool landed = bytes == 0 || mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
@@ -518,12 +631,26 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
         return;
     }
 
-    // ---- merge levels 1..H; level lev+1's descriptors are made while level lev merges
-    int in = a0, out = lay.buf_b;
-    for (int lev = 1; lev <= H; ++lev) {
-        const int2* dc = desc + ((lev - 1) & 1) * P.nmax;
+    // ---- register stage: complete transforms of the nodes of <= 16 rows, A -> B
+    int in = lay.buf_b, out = lay.buf_a;
+    {
+        const int vstep = 33 - regmax;
+        const int nstrip = (p + vstep - 1) / vstep;
+        const int nwork = nreg * nstrip;
+        for (int w = warp; w < nwork; w += nwarps) {
+            const int q = w / nstrip, c = w - q * nstrip;
+            const int nd = rnodes[q];
+            reg_strip_any(smem, a0, lay.buf_b, nd & 0xffff, nd >> 16, p, c * vstep, vstep, lane);
+        }
+        __syncthreads();
+    }
+
+    // ---- merge levels kRegLevels+1 .. H in shared memory; level lev+1's descriptors
+    //      are made while level lev merges
+    for (int lev = kRegLevels + 1; lev <= H; ++lev) {
+        const int2* dc = desc + ((lev - kRegLevels - 1) & 1) * P.nmax;
         if (lev < H) {
-            int2* dn = desc + (lev & 1) * P.nmax;
+            int2* dn = desc + ((lev - kRegLevels) & 1) * P.nmax;
             for (int r = tid; r < n; r += kBottomThreads) dn[r] = bottom_desc(n, lev + 1, r, p);
         }
         for (int r = warp; r < n; r += nwarps) {
@@ -535,7 +662,7 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
         __syncthreads();
         const int t = in;
         in = out;
-        out = (t == a0) ? lay.buf_a : t;
+        out = t;
     }
 
     if constexpr (!kSnr) {
@@ -548,10 +675,10 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
         for (int s = warp; warp < P.snr_warps && s < tr.kept; s += P.snr_warps) {
             const int64_t t = tr.trial0 + s;
             snr_row(smem + in + s * p, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw, lane);
-            if (lane == 0) {
-                P.periods[t] = trial_period(tr.tau, p, tr.m, s);
-                P.foldbins[t] = p;
-            }
+        }
+        for (int s = tid; s < tr.kept; s += kBottomThreads) {
+            P.periods[tr.trial0 + s] = trial_period(tr.tau, p, tr.m, s);
+            P.foldbins[tr.trial0 + s] = p;
         }
     }
     __syncthreads();
@@ -566,7 +693,7 @@ __global__ void __launch_bounds__(kBottomThreads) ffa_bottom_kernel(BottomParams
 // per interval) and merged in shared memory.  The last pass of a periodogram scores
 // its rows with the boxcar filters instead of storing them.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTopThreads) ffa_top_kernel(TopParams P) {
+__global__ void __launch_bounds__(kTopThreads, 1) ffa_top_kernel(TopParams P) {
     extern __shared__ __align__(16) float smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -735,10 +862,10 @@ __global__ void __launch_bounds__(kTopThreads) ffa_top_kernel(TopParams P) {
             } else {
                 snr_row(smem + o0 + r * p, p, S, P.widths, tr.inv_std, dst, lane);
             }
-            if (lane == 0) {
-                P.periods[t] = trial_period(tr.tau, p, m, s);
-                P.foldbins[t] = p;
-            }
+        }
+        for (int r = tid; r < rows0; r += kTopThreads) {
+            P.periods[tr.trial0 + lo0 + r] = trial_period(tr.tau, p, m, lo0 + r);
+            P.foldbins[tr.trial0 + lo0 + r] = p;
         }
     } else {
         float* dst = out + (int64_t)(st0 + lo0) * p;
