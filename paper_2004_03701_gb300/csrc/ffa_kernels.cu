@@ -605,7 +605,8 @@ __global__ void __launch_bounds__(kBottomThreads, 1) ffa_bottom_kernel(BottomPar
     const int H = tree_height(n);
     // nodes of the register stage: height <= kRegLevels, parent higher (one per start row)
     int* rnodes = reinterpret_cast<int*>(desc + P.nmax);  // second descriptor buffer, for now
-    __shared__ int nreg, regmax;
+    int& nreg = reinterpret_cast<int*>(smem)[2];           // header: barrier, then 2 ints
+    int& regmax = reinterpret_cast<int*>(smem)[3];
     if (tid == 0) { nreg = 0; regmax = 1; }
     __syncthreads();
     for (int r = tid; r < n; r += kBottomThreads) {
@@ -886,13 +887,18 @@ __global__ void __launch_bounds__(256) boxcar_snr_kernel(SnrParams P) {
     }
 }
 
-// Raises a kernel's dynamic shared memory limit once per device.
+// Raises a kernel's dynamic shared memory limit once per device (to the CTA maximum
+// minus the kernel's static shared memory).  A failure is left for the launch check.
 void allow_max_smem(const void* func, int slot) {
     static unsigned char done[8][64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || done[slot][dev]) return;
-    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, func) != cudaSuccess) return;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kSmemBytes - (int)fa.sharedSizeBytes) != cudaSuccess)
+        return;
     done[slot][dev] = 1;
 }
 
