@@ -150,7 +150,7 @@ constexpr int64_t kGroupFloats = int64_t(6) << 20;  // 24 MB per scratch buffer 
 // layout fits in shared memory.
 int max_subtree_rows(int p, int row_cap) {
     int n = std::min(row_cap, kBottomMaxRows);
-    while (n > 1 && bottom_layout(n, n * p, 0).total * 4 > kSmemBytes) --n;
+    while (n > 1 && bottom_layout(n, n * p, 0).total * 4 > kBottomSmemBytes) --n;
     return std::max(n, 1);
 }
 int depth_for(int m, int p, int row_cap = kBottomMaxRows) {
@@ -163,7 +163,7 @@ int depth_for(int m, int p, int row_cap = kBottomMaxRows) {
 // Rows per top-kernel CTA: the most that fit in shared memory (at most kTopMaxRows).
 int top_rows(int p, int L, bool score, int wmax) {
     for (int K = kTopMaxRows; K >= 1; --K)
-        if (top_layout(K, L, p, wmax, score).total * 4 <= kSmemBytes) return K;
+        if (top_layout(K, L, p, wmax, score).total * 4 <= kTopSmemBytes) return K;
     return 0;
 }
 

@@ -12,6 +12,24 @@ namespace ffa {
 constexpr int kMaxWidths = 64;       // boxcar widths per search
 constexpr int kMaxCols = 4096;       // base period (bins) limit of this build
 constexpr int kSmemBytes = 232448;   // dynamic shared memory per CTA on sm_103 (227 KB)
+// Shared-memory budgets of the two FFA kernels: the whole CTA maximum (one CTA per SM)
+// or a fraction of it (several CTAs per SM hide each other's barriers and load waits).
+#ifndef FFA_BOTTOM_SMEM
+#define FFA_BOTTOM_SMEM 232448
+#endif
+#ifndef FFA_TOP_SMEM
+#define FFA_TOP_SMEM 232448
+#endif
+#ifndef FFA_BOTTOM_MINB
+#define FFA_BOTTOM_MINB 1
+#endif
+#ifndef FFA_TOP_MINB
+#define FFA_TOP_MINB 1
+#endif
+constexpr int kBottomSmemBytes = FFA_BOTTOM_SMEM;
+constexpr int kTopSmemBytes = FFA_TOP_SMEM;
+constexpr int kBottomMinBlocks = FFA_BOTTOM_MINB;  // resident CTAs per SM to allow for
+constexpr int kTopMinBlocks = FFA_TOP_MINB;
 constexpr int kBottomThreads = 512;  // CTA of the shared-memory sub-tree kernel
 constexpr int kTopThreads = 512;     // CTA of the gathered top-level kernel
 constexpr int kTopMaxLevels = 3;     // merge levels per top pass

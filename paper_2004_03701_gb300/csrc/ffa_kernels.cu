@@ -571,7 +571,7 @@ __device__ __forceinline__ void reg_strip_any(float* sm, int in, int out, int st
 constexpr int kRegLevels = 4;          // levels done in registers: nodes of <= 16 rows
 
 template <bool kSnr>
-__global__ void __launch_bounds__(kBottomThreads, 1) ffa_bottom_kernel(BottomParams P) {
+__global__ void __launch_bounds__(kBottomThreads, kBottomMinBlocks) ffa_bottom_kernel(BottomParams P) {
     extern __shared__ __align__(16) float smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -694,7 +694,7 @@ __global__ void __launch_bounds__(kBottomThreads, 1) ffa_bottom_kernel(BottomPar
 // per interval) and merged in shared memory.  The last pass of a periodogram scores
 // its rows with the boxcar filters instead of storing them.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTopThreads, 1) ffa_top_kernel(TopParams P) {
+__global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(TopParams P) {
     extern __shared__ __align__(16) float smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
