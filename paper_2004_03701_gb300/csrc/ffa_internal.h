@@ -92,9 +92,14 @@ struct TopLayout {
 };
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 
-// Prefix-sum row of the boxcar S/N of a p-bin profile: S[0 .. 32 ceil(p/32) + wmax].
+// Prefix-sum rows of the boxcar S/N of a p-bin profile: S[0 .. 64 ceil(p/64) + wmax]
+// and the same row shifted by one (so that every pair S[j], S[j+1] is 8-byte aligned in
+// one of the two), each snr_half floats.
+__host__ __device__ inline int snr_half(int p, int wmax) {
+    return round4(((p + 63) & ~63) + wmax + 2);
+}
 __host__ __device__ inline int snr_warp_floats(int p, int wmax) {
-    return round4(((p + 31) & ~31) + wmax + 1);
+    return 2 * snr_half(p, wmax);
 }
 
 // Shared-memory layout (in floats) of a sub-tree CTA: barrier, two row-descriptor
