@@ -82,6 +82,25 @@ ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d
                          void* d_ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------
+ * ffa_transform without a workspace, for callers that cannot allocate device memory
+ * (plugins whose host application manages all device allocations, pipelines that
+ * forbid allocation once running, code whose device memory another runtime's pool has
+ * reserved).  The paper has no counterpart: this is a deployment variant of
+ * ffa_transform, with the same arguments minus the workspace and the same bit-exact
+ * result.
+ * Scratch: a fixed 4 MiB array inside the library (per device, held by every GPU that
+ * loads the library until the process exits).  Blocks that need sub-trees may have
+ * rows * cols <= 1048512 floats; larger ones return FFA_ERR_CAPACITY before anything is
+ * launched.  Allocates nothing (no cudaMalloc, cudaFree, events or library allocator).
+ * The first call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.
+ * ---------------------------------------------------------------------------- */
+ffa_status ffa_transform_noalloc(const float* d_in, int32_t rows, int32_t cols, float* d_out,
+                                 void* stream);
+
+/* ------------------------------------------------------------------------------
  * Boxcar matched filter S/N (paper Sec. 5.4, with the Z-statistic normalisation of
  * Sec. 3.3 and App. A.3).  For each profile row r and width w = h_widths[iw]:
  *   d_snr[r * nw + iw] = max_{0<=k<cols} C_k(w) / (stdnoise * sqrt(w)),

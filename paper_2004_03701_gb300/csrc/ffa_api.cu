@@ -548,9 +548,13 @@ bool aligned256(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 255) =
 
 }  // namespace
 
+thread_local bool g_no_alloc_call = false;
+ffa_status set_error(ffa_status st, const char* msg) { return fail(st, "%s", msg); }
+
 // ---------------------------------------------------------------------------------
 LaunchScope::LaunchScope(int k, double b, cudaStream_t s) : kind(k), bytes(b), stream(s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_no_alloc_call) return;  // no event objects are created on the no-allocation path
     std::lock_guard<std::mutex> lk(g_prof_mu);
     if (!g_prof_on) return;
     ev0 = pool_get();
