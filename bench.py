@@ -55,6 +55,20 @@ def workload(name):
     return synth.survey() if name == "survey" else synth.plain_small()
 
 
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, or None if the
+    kernel source changed since it was taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2004_03701_gb300", "csrc", "ffa_kernels.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_prefix"]:
+            return None
+        return rec["dram_bytes_per_launch"] if rec["kernel"] == kernel else None
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -259,7 +273,7 @@ def run_ffa(a):
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / avg_s / 1e9
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": recorded_traffic(top),
                 "peak_source": peak_kind,
                 "share_of_step": kq["ms"] / tot_ms if tot_ms else None,
                 "launches_per_step": kq["launches"] / a.steps}

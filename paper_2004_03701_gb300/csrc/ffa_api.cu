@@ -67,9 +67,9 @@ std::vector<ProfRec> g_pending;
 std::vector<cudaEvent_t> g_pool;
 ProfAcc g_acc[kNumKinds];
 
-const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top", "prefix_final",
-                                     "downsample",     "ffa_bottom", "ffa_bottom_snr",
-                                     "ffa_top",        "ffa_top_snr", "boxcar_snr"};
+const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top",     "prefix_final",
+                                     "downsample",     "ffa_bottom",     "ffa_bottom_snr",
+                                     "ffa_top",        "boxcar_snr"};
 
 cudaEvent_t pool_get() {
     if (!g_pool.empty()) {
@@ -537,7 +537,7 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
             tp.foldbins = d_foldbins;
             tp.snr = d_snr;
             tp.status = status;
-            LaunchScope ls(kFfaTopSnr, sg.bytes, st);
+            LaunchScope ls(kFfaTop, sg.bytes, st);
             FFA_CUDA(launch_top(tp, (int)sg.cnt, sg.smem, st), "ffa_top launch");
         }
     }

@@ -174,7 +174,6 @@ enum KernelKind : int {
     kFfaBottom,
     kFfaBottomSnr,
     kFfaTop,
-    kFfaTopSnr,
     kBoxcarSnr,
     kNumKinds
 };

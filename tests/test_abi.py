@@ -101,7 +101,7 @@ def test_other_calls_reject_bad_arguments(lib):
 
 def test_kernel_kinds(lib):
     names = ffa.kernel_names()
-    assert "ffa_bottom" in names and "ffa_top_snr" in names and "downsample" in names
+    assert "ffa_bottom" in names and "ffa_top" in names and "downsample" in names
 
 
 def test_width_sets_fit_the_plan(lib):
