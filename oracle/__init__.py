@@ -15,6 +15,7 @@ Paper passages followed (sections and equations of the paper):
   * ffa ............. Sec. 2.2, Eq. ffa_merge_rule (depth-first, m_h = floor(m/2))
   * trial periods ... Sec. 2.3 (P_s = p^2 tau / (p - s/(m-1)); redundant rows)
   * boxcar S/N ...... Sec. 5.4, Sec. 3.3 (Z = x.s, unit square sum), App. A.3
+  * normalise ....... Sec. 3.1, Sec. 5.2 (zero mean, unit std from the whole series)
 """
 from __future__ import annotations
 
@@ -76,6 +77,8 @@ def _load():
     lib.oracle_trial_period.argtypes = [_dbl, _i64, _i64, _i64]
     lib.oracle_boxcar_snr.restype = _int
     lib.oracle_boxcar_snr.argtypes = [_p, _i64, _i64, _p, _int, _dbl, _p]
+    lib.oracle_normalise.restype = _int
+    lib.oracle_normalise.argtypes = [_p, _i64, _p, _p, _p]
     lib.oracle_periodogram.restype = _i64
     lib.oracle_periodogram.argtypes = [_p, _i64, _dbl, _dbl, _dbl, _int, _int, _p, _int,
                                        _p, _p, _p, _p, _i64]
@@ -201,6 +204,17 @@ def boxcar_snr(prof: np.ndarray, widths, stdnoise: float) -> np.ndarray:
     if lib.oracle_boxcar_snr(_ptr(P), rows, p, _ptr(w), len(w), stdnoise, _ptr(out)) != 0:
         raise ValueError("invalid boxcar arguments")
     return out
+
+
+def normalise(x: np.ndarray):
+    """Sec. 3.1 / 5.2: (mean, std, (x - mean) / std) of a float32 series, FP64."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    mean, std = ctypes.c_double(), ctypes.c_double()
+    out = np.zeros(len(x), np.float64)
+    if lib.oracle_normalise(_ptr(x), len(x), ctypes.byref(mean), ctypes.byref(std), _ptr(out)) != 0:
+        raise ValueError("empty series")
+    return mean.value, std.value, out
 
 
 @dataclass

@@ -14,6 +14,7 @@
  *   - depth-first FFA                    Sec. 2.2, Eq. "ffa_merge_rule"
  *   - trial periods, redundant rows      Sec. 2.3, Eqs. for nu_s and P_s
  *   - boxcar S/N                         Sec. 5.4, Sec. 3.3 (Z-statistic), App. A.3
+ *   - normalisation                      Sec. 3.1, Sec. 5.2 (whole-series mean/std)
  *
  * Readings where the paper is silent (each is shared with the CUDA path as a
  * written convention, never as code):
@@ -265,6 +266,30 @@ int oracle_boxcar_snr(const double* prof, int64_t rows, int64_t p, const int* wi
             snr[r * nw + iw] = best / (stdnoise * sqrt((double)w));
         }
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Normalisation (Sec. 3.1, Sec. 5.2): the series is brought to zero mean and  */
+/* unit standard deviation once, from statistics of the whole series.          */
+/* Two passes in FP64; population standard deviation.                          */
+/* ------------------------------------------------------------------------- */
+
+int oracle_normalise(const float* x, int64_t n, double* mean, double* stdev, double* out)
+{
+    int64_t i;
+    double s = 0.0, q = 0.0;
+    if (n <= 0) return -1;
+    for (i = 0; i < n; ++i) s += (double)x[i];
+    *mean = s / (double)n;
+    for (i = 0; i < n; ++i) {
+        double d = (double)x[i] - *mean;
+        q += d * d;
+    }
+    *stdev = sqrt(q / (double)n);
+    if (out)
+        for (i = 0; i < n; ++i)
+            out[i] = *stdev > 0.0 ? ((double)x[i] - *mean) / *stdev : 0.0;
     return 0;
 }
 
