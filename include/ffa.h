@@ -117,6 +117,21 @@ ffa_status ffa_boxcar_snr(const float* d_prof, int32_t rows, int32_t cols,
                           float* d_snr, void* stream);
 
 /* ------------------------------------------------------------------------------
+ * Normalisation of a whole series (paper Sec. 3.1 and Sec. 5.2): the noise mean and
+ * standard deviation are estimated once from the whole series and every sample becomes
+ *   x' = (x - mean) / std,
+ * mean and std (population) accumulated in double.  d_mean_std (device, 2 doubles)
+ * receives {mean, std}.  d_out (device) receives n values of type out_dtype:
+ * FFA_F32 float, FFA_F16 binary16, FFA_I8 int8 q = clamp(rint(16 x'), -128, 127)
+ * (value q / 16, i.e. clipped at +-8 sigma).  A constant series (std = 0) gives zeros.
+ * Workspace: ffa_normalise_workspace(n) bytes.  Deterministic for a given n.
+ * Errors: FFA_ERR_ARG (null pointers, n <= 0, bad dtype), FFA_ERR_CAPACITY.
+ * ---------------------------------------------------------------------------- */
+ffa_status ffa_normalise_workspace(int64_t n, size_t* bytes);
+ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out_dtype,
+                         double* d_mean_std, void* d_ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------
  * Periodogram search plan (paper Sec. 5.3, Fig. 4; Sec. 5.6 for the first factor).
  *   f0 = pmin / (bmin * tsamp) (must be >= 1), fg = (bmax + 1) / bmin,
  *   octave k: factor F_k = f0 * fg^k while bmin * tsamp * F_k <= pmax,

@@ -23,7 +23,7 @@ from typing import Optional, Sequence, Tuple
 import numpy as np
 
 __all__ = [
-    "FFAError", "library", "build", "downsample", "ffa_transform", "boxcar_snr",
+    "FFAError", "library", "build", "normalise", "downsample", "ffa_transform", "boxcar_snr",
     "PlanInfo", "periodogram_plan", "periodogram", "periodogram_host", "Searcher",
     "check", "launch_count", "kernel_names", "profile_enable", "profile_reset",
     "profile_query",
@@ -84,6 +84,8 @@ def library() -> ctypes.CDLL:
     L.ffa_periodogram_host.argtypes = [vp, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
                                        i64, vp, sz, vp]
     L.ffa_check.argtypes = [vp, vp]
+    L.ffa_normalise_workspace.argtypes = [i64, ctypes.POINTER(sz)]
+    L.ffa_normalise.argtypes = [vp, i64, vp, i32, vp, vp, sz, vp]
     L.ffa_launch_count.restype = i64
     L.ffa_kernel_kinds.restype = i32
     L.ffa_kernel_name.restype = ctypes.c_char_p
@@ -94,6 +96,7 @@ def library() -> ctypes.CDLL:
     for f in ("ffa_downsample_workspace", "ffa_downsample", "ffa_transform_workspace",
               "ffa_transform", "ffa_boxcar_snr", "ffa_periodogram_plan", "ffa_periodogram",
               "ffa_periodogram_host", "ffa_check", "ffa_profile_enable", "ffa_profile_reset",
+              "ffa_normalise_workspace", "ffa_normalise",
               "ffa_profile_query"):
         getattr(L, f).restype = i32
     _lib = L
@@ -141,6 +144,29 @@ def _vp(a) -> ctypes.c_void_p:
 
 
 # ----------------------------------------------------------------------------------
+def normalise(x, dtype=None, stream=None):
+    """Whole-series normalisation (Sec. 3.1, 5.2) of a float32 CUDA series.
+
+    Returns (x', mean, std): x' of `dtype` (torch.float32, torch.float16, or torch.int8
+    holding q with value q/16), mean and std as Python floats (FP64 on the device)."""
+    torch = _torch()
+    _dev_tensor(x, "x")
+    if x.dtype != torch.float32 or x.dim() != 1:
+        raise TypeError("x must be a 1-D float32 tensor")
+    dtype = torch.float32 if dtype is None else dtype
+    code = {torch.float32: FFA_F32, torch.float16: FFA_F16, torch.int8: FFA_I8}[dtype]
+    L = library()
+    need = ctypes.c_size_t()
+    _check(L.ffa_normalise_workspace(x.numel(), ctypes.byref(need)))
+    ws = _workspace(need.value, x.device)
+    out = torch.empty(x.numel(), dtype=dtype, device=x.device)
+    stats = torch.empty(2, dtype=torch.float64, device=x.device)
+    _check(L.ffa_normalise(_vp(x), x.numel(), _vp(out), code, _vp(stats), _vp(ws), ws.numel(),
+                           _stream_handle(stream)))
+    m, s = stats.tolist()
+    return out, m, s
+
+
 def downsample(x, factor: float, stream=None):
     """Real-factor downsampling of a float32 CUDA series (Sec. 5.3, App. A.4)."""
     torch = _torch()

@@ -69,7 +69,7 @@ ProfAcc g_acc[kNumKinds];
 
 const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top",     "prefix_final",
                                      "downsample",     "ffa_bottom",     "ffa_bottom_snr",
-                                     "ffa_top",        "boxcar_snr"};
+                                     "ffa_top",        "boxcar_snr",     "normalise"};
 
 cudaEvent_t pool_get() {
     if (!g_pool.empty()) {
@@ -749,6 +749,36 @@ ffa_status ffa_boxcar_snr(const float* d_prof, int32_t rows, int32_t cols,
     if (8 * sp.warp_floats * 4 > kSmemBytes)
         return fail(FFA_ERR_UNSUPPORTED, "cols + max width too large for shared memory");
     FFA_CUDA(launch_snr(sp, static_cast<cudaStream_t>(stream)), "boxcar_snr launch");
+    return FFA_OK;
+}
+
+// ---------------------------------------------------------------------------------
+ffa_status ffa_normalise_workspace(int64_t n, size_t* bytes) {
+    if (!bytes) return fail(FFA_ERR_ARG, "bytes is null");
+    if (n <= 0) return fail(FFA_ERR_ARG, "n must be positive");
+    *bytes = kStatusBytes + align_up((size_t)kNormaliseBlocks * sizeof(double), 256);
+    return FFA_OK;
+}
+
+ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out_dtype,
+                         double* d_mean_std, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!d_x || !d_out || !d_mean_std || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
+    if (out_dtype != FFA_F32 && out_dtype != FFA_F16 && out_dtype != FFA_I8)
+        return fail(FFA_ERR_ARG, "bad dtype");
+    size_t need = 0;
+    ffa_status st = ffa_normalise_workspace(n, &need);
+    if (st != FFA_OK) return st;
+    if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
+    if (ws_bytes < need) return fail(FFA_ERR_CAPACITY, "workspace needs %zu bytes", need);
+    NormaliseParams P{};
+    P.x = d_x;
+    P.n = n;
+    P.partial = reinterpret_cast<double*>(static_cast<char*>(d_ws) + kStatusBytes);
+    P.nblocks = kNormaliseBlocks;
+    P.stats = d_mean_std;
+    P.out = d_out;
+    P.out_dtype = out_dtype;
+    FFA_CUDA(launch_normalise(P, static_cast<cudaStream_t>(stream)), "normalise launch");
     return FFA_OK;
 }
 

@@ -175,6 +175,7 @@ enum KernelKind : int {
     kFfaBottomSnr,
     kFfaTop,
     kBoxcarSnr,
+    kNormalise,
     kNumKinds
 };
 
@@ -245,6 +246,16 @@ struct SnrParams {
     int warp_floats;
 };
 
+struct NormaliseParams {
+    const float* x;
+    int64_t n;
+    double* partial;                // per-CTA FP64 partial sums
+    int nblocks;
+    double* stats;                  // [0] mean, [1] standard deviation (device)
+    void* out;
+    int out_dtype;                  // ffa_dtype
+};
+
 // Launchers (ffa_kernels.cu).  Each returns the cudaError_t of the launch.
 cudaError_t launch_prefix(const PrefixParams& P, cudaStream_t s);
 cudaError_t launch_downsample(const DownsampleParams& P, cudaStream_t s);
@@ -252,6 +263,8 @@ cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bo
                           cudaStream_t s);
 cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s);
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s);
+cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s);
+constexpr int kNormaliseBlocks = 1216;  // 8 CTAs per SM
 
 // Launch accounting (ffa_api.cu): brackets one launch with profiling events.
 struct LaunchScope {

@@ -919,6 +919,68 @@ __global__ void __launch_bounds__(256, 2) boxcar_snr_kernel(SnrParams P) {
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Normalisation (Sec. 3.1, Sec. 5.2): mean and standard deviation of the whole series
+// in FP64 (two passes: sum, then sum of squared deviations), then every sample becomes
+// (x - mean) / std, rounded to the storage type: float, half, or int8 q with value q/16
+// (q = rint(16 x'), clipped to [-128, 127]).  Reduction order is fixed (grid size and
+// block shape constant), so results are deterministic.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum_f64(double v, double* sh) {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+// mode 0: partial sums of x; mode 1: partial sums of (x - mean)^2
+__global__ void __launch_bounds__(256) normalise_partial_kernel(NormaliseParams P, int mode) {
+    __shared__ double sh[8];
+    const double mean = mode ? P.stats[0] : 0.0;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = (double)P.x[i] - mean;
+        acc += mode ? d * d : d;
+    }
+    const double t = block_sum_f64(acc, sh);
+    if (threadIdx.x == 0) P.partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(256) normalise_final_kernel(NormaliseParams P, int mode) {
+    __shared__ double sh[8];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < P.nblocks; b += blockDim.x) acc += P.partial[b];
+    const double t = block_sum_f64(acc, sh);
+    if (threadIdx.x == 0) {
+        if (mode == 0) P.stats[0] = t / (double)P.n;
+        else P.stats[1] = sqrt(t / (double)P.n);
+    }
+}
+
+__global__ void __launch_bounds__(256) normalise_write_kernel(NormaliseParams P) {
+    const double mean = P.stats[0];
+    const double sd = P.stats[1];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = sd > 0.0 ? ((double)P.x[i] - mean) / sd : 0.0;
+        if (P.out_dtype == 0) {
+            static_cast<float*>(P.out)[i] = (float)v;
+        } else if (P.out_dtype == 1) {
+            static_cast<__half*>(P.out)[i] = __double2half(v);
+        } else {
+            double q = rint(16.0 * v);
+            q = q < -128.0 ? -128.0 : (q > 127.0 ? 127.0 : q);
+            static_cast<signed char*>(P.out)[i] = (signed char)q;
+        }
+    }
+}
+
 // Raises a kernel's dynamic shared memory limit once per device (to the CTA maximum
 // minus the kernel's static shared memory).  A failure is left for the launch check.
 void allow_max_smem(const void* func, int slot) {
@@ -996,6 +1058,32 @@ cudaError_t launch_snr(const SnrParams& P, cudaStream_t s) {
     allow_max_smem((const void*)boxcar_snr_kernel, 3);
     LaunchScope ls(kBoxcarSnr, 4.0 * (double)P.rows * (P.cols + P.widths.nw), s);
     boxcar_snr_kernel<<<(unsigned)blocks, 256, smem, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s) {
+    // algorithmic bytes: three reads of x (sum, deviations, write pass) and the output
+    const double out_bytes = P.out_dtype == 0 ? 4.0 : (P.out_dtype == 1 ? 2.0 : 1.0);
+    {
+        LaunchScope ls(kNormalise, 4.0 * P.n, s);
+        normalise_partial_kernel<<<P.nblocks, 256, 0, s>>>(P, 0);
+    }
+    {
+        LaunchScope ls(kNormalise, 8.0 * P.nblocks, s);
+        normalise_final_kernel<<<1, 256, 0, s>>>(P, 0);
+    }
+    {
+        LaunchScope ls(kNormalise, 4.0 * P.n, s);
+        normalise_partial_kernel<<<P.nblocks, 256, 0, s>>>(P, 1);
+    }
+    {
+        LaunchScope ls(kNormalise, 8.0 * P.nblocks, s);
+        normalise_final_kernel<<<1, 256, 0, s>>>(P, 1);
+    }
+    {
+        LaunchScope ls(kNormalise, (4.0 + out_bytes) * P.n, s);
+        normalise_write_kernel<<<P.nblocks, 256, 0, s>>>(P);
+    }
     return cudaGetLastError();
 }
 
