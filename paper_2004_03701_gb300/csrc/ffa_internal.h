@@ -30,8 +30,14 @@ constexpr int kBottomSmemBytes = FFA_BOTTOM_SMEM;
 constexpr int kTopSmemBytes = FFA_TOP_SMEM;
 constexpr int kBottomMinBlocks = FFA_BOTTOM_MINB;  // resident CTAs per SM to allow for
 constexpr int kTopMinBlocks = FFA_TOP_MINB;
-constexpr int kBottomThreads = 512;  // CTA of the shared-memory sub-tree kernel
-constexpr int kTopThreads = 512;     // CTA of the gathered top-level kernel
+#ifndef FFA_BOTTOM_THREADS
+#define FFA_BOTTOM_THREADS 512
+#endif
+#ifndef FFA_TOP_THREADS
+#define FFA_TOP_THREADS 512
+#endif
+constexpr int kBottomThreads = FFA_BOTTOM_THREADS;  // CTA of the shared-memory sub-tree kernel
+constexpr int kTopThreads = FFA_TOP_THREADS;        // CTA of the gathered top-level kernel
 constexpr int kTopMaxLevels = 3;     // merge levels per top pass
 constexpr int kTopMaxRows = 128;     // output rows per top CTA
 
@@ -92,14 +98,9 @@ struct TopLayout {
 };
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 
-// Prefix-sum rows of the boxcar S/N of a p-bin profile: S[0 .. 64 ceil(p/64) + wmax]
-// and the same row shifted by one (so that every pair S[j], S[j+1] is 8-byte aligned in
-// one of the two), each snr_half floats.
-__host__ __device__ inline int snr_half(int p, int wmax) {
-    return round4(((p + 63) & ~63) + wmax + 2);
-}
+// Prefix-sum row of the boxcar S/N of a p-bin profile: S[0 .. 32 ceil(p/32) + wmax].
 __host__ __device__ inline int snr_warp_floats(int p, int wmax) {
-    return 2 * snr_half(p, wmax);
+    return round4(((p + 31) & ~31) + wmax + 1);
 }
 
 // Shared-memory layout (in floats) of a sub-tree CTA: barrier, two row-descriptor

@@ -272,28 +272,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 // ---------------------------------------------------------------------------------
 constexpr int kSnrMaxSlots = 17;
 
-// d = a - b on two lanes of a float pair (packed f32x2 subtract, round to nearest).
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
-        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-// max of three floats in one instruction.
-__device__ __forceinline__ float max3(float a, float b, float c) {
-    float r;
-    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
-
 template <int T>
 __device__ __forceinline__ void snr_from_regs(const float (&v)[T], int p, float* S,
                                               const Widths& W, float inv_std, float* out,
                                               int lane) {
-    constexpr int T2 = (T + 1) / 2;  // pairs of phases per lane: k = 2 lane + 64 u
-    float* S1 = S + snr_half(p, W.wmax);  // S1[i] = S[i + 1]
     float carry = 0.f;
 #pragma unroll
     for (int t = 0; t < T; ++t) {
@@ -304,31 +286,21 @@ __device__ __forceinline__ void snr_from_regs(const float (&v)[T], int p, float*
             if (lane >= o) inc += u;
         }
         const int x = lane + 32 * t;
-        if (x < p) {
-            const float sx = carry + inc;
-            S[x + 1] = sx;
-            S1[x] = sx;
-        }
+        if (x < p) S[x + 1] = carry + inc;
         carry += __shfl_sync(kFull, inc, 31);
     }
     if (lane == 0) S[0] = 0.f;
     __syncwarp();
     const float total = S[p];
-    const int jmax = 64 * T2 - 1 + W.wmax - p;  // S is read up to index 64 T2 - 1 + wmax
-    for (int j = lane + 1; j <= jmax; j += 32) {
-        const float sv = j <= p ? total + S[j] : 0.f;  // second repeat; finite padding beyond
-        S[p + j] = sv;
-        S1[p + j - 1] = sv;
-    }
+    const int jmax = 32 * T - 1 + W.wmax - p;  // S is read up to index 32 T - 1 + wmax
+    for (int j = lane + 1; j <= jmax; j += 32)
+        S[p + j] = j <= p ? total + S[j] : 0.f;  // second repeat; finite padding beyond
     __syncwarp();
-    float2 sk[T2];
+    float sk[T];
 #pragma unroll
-    for (int u = 0; u < T2; ++u) {
-        const int k = 2 * lane + 64 * u;
-        float2 s = *reinterpret_cast<const float2*>(S + k);
-        if (k >= p) s.x = INFINITY;  // padding phases never win
-        if (k + 1 >= p) s.y = INFINITY;
-        sk[u] = s;
+    for (int t = 0; t < T; ++t) {
+        const int x = lane + 32 * t;
+        sk[t] = x < p ? S[x] : INFINITY;
     }
     // 16 widths at a time: per-lane maxima, then one transposed butterfly reduction
     // (16 shuffles for 16 widths); afterwards lane pair (2v, 2v+1) holds width v.
@@ -338,13 +310,9 @@ __device__ __forceinline__ void snr_from_regs(const float (&v)[T], int p, float*
         for (int i = 0; i < 16; ++i) {
             b[i] = -INFINITY;
             if (w0 + i < W.nw) {
-                const int w = W.w[w0 + i];
-                const float* base = ((w & 1) ? S1 + (w - 1) : S + w) + 2 * lane;  // 8-byte aligned
+                const float* Sw = S + W.w[w0 + i] + lane;
 #pragma unroll
-                for (int u = 0; u < T2; ++u) {
-                    const float2 d = sub2(*reinterpret_cast<const float2*>(base + 64 * u), sk[u]);
-                    b[i] = max3(b[i], d.x, d.y);
-                }
+                for (int t = 0; t < T; ++t) b[i] = fmaxf(b[i], Sw[32 * t] - sk[t]);
             }
         }
         const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
@@ -368,9 +336,9 @@ __device__ __forceinline__ void snr_from_regs(const float (&v)[T], int p, float*
             b[0] = fmaxf(keep, __shfl_xor_sync(kFull, send, 2));
         }
         b[0] = fmaxf(b[0], __shfl_xor_sync(kFull, b[0], 1));
-        const int vi = (h16 ? 8 : 0) + (h8 ? 4 : 0) + (h4 ? 2 : 0) + (h2 ? 1 : 0);
-        if ((lane & 1) == 0 && w0 + vi < W.nw)
-            out[w0 + vi] = b[0] * inv_std * W.inv_sqrt_w[w0 + vi];
+        const int v = (h16 ? 8 : 0) + (h8 ? 4 : 0) + (h4 ? 2 : 0) + (h2 ? 1 : 0);
+        if ((lane & 1) == 0 && w0 + v < W.nw)
+            out[w0 + v] = b[0] * inv_std * W.inv_sqrt_w[w0 + v];
     }
     __syncwarp();
 }
@@ -814,29 +782,6 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
     }
     __syncthreads();
 
-    // ---- row descriptors {out, head row, tail row, shift} for levels L-1 .. 0
-    int4* desc = reinterpret_cast<int4*>(smem + lay.desc);
-    const int ndesc = lvl_desc[L];
-    for (int q = tid; q < ndesc; q += kTopThreads) {
-        int l = L - 1;
-        while (q >= lvl_desc[L - l]) --l;  // level of descriptor q
-        int r = q - lvl_desc[L - 1 - l];
-        int e = (1 << l) - 1;
-        while (r > tab[8 * e + 3] - tab[8 * e + 2]) {
-            r -= tab[8 * e + 3] - tab[8 * e + 2] + 1;
-            ++e;
-        }
-        const int s = tab[8 * e + 2] + r;
-        const Split sp = merge_split(tab[8 * e + 1], s);
-        const int eh = 2 * e + 1, et = 2 * e + 2;
-        int4 d;
-        d.x = tab[8 * e + 4] + r * p;
-        d.y = tab[8 * eh + 4] + (sp.i - tab[8 * eh + 2]) * p;
-        d.z = tab[8 * et + 4] + (sp.j - tab[8 * et + 2]) * p;
-        d.w = sp.shift % p;
-        desc[q] = d;
-    }
-
     // ---- gather the needed rows of the depth-d_in transforms: one bulk copy per interval,
     //      all counted by a single arrival on the barrier
     unsigned bytes = 0;
@@ -859,6 +804,30 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
         load_row_ends(smem, tab[8 * e + 4], g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p, tid,
                       kTopThreads);
     }
+    // ---- row descriptors {out, head row, tail row, shift} for levels L-1 .. 0, made
+    //      while the bulk copies are in flight
+    int4* desc = reinterpret_cast<int4*>(smem + lay.desc);
+    const int ndesc = lvl_desc[L];
+    for (int q = tid; q < ndesc; q += kTopThreads) {
+        int l = L - 1;
+        while (q >= lvl_desc[L - l]) --l;  // level of descriptor q
+        int r = q - lvl_desc[L - 1 - l];
+        int e = (1 << l) - 1;
+        while (r > tab[8 * e + 3] - tab[8 * e + 2]) {
+            r -= tab[8 * e + 3] - tab[8 * e + 2] + 1;
+            ++e;
+        }
+        const int s = tab[8 * e + 2] + r;
+        const Split sp = merge_split(tab[8 * e + 1], s);
+        const int eh = 2 * e + 1, et = 2 * e + 2;
+        int4 d;
+        d.x = tab[8 * e + 4] + r * p;
+        d.y = tab[8 * eh + 4] + (sp.i - tab[8 * eh + 2]) * p;
+        d.z = tab[8 * et + 4] + (sp.j - tab[8 * et + 2]) * p;
+        d.w = sp.shift % p;
+        desc[q] = d;
+    }
+
     const bool landed = bytes == 0 || mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
@@ -909,7 +878,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
 }
 
 // Standalone boxcar S/N of stored profiles: one warp per row.
-__global__ void __launch_bounds__(256, 2) boxcar_snr_kernel(SnrParams P) {
+__global__ void __launch_bounds__(256) boxcar_snr_kernel(SnrParams P) {
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* S = smem + warp * P.warp_floats;
