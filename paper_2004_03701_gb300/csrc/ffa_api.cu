@@ -122,6 +122,8 @@ struct Plan {
     std::vector<OctaveDesc> oct;
     std::vector<TransformDesc> trs;
     std::vector<WorkItem> items;
+    std::vector<int> top_tables;  // kTopTableInts per top-pass item (WorkItem::pad)
+    std::vector<int2> ds_blocks;  // downsampling CTAs: {octave, first output}
     int64_t bottom0_off = 0, bottom0_cnt = 0;
     int bottom0_smem = 0, bottom0_nmax = 0, bottom0_elems = 0, bottom0_snr_warps = 0;
     int bottom0_snr_floats = 0;
@@ -132,7 +134,8 @@ struct Plan {
     int max_rows = 0, max_p = 0;
     int64_t nchunks = 0;
     // workspace layout (bytes)
-    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, tables_bytes = 0;
+    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, o_toptab = 0, o_dsblk = 0;
+    size_t tables_bytes = 0;
     size_t o_prefix = 0, o_partial = 0, o_ds = 0, o_s0 = 0, o_s1 = 0, ws_bytes = 0;
     size_t o_hx = 0, o_hper = 0, o_hfb = 0, o_hsnr = 0, ws_host_bytes = 0;
     void* pinned = nullptr;
@@ -234,6 +237,11 @@ ffa_status build_plan(Plan& pl) {
     }
     pl.ds_total = first;
     pl.ds_floats = ds_off;
+    for (size_t k = 0; k < pl.oct.size(); ++k)
+        for (int64_t s = 0; s < pl.oct[k].nk; s += kDownsamplePerBlock) {
+            if (s > INT32_MAX) return fail(FFA_ERR_UNSUPPORTED, "octave too long");
+            pl.ds_blocks.push_back(make_int2((int)k, (int)s));
+        }
     // Transforms in (octave, p) order (Sec. 5.3, Fig. 4).
     int64_t trial = 0;
     for (size_t k = 0; k < pl.oct.size(); ++k) {
@@ -333,8 +341,22 @@ ffa_status build_plan(Plan& pl) {
                 const int lim = score ? d.kept : nmax;
                 const int nb = (lim + K - 1) / K;
                 const int cnt = score ? nb : (1 << dout) * nb;
-                for (int i = 0; i < cnt; ++i)
-                    pl.items.push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, 0});
+                for (int i = 0; i < cnt; ++i) {
+                    // the item's target node and row block, as the kernel derives them
+                    const int node = i / nb, blk = i - node * nb;
+                    int st0 = 0, n0 = d.m;
+                    for (int b = dout - 1; b >= 0; --b) {
+                        const int nh = n0 >> 1;
+                        if ((node >> b) & 1) { st0 += nh; n0 -= nh; } else { n0 = nh; }
+                    }
+                    const int lo0 = blk * K;
+                    const int hi0 = std::min(lo0 + K, score ? d.kept : n0) - 1;
+                    const int tix = (int)(pl.top_tables.size() / kTopTableInts);
+                    pl.top_tables.resize(pl.top_tables.size() + kTopTableInts, 0);
+                    if (lo0 <= hi0)
+                        top_intervals(st0, n0, lo0, hi0, L, pl.top_tables.data() + (size_t)tix * kTopTableInts);
+                    pl.items.push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, tix});
+                }
                 s.bytes += 4.0 * d.m * d.p + (score ? out_row_bytes * d.kept : 4.0 * d.m * d.p);
             }
             s.cnt = (int64_t)pl.items.size() - s.off;
@@ -369,6 +391,10 @@ ffa_status build_plan(Plan& pl) {
     o = align_up(o + pl.trs.size() * sizeof(TransformDesc), 256);
     pl.o_items = o;
     o = align_up(o + pl.items.size() * sizeof(WorkItem), 256);
+    pl.o_toptab = o;
+    o = align_up(o + pl.top_tables.size() * sizeof(int), 256);
+    pl.o_dsblk = o;
+    o = align_up(o + pl.ds_blocks.size() * sizeof(int2), 256);
     pl.tables_bytes = std::max<size_t>(o, 256);
 
     // Workspace: status | tables | prefix | chunk sums | series | scratch 0 | scratch 1
@@ -413,6 +439,8 @@ ffa_status ensure_pinned(Plan& pl) {
     std::memcpy(h + pl.o_oct, pl.oct.data(), pl.oct.size() * sizeof(OctaveDesc));
     std::memcpy(h + pl.o_trs, pl.trs.data(), pl.trs.size() * sizeof(TransformDesc));
     std::memcpy(h + pl.o_items, pl.items.data(), pl.items.size() * sizeof(WorkItem));
+    std::memcpy(h + pl.o_toptab, pl.top_tables.data(), pl.top_tables.size() * sizeof(int));
+    std::memcpy(h + pl.o_dsblk, pl.ds_blocks.data(), pl.ds_blocks.size() * sizeof(int2));
     pl.pinned = p;
     return FFA_OK;
 }
@@ -489,7 +517,8 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     dp.n = pl.n;
     dp.prefix = prefix;
     dp.oct = d_oct;
-    dp.noct = (int)pl.oct.size();
+    dp.blocks = reinterpret_cast<const int2*>(ws + pl.o_tables + pl.o_dsblk);
+    dp.nblocks = (int)pl.ds_blocks.size();
     dp.total = pl.ds_total;
     dp.out = ds;
     FFA_CUDA(launch_downsample(dp, st), "downsample launch");
@@ -537,6 +566,7 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
             tp.foldbins = d_foldbins;
             tp.snr = d_snr;
             tp.status = status;
+            tp.tables = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_toptab);
             LaunchScope ls(kFfaTop, sg.bytes, st);
             FFA_CUDA(launch_top(tp, (int)sg.cnt, sg.smem, st), "ffa_top launch");
         }
@@ -647,7 +677,10 @@ ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_o
     dp.n = n;
     dp.prefix = prefix;
     dp.oct = nullptr;
-    dp.noct = 1;
+    dp.blocks = nullptr;
+    if ((nk + kDownsamplePerBlock - 1) / kDownsamplePerBlock > INT32_MAX)
+        return fail(FFA_ERR_UNSUPPORTED, "series too long");
+    dp.nblocks = (int)((nk + kDownsamplePerBlock - 1) / kDownsamplePerBlock);
     dp.total = nk;
     dp.out = d_out;
     dp.single.nk = nk;

@@ -45,6 +45,46 @@ constexpr int kTopMaxRows = 128;     // output rows per top CTA
 constexpr unsigned kDevTimeout = 1u;
 constexpr unsigned kDevBadItem = 2u;
 
+// nint(a / d), ties up, for a >= 0, d > 0 (Sec. 2.2: i and j of the merge rule).
+__host__ __device__ inline int nint_div(long long a, long long d) {
+    long long num = 2 * a + d, den = 2 * d;
+    if (num < 4294967296LL) return (int)((unsigned)num / (unsigned)den);
+    return (int)(num / den);
+}
+
+// Merge rule for output row s of an n-row node: head row i, tail row j, shift i + b.
+struct Split {
+    int i, j, shift;
+};
+__host__ __device__ inline Split merge_split(int n, int s) {
+    int nh = n >> 1, nt = n - nh;
+    Split r;
+    r.i = nint_div((long long)(nh - 1) * s, n - 1);
+    r.j = nint_div((long long)(nt - 1) * s, n - 1);
+    r.shift = s - r.j;  // i + b = s - j
+    return r;
+}
+
+// Interval table of a top-pass work item, heap order (node e at level l is 2^l - 1 + j,
+// children 2e + 1 and 2e + 2): per node {absolute start row, rows, lo, hi}, where rows
+// lo..hi of the node are the ones the item needs.  Node 0 is the output block.
+constexpr int kTopTableInts = 64;
+__host__ __device__ inline void top_intervals(int st0, int n0, int lo0, int hi0, int L, int* t) {
+    t[0] = st0; t[1] = n0; t[2] = lo0; t[3] = hi0;
+    for (int l = 0; l < L; ++l) {
+        for (int j = 0; j < (1 << l); ++j) {
+            const int e = (1 << l) - 1 + j;
+            const int st = t[4 * e], n = t[4 * e + 1], lo = t[4 * e + 2], hi = t[4 * e + 3];
+            const int nh = n >> 1;
+            const Split a = merge_split(n, lo), z = merge_split(n, hi);
+            int* h = t + 4 * (2 * e + 1);
+            int* q = t + 4 * (2 * e + 2);
+            h[0] = st; h[1] = nh; h[2] = a.i; h[3] = z.i;
+            q[0] = st + nh; q[1] = n - nh; q[2] = a.j; q[3] = z.j;
+        }
+    }
+}
+
 // One FFA transform of a search: base period p (bins), m rows of the octave series.
 struct TransformDesc {
     int64_t src_off;      // float offset of row 0 in the source buffer
@@ -192,6 +232,9 @@ struct PrefixParams {
     int64_t nchunks;
 };
 
+constexpr int kDownsampleThreads = 256;
+constexpr int kDownsamplePerBlock = 1024;  // output samples per CTA (4 per thread)
+
 struct DownsampleParams {
     const void* x;
     int dtype;
@@ -199,8 +242,9 @@ struct DownsampleParams {
     const float2* prefix;
     const OctaveDesc* oct;          // null: one octave, `single`
     OctaveDesc single;
-    int noct;
-    int64_t total;        // sum of nk
+    const int2* blocks;             // per CTA: {octave, first output}; null: octave 0
+    int nblocks;
+    int64_t total;        // sum of nk (algorithmic accounting)
     float* out;           // series buffer
 };
 
@@ -233,6 +277,7 @@ struct TopParams {
     int32_t* foldbins;
     float* snr;                     // null: the last pass stores the transform instead
     unsigned* status;
+    const int* tables;              // per-item interval tables (WorkItem::pad), or null
     int single_pass;                // pass and rows per block when items is null
     int single_rows;
 };

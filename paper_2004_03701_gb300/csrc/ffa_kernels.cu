@@ -35,26 +35,6 @@ constexpr unsigned kFull = 0xffffffffu;
 // ceil(log2(n)): the number of merge levels above an n-row block (0 for n = 1).
 __device__ __forceinline__ int tree_height(int n) { return n <= 1 ? 0 : 32 - __clz(n - 1); }
 
-// nint(a / d), ties up, for a >= 0, d > 0 (Sec. 2.2: i and j of the merge rule).
-__device__ __forceinline__ int nint_div(long long a, long long d) {
-    long long num = 2 * a + d, den = 2 * d;
-    if (num < 4294967296LL) return (int)((unsigned)num / (unsigned)den);
-    return (int)(num / den);
-}
-
-// Merge rule for output row s of an n-row node: head row i, tail row j, shift i + b.
-struct Split {
-    int i, j, shift;
-};
-__device__ __forceinline__ Split merge_split(int n, int s) {
-    int nh = n >> 1, nt = n - nh;
-    Split r;
-    r.i = nint_div((long long)(nh - 1) * s, n - 1);
-    r.j = nint_div((long long)(nt - 1) * s, n - 1);
-    r.shift = s - r.j;  // i + b = s - j
-    return r;
-}
-
 // ---------------------------------------------------------------------------------
 // Double-float ("float2" = hi + lo) arithmetic: Knuth's two-sum, ~48-bit significand.
 // ---------------------------------------------------------------------------------
@@ -178,16 +158,17 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_final_kernel(PrefixPara
 //   out = (S[floor B] - S[floor A]) - frac(A) x[floor A] + frac(B) x[floor B],
 // S the exclusive prefix sum.  A and B are exact in 64.64 fixed point.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) downsample_kernel(DownsampleParams P) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P.total; g += stride) {
-        int lo = 0, hi = P.oct ? P.noct - 1 : 0;  // last octave with first <= g
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (P.oct[mid].first <= g) lo = mid; else hi = mid - 1;
-        }
-        const OctaveDesc od = P.oct ? P.oct[lo] : P.single;
-        const uint64_t i = (uint64_t)(g - od.first);
+// Each CTA covers up to kDownsamplePerBlock consecutive outputs of one octave (the plan
+// assigns CTAs to octaves), four per thread at a stride of the CTA size.
+__global__ void __launch_bounds__(kDownsampleThreads) downsample_kernel(DownsampleParams P) {
+    const int2 bi = P.blocks ? P.blocks[blockIdx.x]
+                             : make_int2(0, (int)blockIdx.x * kDownsamplePerBlock);
+    const OctaveDesc od = P.oct ? P.oct[bi.x] : P.single;
+#pragma unroll
+    for (int q = 0; q < kDownsamplePerBlock / kDownsampleThreads; ++q) {
+        const int64_t i64 = (int64_t)bi.y + q * kDownsampleThreads + threadIdx.x;
+        if (i64 >= od.nk) break;
+        const uint64_t i = (uint64_t)i64;
         float out;
         if (od.f_int == 1 && od.f_frac == 0) {
             out = load_sample(P.x, P.dtype, (int64_t)i);
@@ -210,7 +191,7 @@ __global__ void __launch_bounds__(256) downsample_kernel(DownsampleParams P) {
                 out = __fadd_rn(out, __fmul_rn(be, load_sample(P.x, P.dtype, (int64_t)b_int)));
             }
         }
-        P.out[od.out_off + (int64_t)i] = out;
+        P.out[od.out_off + i64] = out;
     }
 }
 
@@ -733,49 +714,55 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
 
     // ---- interval table, heap order: node e at level l is e = 2^l - 1 + j.
     //      per node: [0] abs start row, [1] size, [2] lo, [3] hi, [4] smem offset of row lo
-    //      Built by warp 0, one lane per node of a level.
+    //      Intervals come precomputed with the plan (or are built here for a single
+    //      transform); warp 0 lays them out in shared memory with prefix sums.
     int* tab = reinterpret_cast<int*>(smem + lay.table);
     int* lvl_desc = tab + 120;  // first descriptor of each level, levels L-1..0, + end
+    const int nnodes = (2 << L) - 1;
+    if (P.tables) {
+        const int* src = P.tables + (int64_t)item.pad * kTopTableInts;
+        if (tid < 4 * nnodes) tab[8 * (tid >> 2) + (tid & 3)] = src[tid];
+    } else if (tid == 0) {
+        int t4[4 * 15];
+        top_intervals(st0, n0, lo0, hi0, L, t4);
+        for (int e = 0; e < nnodes; ++e)
+            for (int c = 0; c < 4; ++c) tab[8 * e + c] = t4[4 * e + c];
+    }
+    __syncthreads();
     if (warp == 0) {
-        if (lane == 0) {
-            tab[0] = st0; tab[1] = n0; tab[2] = lo0; tab[3] = hi0;
-        }
-        __syncwarp();
-        for (int l = 0; l < L; ++l) {
-            if (lane < (1 << l)) {
-                const int e = (1 << l) - 1 + lane;
-                const int st = tab[8 * e], n = tab[8 * e + 1], lo = tab[8 * e + 2], hi = tab[8 * e + 3];
-                const int nh = n >> 1;
-                const Split a = merge_split(n, lo), z = merge_split(n, hi);
-                const int eh = 2 * e + 1, et = 2 * e + 2;
-                tab[8 * eh] = st; tab[8 * eh + 1] = nh; tab[8 * eh + 2] = a.i; tab[8 * eh + 3] = z.i;
-                tab[8 * et] = st + nh; tab[8 * et + 1] = n - nh; tab[8 * et + 2] = a.j;
-                tab[8 * et + 3] = z.j;
-            }
-            __syncwarp();
-        }
-        if (lane == 0) {
-            // offsets: level L with alignment slack (buffer A), the others compact
-            int off = lay.buf_a;
-            for (int j = 0; j < (1 << L); ++j) {
-                const int e = (1 << L) - 1 + j;
+        // level L: each interval in a 16-byte-aligned region, data at +h so that the bulk
+        // copy of its aligned interior lands aligned
+        {
+            const int j = lane, e = (1 << L) - 1 + j;
+            int h = 0, region = 0;
+            if (j < (1 << L)) {
                 const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
-                const int h = (int)((reinterpret_cast<uintptr_t>(g) >> 2) & 3);
-                tab[8 * e + 4] = off + h;
-                off = round4(off + h + (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p);
+                h = (int)((reinterpret_cast<uintptr_t>(g) >> 2) & 3);
+                region = round4(h + (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p);
             }
-            int nd = 0;
-            for (int l = L - 1; l >= 0; --l) {
-                int o = (((L - l) & 1) == 0) ? lay.buf_a : lay.buf_b;
-                lvl_desc[L - 1 - l] = nd;
-                for (int j = 0; j < (1 << l); ++j) {
-                    const int e = (1 << l) - 1 + j;
-                    tab[8 * e + 4] = o;
-                    const int rows = tab[8 * e + 3] - tab[8 * e + 2] + 1;
-                    o += rows * p;
-                    nd += rows;
-                }
+            int inc = region;
+            for (int o = 1; o < 8; o <<= 1) {
+                const int u = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += u;
             }
+            if (j < (1 << L)) tab[8 * e + 4] = lay.buf_a + inc - region + h;
+        }
+        // levels L-1 .. 0: compact, one row after another
+        int nd = 0;
+        for (int l = L - 1; l >= 0; --l) {
+            const int base = (((L - l) & 1) == 0) ? lay.buf_a : lay.buf_b;
+            const int j = lane, e = (1 << l) - 1 + j;
+            const int rows = j < (1 << l) ? tab[8 * e + 3] - tab[8 * e + 2] + 1 : 0;
+            int inc = rows;
+            for (int o = 1; o < 4; o <<= 1) {
+                const int u = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += u;
+            }
+            if (j < (1 << l)) tab[8 * e + 4] = base + (inc - rows) * p;
+            if (lane == 0) lvl_desc[L - 1 - l] = nd;
+            nd += __shfl_sync(kFull, inc, (1 << l) - 1);
+        }
+        if (lane == 0) {
             lvl_desc[L] = nd;
             mbar_init(bar, 1);
         }
@@ -990,12 +977,10 @@ cudaError_t launch_prefix(const PrefixParams& P, cudaStream_t s) {
 }
 
 cudaError_t launch_downsample(const DownsampleParams& P, cudaStream_t s) {
-    if (P.total <= 0) return cudaSuccess;
-    int64_t blocks = (P.total + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (P.total <= 0 || P.nblocks <= 0) return cudaSuccess;
     // per output: two prefix lookups (8 B each), up to two samples, one store
     LaunchScope ls(kDownsample, 28.0 * (double)P.total, s);
-    downsample_kernel<<<(unsigned)blocks, 256, 0, s>>>(P);
+    downsample_kernel<<<(unsigned)P.nblocks, kDownsampleThreads, 0, s>>>(P);
     return cudaGetLastError();
 }
 
