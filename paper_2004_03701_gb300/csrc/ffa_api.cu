@@ -69,7 +69,8 @@ ProfAcc g_acc[kNumKinds];
 
 const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top",     "prefix_final",
                                      "downsample",     "ffa_bottom",     "ffa_bottom_snr",
-                                     "ffa_top",        "boxcar_snr",     "normalise"};
+                                     "ffa_top",        "boxcar_snr",     "normalise",
+                                     "ffa_persistent"};
 
 cudaEvent_t pool_get() {
     if (!g_pool.empty()) {
@@ -99,18 +100,6 @@ void drain_pending() {
 // ---------------------------------------------------------------------------------
 // Search plan.
 // ---------------------------------------------------------------------------------
-struct Stage {              // one top-kernel launch: pass j of every transform that has it
-    int64_t off = 0, cnt = 0;
-    int smem = 0;
-    double bytes = 0;
-};
-struct Group {
-    int64_t bottom_off = 0, bottom_cnt = 0;
-    int bottom_smem = 0, bottom_nmax = 0, bottom_elems = 0;
-    double bottom_bytes = 0;
-    std::vector<Stage> stages;
-};
-
 struct Plan {
     // parameters
     int64_t n = 0;
@@ -124,17 +113,20 @@ struct Plan {
     std::vector<WorkItem> items;
     std::vector<int> top_tables;  // kTopTableInts per top-pass item (WorkItem::pad)
     std::vector<int2> ds_blocks;  // downsampling CTAs: {octave, first output}
-    int64_t bottom0_off = 0, bottom0_cnt = 0;
-    int bottom0_smem = 0, bottom0_nmax = 0, bottom0_elems = 0, bottom0_snr_warps = 0;
+    int bottom0_nmax = 0, bottom0_elems = 0, bottom0_snr_warps = 0;
     int bottom0_snr_floats = 0;
     int row_cap = kBottomMaxRows;  // sub-tree row limit (lowered if a launch's mix overflows)
-    double bottom0_bytes = 0;
-    std::vector<Group> groups;
+    std::vector<int> stage_count;
+    int bottom_nmax = 0, bottom_elems = 0;
+    int smem_floats = 0;
+    int nitems = 0;
+    double ffa_bytes = 0;
+    size_t o_counters = 0, counter_bytes = 0;
     int64_t ntrials = 0, ds_total = 0, ds_floats = 0, scratch_floats = 0, folded = 0;
     int max_rows = 0, max_p = 0;
     int64_t nchunks = 0;
     // workspace layout (bytes)
-    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, o_toptab = 0, o_dsblk = 0;
+    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, o_toptab = 0, o_dsblk = 0, o_stcnt = 0;
     size_t tables_bytes = 0;
     size_t o_prefix = 0, o_partial = 0, o_ds = 0, o_s0 = 0, o_s1 = 0, ws_bytes = 0;
     size_t o_hx = 0, o_hper = 0, o_hfb = 0, o_hsnr = 0, ws_host_bytes = 0;
@@ -147,13 +139,14 @@ struct Plan {
 constexpr size_t kStatusBytes = 256;
 constexpr ffa_status kRetrySmaller = -1;  // internal: a launch's sub-tree mix overflows
 std::mutex g_plan_mu;
-constexpr int64_t kGroupFloats = int64_t(6) << 20;  // 24 MB per scratch buffer (L2-resident)
+constexpr int64_t kBatchFloats = int64_t(6) << 20;  // folded samples per batch of transforms
 
 // Rows of one shared-memory sub-tree of p bins: the most (at most row_cap) whose
 // layout fits in shared memory.
 int max_subtree_rows(int p, int row_cap) {
     int n = std::min(row_cap, kBottomMaxRows);
-    while (n > 1 && bottom_layout(n, n * p, 0).total * 4 > kBottomSmemBytes) --n;
+    // + 16 bytes: the persistent kernel's queue slot after the layout
+    while (n > 1 && bottom_layout(n, n * p, 0).total * 4 + 16 > kBottomSmemBytes) --n;
     return std::max(n, 1);
 }
 int depth_for(int m, int p, int row_cap = kBottomMaxRows) {
@@ -166,7 +159,7 @@ int depth_for(int m, int p, int row_cap = kBottomMaxRows) {
 // Rows per top-kernel CTA: the most that fit in shared memory (at most kTopMaxRows).
 int top_rows(int p, int L, bool score, int wmax) {
     for (int K = kTopMaxRows; K >= 1; --K)
-        if (top_layout(K, L, p, wmax, score).total * 4 <= kTopSmemBytes) return K;
+        if (top_layout(K, L, p, wmax, score).total * 4 + 16 <= kTopSmemBytes) return K;
     return 0;
 }
 
@@ -279,64 +272,74 @@ ffa_status build_plan(Plan& pl) {
     const int nw = pl.W.nw;
     const double out_row_bytes = 4.0 * nw + 12.0;
 
-    // Whole-tree-in-shared-memory transforms: one launch, fused S/N.
-    pl.bottom0_off = (int64_t)pl.items.size();
+    // ---- persistent work queue.  Whole-tree transforms (scored inside one CTA) come
+    //      first; the others are cut into batches of consecutive transforms, and the
+    //      stages of the batches (sub-trees, then top passes) are listed along
+    //      diagonals, so that an item's inputs were listed about one batch-stage earlier.
+    pl.stage_count.assign(pl.trs.size() * kMaxStages, 0);
     int p0 = 0;
     for (size_t t = 0; t < pl.trs.size(); ++t) {
         const TransformDesc& d = pl.trs[t];
         if (d.depth != 0) continue;
-        pl.items.push_back(WorkItem{(int32_t)t, 0, 0, 0, 0});
+        pl.items.push_back(WorkItem{(int32_t)t, 0, -2, 0, 0});
+        pl.stage_count[t * kMaxStages] = 1;
         pl.bottom0_nmax = std::max(pl.bottom0_nmax, d.m);
         pl.bottom0_elems = std::max(pl.bottom0_elems, d.m * d.p);
         p0 = std::max(p0, d.p);
-        pl.bottom0_bytes += 4.0 * d.m * d.p + out_row_bytes * d.kept;
+        pl.ffa_bytes += 4.0 * d.m * d.p + out_row_bytes * d.kept;
     }
-    pl.bottom0_cnt = (int64_t)pl.items.size() - pl.bottom0_off;
-    if (pl.bottom0_cnt) {
+    if (pl.bottom0_nmax) {
         const int per_warp = snr_warp_floats(p0, wmax);
         const BottomLayout l0 = bottom_layout(pl.bottom0_nmax, pl.bottom0_elems, 0);
         pl.bottom0_snr_warps = std::min(kBottomThreads / 32, l0.buf_floats / per_warp);
         if (pl.bottom0_snr_warps < 1) pl.bottom0_snr_warps = 1;
         pl.bottom0_snr_floats = pl.bottom0_snr_warps * per_warp;
-        pl.bottom0_smem =
-            bottom_layout(pl.bottom0_nmax, pl.bottom0_elems, pl.bottom0_snr_floats).total * 4;
-        if (pl.bottom0_smem > kSmemBytes) return kRetrySmaller;
+        pl.smem_floats = std::max(
+            pl.smem_floats,
+            bottom_layout(pl.bottom0_nmax, pl.bottom0_elems, pl.bottom0_snr_floats).total);
     }
-
-    // Deeper transforms: groups of consecutive transforms sharing the scratch buffers.
-    int64_t gfloats = 0;
-    bool open = false;
-    std::vector<int> members;
-    ffa_status kerr = FFA_OK;
-    auto close_group = [&]() {
-        if (!open) return;
-        Group g;
-        g.bottom_off = (int64_t)pl.items.size();
-        int maxpass = 0;
-        for (int t : members) {
-            const TransformDesc& d = pl.trs[t];
-            for (int c = 0; c < (1 << d.depth); ++c) pl.items.push_back(WorkItem{t, c, 0, 0, 0});
-            const int rows = (d.m + (1 << d.depth) - 1) >> d.depth;
-            g.bottom_nmax = std::max(g.bottom_nmax, rows);
-            g.bottom_elems = std::max(g.bottom_elems, rows * d.p);
-            maxpass = std::max(maxpass, top_passes(d.depth, d.chunk));
-            g.bottom_bytes += 8.0 * d.m * d.p;
+    std::vector<std::vector<int>> batches;
+    {
+        int64_t bf = 0, scratch = 0;
+        for (size_t t = 0; t < pl.trs.size(); ++t) {
+            TransformDesc& d = pl.trs[t];
+            if (d.depth == 0) continue;
+            const int64_t need = (int64_t)d.m * d.p;
+            if (batches.empty() || bf + need > kBatchFloats) {
+                batches.emplace_back();
+                bf = 0;
+            }
+            batches.back().push_back((int)t);
+            bf += need;
+            d.scratch_off = scratch;
+            scratch += (int64_t)align_up((size_t)need, 4);
         }
-        g.bottom_cnt = (int64_t)pl.items.size() - g.bottom_off;
-        g.bottom_smem = bottom_layout(g.bottom_nmax, g.bottom_elems, 0).total * 4;
-        for (int j = 0; j < maxpass; ++j) {
-            Stage s;
-            s.off = (int64_t)pl.items.size();
-            for (int t : members) {
-                const TransformDesc& d = pl.trs[t];
-                const int np = top_passes(d.depth, d.chunk);
-                if (j >= np) continue;
+        pl.scratch_floats = scratch;
+    }
+    // items of each (batch, stage)
+    std::vector<std::vector<std::vector<WorkItem>>> st_items(batches.size());
+    int max_stage = 0;
+    for (size_t b = 0; b < batches.size(); ++b) {
+        auto& sv = st_items[b];
+        sv.emplace_back();
+        for (int t : batches[b]) {
+            const TransformDesc& d = pl.trs[t];
+            for (int c = 0; c < (1 << d.depth); ++c) sv[0].push_back(WorkItem{t, c, -1, 0, 0});
+            pl.stage_count[(size_t)t * kMaxStages] = 1 << d.depth;
+            const int rows = (d.m + (1 << d.depth) - 1) >> d.depth;
+            pl.bottom_nmax = std::max(pl.bottom_nmax, rows);
+            pl.bottom_elems = std::max(pl.bottom_elems, rows * d.p);
+            pl.ffa_bytes += 8.0 * d.m * d.p;
+            const int np = top_passes(d.depth, d.chunk);
+            if (np + 1 > kMaxStages) return fail(FFA_ERR_UNSUPPORTED, "tree too deep");
+            for (int j = 0; j < np; ++j) {
+                if ((int)sv.size() < j + 2) sv.emplace_back();
                 const int dout = top_pass_out_depth(d.depth, d.chunk, j);
                 const int L = top_pass_in_depth(d.depth, d.chunk, j) - dout;
                 const bool score = j == np - 1;
                 const int K = top_rows(d.p, L, score, wmax);
-                if (K < 1) { kerr = fail(FFA_ERR_UNSUPPORTED, "profile too long"); return; }
-                s.smem = std::max(s.smem, top_layout(K, L, d.p, wmax, score).total * 4);
+                if (K < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+                pl.smem_floats = std::max(pl.smem_floats, top_layout(K, L, d.p, wmax, score).total);
                 const int nmax = (d.m + (1 << dout) - 1) >> dout;
                 const int lim = score ? d.kept : nmax;
                 const int nb = (lim + K - 1) / K;
@@ -345,43 +348,36 @@ ffa_status build_plan(Plan& pl) {
                     // the item's target node and row block, as the kernel derives them
                     const int node = i / nb, blk = i - node * nb;
                     int st0 = 0, n0 = d.m;
-                    for (int b = dout - 1; b >= 0; --b) {
+                    for (int bb = dout - 1; bb >= 0; --bb) {
                         const int nh = n0 >> 1;
-                        if ((node >> b) & 1) { st0 += nh; n0 -= nh; } else { n0 = nh; }
+                        if ((node >> bb) & 1) { st0 += nh; n0 -= nh; } else { n0 = nh; }
                     }
                     const int lo0 = blk * K;
                     const int hi0 = std::min(lo0 + K, score ? d.kept : n0) - 1;
                     const int tix = (int)(pl.top_tables.size() / kTopTableInts);
                     pl.top_tables.resize(pl.top_tables.size() + kTopTableInts, 0);
                     if (lo0 <= hi0)
-                        top_intervals(st0, n0, lo0, hi0, L, pl.top_tables.data() + (size_t)tix * kTopTableInts);
-                    pl.items.push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, tix});
+                        top_intervals(st0, n0, lo0, hi0, L,
+                                      pl.top_tables.data() + (size_t)tix * kTopTableInts);
+                    sv[j + 1].push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, tix});
                 }
-                s.bytes += 4.0 * d.m * d.p + (score ? out_row_bytes * d.kept : 4.0 * d.m * d.p);
+                pl.stage_count[(size_t)t * kMaxStages + j + 1] = cnt;
+                pl.ffa_bytes += 4.0 * d.m * d.p + (score ? out_row_bytes * d.kept : 4.0 * d.m * d.p);
             }
-            s.cnt = (int64_t)pl.items.size() - s.off;
-            g.stages.push_back(s);
         }
-        pl.groups.push_back(g);
-        members.clear();
-        open = false;
-        gfloats = 0;
-    };
-    for (size_t t = 0; t < pl.trs.size(); ++t) {
-        TransformDesc& d = pl.trs[t];
-        if (d.depth == 0) continue;
-        const int64_t need = (int64_t)d.m * d.p;
-        if (open && gfloats + need > kGroupFloats) close_group();
-        d.scratch_off = gfloats;
-        gfloats += (int64_t)align_up((size_t)need, 4);
-        pl.scratch_floats = std::max(pl.scratch_floats, gfloats);
-        members.push_back((int)t);
-        open = true;
+        max_stage = std::max(max_stage, (int)sv.size());
     }
-    close_group();
-    if (kerr != FFA_OK) return kerr;
-    for (const Group& g : pl.groups)
-        if (g.bottom_smem > kSmemBytes) return kRetrySmaller;
+    for (int diag = 0; diag < (int)batches.size() + max_stage; ++diag)
+        for (int s = max_stage - 1; s >= 0; --s) {
+            const int b = diag - s;
+            if (b < 0 || b >= (int)batches.size() || s >= (int)st_items[b].size()) continue;
+            pl.items.insert(pl.items.end(), st_items[b][s].begin(), st_items[b][s].end());
+        }
+    if (pl.bottom_nmax)
+        pl.smem_floats =
+            std::max(pl.smem_floats, bottom_layout(pl.bottom_nmax, pl.bottom_elems, 0).total);
+    if ((pl.smem_floats + 4) * 4 > kSmemBytes) return kRetrySmaller;
+    pl.nitems = (int)pl.items.size();
 
     // Tables: octaves | transforms | items, each 256-byte aligned.
     size_t o = 0;
@@ -395,6 +391,8 @@ ffa_status build_plan(Plan& pl) {
     o = align_up(o + pl.top_tables.size() * sizeof(int), 256);
     pl.o_dsblk = o;
     o = align_up(o + pl.ds_blocks.size() * sizeof(int2), 256);
+    pl.o_stcnt = o;
+    o = align_up(o + pl.stage_count.size() * sizeof(int), 256);
     pl.tables_bytes = std::max<size_t>(o, 256);
 
     // Workspace: status | tables | prefix | chunk sums | series | scratch 0 | scratch 1
@@ -412,6 +410,9 @@ ffa_status build_plan(Plan& pl) {
     w = align_up(w + (size_t)pl.scratch_floats * 4, 256);
     pl.o_s1 = w;
     w = align_up(w + (size_t)pl.scratch_floats * 4, 256);
+    pl.o_counters = w;  // queue counter, then per transform and stage completions
+    pl.counter_bytes = (1 + pl.trs.size() * kMaxStages) * sizeof(int);
+    w = align_up(w + pl.counter_bytes, 256);
     pl.ws_bytes = w;
     // host-buffer variant: + input and outputs
     pl.o_hx = w;
@@ -441,6 +442,7 @@ ffa_status ensure_pinned(Plan& pl) {
     std::memcpy(h + pl.o_items, pl.items.data(), pl.items.size() * sizeof(WorkItem));
     std::memcpy(h + pl.o_toptab, pl.top_tables.data(), pl.top_tables.size() * sizeof(int));
     std::memcpy(h + pl.o_dsblk, pl.ds_blocks.data(), pl.ds_blocks.size() * sizeof(int2));
+    std::memcpy(h + pl.o_stcnt, pl.stage_count.data(), pl.stage_count.size() * sizeof(int));
     pl.pinned = p;
     return FFA_OK;
 }
@@ -476,7 +478,7 @@ ffa_status get_plan(int64_t n, double tsamp, double pmin, double pmax, int bmin,
         if (st != kRetrySmaller) break;
         // sub-trees of different widths share one launch: lower the row limit and replan
         cap = std::min(cap, pl->row_cap) - 1;
-        if (cap < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+        if (cap < 2) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
         auto fresh = std::make_unique<Plan>();
         fresh->n = n; fresh->tsamp = tsamp; fresh->pmin = pmin; fresh->pmax = pmax;
         fresh->bmin = bmin; fresh->bmax = bmax; fresh->widths = pl->widths; fresh->W = W;
@@ -488,6 +490,22 @@ ffa_status get_plan(int64_t n, double tsamp, double pmin, double pmax, int bmin,
     *out = pl.get();
     g_plans[key] = std::move(pl);
     return FFA_OK;
+}
+
+// One CTA per SM (the kernel's shared memory allows no more).
+int persistent_ctas() {
+    static int n[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 152;
+    if (!n[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0)
+            sms = 152;
+        n[dev] = sms;
+    }
+    return n[dev];
 }
 
 // Issues the whole periodogram on `st`: tables upload, prefix, downsampling, then
@@ -508,9 +526,9 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     float* s0 = reinterpret_cast<float*>(ws + pl.o_s0);
     float* s1 = reinterpret_cast<float*>(ws + pl.o_s1);
 
-    PrefixParams pp{d_x, dtype, pl.n, reinterpret_cast<float2*>(ws + pl.o_partial), prefix,
+    PrefixParams xp{d_x, dtype, pl.n, reinterpret_cast<float2*>(ws + pl.o_partial), prefix,
                     pl.nchunks};
-    FFA_CUDA(launch_prefix(pp, st), "prefix launch");
+    FFA_CUDA(launch_prefix(xp, st), "prefix launch");
     DownsampleParams dp{};
     dp.x = d_x;
     dp.dtype = dtype;
@@ -523,53 +541,47 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     dp.out = ds;
     FFA_CUDA(launch_downsample(dp, st), "downsample launch");
 
-    BottomParams bp{};
+    // ---- all FFA work: one persistent launch over the plan's queue
+    int* counters = reinterpret_cast<int*>(ws + pl.o_counters);
+    FFA_CUDA(cudaMemsetAsync(counters, 0, pl.counter_bytes, st), "cudaMemsetAsync(counters)");
+    PersistentParams pp{};
+    BottomParams& bp = pp.bottom;
     bp.src = ds;
+    bp.dst = s0;  // sub-trees of a transform with P top passes land in buffer P % 2
+    bp.dst_odd = s1;
     bp.trs = d_trs;
     bp.widths = pl.W;
     bp.periods = d_periods;
     bp.foldbins = d_foldbins;
     bp.snr = d_snr;
     bp.status = status;
-    if (pl.bottom0_cnt) {
-        bp.items = d_items + pl.bottom0_off;
-        bp.nmax = pl.bottom0_nmax;
-        bp.elems_max = pl.bottom0_elems;
-        bp.snr_warps = pl.bottom0_snr_warps;
-        bp.snr_floats = pl.bottom0_snr_floats;
-        LaunchScope ls(kFfaBottomSnr, pl.bottom0_bytes, st);
-        FFA_CUDA(launch_bottom(bp, (int)pl.bottom0_cnt, pl.bottom0_smem, true, st),
-                 "ffa_bottom_snr launch");
-    }
-    for (const Group& g : pl.groups) {
-        bp.items = d_items + g.bottom_off;
-        bp.dst = s0;      // sub-trees of a transform with P top passes land in buffer P % 2
-        bp.dst_odd = s1;
-        bp.nmax = g.bottom_nmax;
-        bp.elems_max = g.bottom_elems;
-        bp.snr_warps = 0;
-        bp.snr_floats = 0;
-        {
-            LaunchScope ls(kFfaBottom, g.bottom_bytes, st);
-            FFA_CUDA(launch_bottom(bp, (int)g.bottom_cnt, g.bottom_smem, false, st),
-                     "ffa_bottom launch");
-        }
-        for (size_t j = 0; j < g.stages.size(); ++j) {
-            const Stage& sg = g.stages[j];
-            TopParams tp{};
-            tp.buf0 = s0;
-            tp.buf1 = s1;
-            tp.trs = d_trs;
-            tp.items = d_items + sg.off;
-            tp.widths = pl.W;
-            tp.periods = d_periods;
-            tp.foldbins = d_foldbins;
-            tp.snr = d_snr;
-            tp.status = status;
-            tp.tables = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_toptab);
-            LaunchScope ls(kFfaTop, sg.bytes, st);
-            FFA_CUDA(launch_top(tp, (int)sg.cnt, sg.smem, st), "ffa_top launch");
-        }
+    bp.nmax = pl.bottom_nmax;
+    bp.elems_max = pl.bottom_elems;
+    pp.bottom_snr = bp;
+    pp.bottom_snr.nmax = pl.bottom0_nmax;
+    pp.bottom_snr.elems_max = pl.bottom0_elems;
+    pp.bottom_snr.snr_warps = pl.bottom0_snr_warps;
+    pp.bottom_snr.snr_floats = pl.bottom0_snr_floats;
+    TopParams& tp = pp.top;
+    tp.buf0 = s0;
+    tp.buf1 = s1;
+    tp.trs = d_trs;
+    tp.widths = pl.W;
+    tp.periods = d_periods;
+    tp.foldbins = d_foldbins;
+    tp.snr = d_snr;
+    tp.status = status;
+    tp.tables = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_toptab);
+    pp.items = d_items;
+    pp.nitems = pl.nitems;
+    pp.queue = counters;
+    pp.done = counters + 1;
+    pp.stage_count = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt);
+    pp.smem_floats = pl.smem_floats;
+    {
+        LaunchScope ls(kFfaPersistent, pl.ffa_bytes, st);
+        FFA_CUDA(launch_persistent(pp, persistent_ctas(), (pl.smem_floats + 4) * 4, st),
+                 "ffa_persistent launch");
     }
     return FFA_OK;
 }

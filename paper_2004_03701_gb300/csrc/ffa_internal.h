@@ -217,6 +217,7 @@ enum KernelKind : int {
     kFfaTop,
     kBoxcarSnr,
     kNormalise,
+    kFfaPersistent,
     kNumKinds
 };
 
@@ -282,6 +283,20 @@ struct TopParams {
     int single_rows;
 };
 
+constexpr int kMaxStages = 8;  // sub-trees + up to 7 top passes per transform
+
+struct PersistentParams {
+    BottomParams bottom;            // sub-tree items (pass -1)
+    BottomParams bottom_snr;        // whole-tree items scored directly (pass -2)
+    TopParams top;                  // top-pass items (pass >= 0)
+    const WorkItem* items;          // queue order
+    int nitems;
+    int* queue;                     // dispatch counter, zero at launch
+    int* done;                      // per transform and stage: items completed, zero at launch
+    const int* stage_count;         // per transform and stage: items listed
+    int smem_floats;                // dynamic shared floats before the 16-byte queue slot
+};
+
 struct SnrParams {
     const float* prof;
     int64_t rows;
@@ -308,6 +323,8 @@ cudaError_t launch_downsample(const DownsampleParams& P, cudaStream_t s);
 cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bool snr_mode,
                           cudaStream_t s);
 cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s);
+cudaError_t launch_persistent(const PersistentParams& P, int nblocks, int smem_bytes,
+                              cudaStream_t s);
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s);
 cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s);
 constexpr int kNormaliseBlocks = 1216;  // 8 CTAs per SM

@@ -552,15 +552,13 @@ __device__ __forceinline__ void reg_strip_any(float* sm, int in, int out, int st
 constexpr int kRegLevels = 4;          // levels done in registers: nodes of <= 16 rows
 
 template <bool kSnr>
-__global__ void __launch_bounds__(kBottomThreads, kBottomMinBlocks) ffa_bottom_kernel(BottomParams P) {
-    extern __shared__ __align__(16) float smem[];
+__device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkItem item, float* smem) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kBottomThreads / 32;
     const BottomLayout lay = bottom_layout(P.nmax, P.elems_max, P.snr_floats);
     int2* desc = reinterpret_cast<int2*>(smem + lay.desc);  // 2 x nmax
 
-    const WorkItem item = P.items ? P.items[blockIdx.x] : WorkItem{0, (int)blockIdx.x, 0, 0, 0};
     const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
     const int p = tr.p;
 
@@ -667,6 +665,13 @@ __global__ void __launch_bounds__(kBottomThreads, kBottomMinBlocks) ffa_bottom_k
     if (tid == 0) mbar_inval(bar);
 }
 
+template <bool kSnr>
+__global__ void __launch_bounds__(kBottomThreads, kBottomMinBlocks) ffa_bottom_kernel(BottomParams P) {
+    extern __shared__ __align__(16) float smem[];
+    const WorkItem item = P.items ? P.items[blockIdx.x] : WorkItem{0, (int)blockIdx.x, 0, 0, 0};
+    bottom_item<kSnr>(P, item, smem);
+}
+
 // ---------------------------------------------------------------------------------
 // Top of the tree: up to three merge levels per pass, gathered.  A CTA computes rows
 // [lo, hi] of one node at depth d_out from the complete transforms of its descendants
@@ -675,15 +680,11 @@ __global__ void __launch_bounds__(kBottomThreads, kBottomMinBlocks) ffa_bottom_k
 // per interval) and merged in shared memory.  The last pass of a periodogram scores
 // its rows with the boxcar filters instead of storing them.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(TopParams P) {
-    extern __shared__ __align__(16) float smem[];
+__device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item, float* smem) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kTopThreads / 32;
 
-    const WorkItem item = P.items ? P.items[blockIdx.x]
-                                  : WorkItem{0, (int)blockIdx.x, (int16_t)P.single_pass,
-                                             (int16_t)P.single_rows, 0};
     const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
     const int p = tr.p, m = tr.m;
     const int npass = top_passes(tr.depth, tr.chunk);
@@ -864,6 +865,74 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
     if (tid == 0) mbar_inval(bar);
 }
 
+__global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(TopParams P) {
+    extern __shared__ __align__(16) float smem[];
+    const WorkItem item = P.items ? P.items[blockIdx.x]
+                                  : WorkItem{0, (int)blockIdx.x, (int16_t)P.single_pass,
+                                             (int16_t)P.single_rows, 0};
+    top_item(P, item, smem);
+}
+
+// ---------------------------------------------------------------------------------
+// Persistent FFA kernel of a periodogram: one CTA per SM takes work items from a
+// queue (one atomic counter) until the list is exhausted.  Items are sub-trees
+// (stage 0) or top passes (stage pass + 1) of the transforms; an item of stage s > 0
+// first waits until every item of stage s - 1 of its transform has completed.  The
+// queue lists all items of a stage before any item of the next stage of the same
+// transform, and a CTA never waits on an item listed after its own, so every wait
+// ends: the items it waits on were taken earlier by CTAs that are running.  Waits are
+// bounded (about 1 s); on expiry the status word gets kDevTimeout and all CTAs stop.
+// Completion: every thread fences its stores, the CTA synchronises, one thread adds to
+// the stage counter.  The waiting thread acquires the counter, then orders the async
+// (bulk-copy) proxy after it before the item's rows are copied in.
+// ---------------------------------------------------------------------------------
+static_assert(kBottomThreads == kTopThreads, "persistent CTAs run both item kinds");
+__global__ void __launch_bounds__(kTopThreads, 1) ffa_persistent_kernel(PersistentParams P) {
+    extern __shared__ __align__(16) float smem[];
+    int* slot = reinterpret_cast<int*>(smem + P.smem_floats);  // queue broadcast
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            int q = atomicAdd(P.queue, 1);
+            if (*reinterpret_cast<volatile unsigned*>(P.bottom.status) & kDevTimeout) q = P.nitems;
+            slot[0] = q;
+        }
+        __syncthreads();
+        const int q = slot[0];
+        __syncthreads();
+        if (q >= P.nitems) break;
+        const WorkItem item = P.items[q];
+        const int stage = item.pass < 0 ? 0 : item.pass + 1;
+        if (stage > 0) {
+            if (tid == 0) {
+                const int* cnt = P.done + item.tr * kMaxStages + stage - 1;
+                const int need = P.stage_count[item.tr * kMaxStages + stage - 1];
+                const long long t0 = clock64();
+                int seen = 0;
+                for (;;) {
+                    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(seen) : "l"(cnt) : "memory");
+                    if (seen >= need) break;
+                    if (clock64() - t0 > (1LL << 31)) {
+                        atomicOr(P.bottom.status, kDevTimeout);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                slot[1] = seen >= need;
+            }
+            __syncthreads();
+            if (!slot[1]) break;
+        }
+        if (item.pass == -2) bottom_item<true>(P.bottom_snr, item, smem);
+        else if (item.pass == -1) bottom_item<false>(P.bottom, item, smem);
+        else top_item(P.top, item, smem);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0 && item.pass != -2) atomicAdd(P.done + item.tr * kMaxStages + stage, 1);
+    }
+}
+
 // Standalone boxcar S/N of stored profiles: one warp per row.
 __global__ void __launch_bounds__(256) boxcar_snr_kernel(SnrParams P) {
     extern __shared__ __align__(16) float smem[];
@@ -1038,6 +1107,14 @@ cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s) {
         LaunchScope ls(kNormalise, (4.0 + out_bytes) * P.n, s);
         normalise_write_kernel<<<P.nblocks, 256, 0, s>>>(P);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_persistent(const PersistentParams& P, int nblocks, int smem_bytes,
+                              cudaStream_t s) {
+    if (nblocks <= 0 || P.nitems <= 0) return cudaSuccess;
+    allow_max_smem((const void*)ffa_persistent_kernel, 4);
+    ffa_persistent_kernel<<<nblocks, kTopThreads, smem_bytes, s>>>(P);
     return cudaGetLastError();
 }
 
