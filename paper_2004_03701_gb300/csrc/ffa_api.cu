@@ -492,22 +492,6 @@ ffa_status get_plan(int64_t n, double tsamp, double pmin, double pmax, int bmin,
     return FFA_OK;
 }
 
-// One CTA per SM (the kernel's shared memory allows no more).
-int persistent_ctas() {
-    static int n[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return 152;
-    if (!n[dev]) {
-        int sms = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            sms <= 0)
-            sms = 152;
-        n[dev] = sms;
-    }
-    return n[dev];
-}
-
 // Issues the whole periodogram on `st`: tables upload, prefix, downsampling, then
 // the FFA + S/N launches group by group.
 ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d_periods,
@@ -580,8 +564,7 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     pp.smem_floats = pl.smem_floats;
     {
         LaunchScope ls(kFfaPersistent, pl.ffa_bytes, st);
-        FFA_CUDA(launch_persistent(pp, persistent_ctas(), (pl.smem_floats + 4) * 4, st),
-                 "ffa_persistent launch");
+        FFA_CUDA(launch_persistent(pp, (pl.smem_floats + 4) * 4, st), "ffa_persistent launch");
     }
     return FFA_OK;
 }

@@ -323,8 +323,7 @@ cudaError_t launch_downsample(const DownsampleParams& P, cudaStream_t s);
 cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bool snr_mode,
                           cudaStream_t s);
 cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s);
-cudaError_t launch_persistent(const PersistentParams& P, int nblocks, int smem_bytes,
-                              cudaStream_t s);
+cudaError_t launch_persistent(const PersistentParams& P, int smem_bytes, cudaStream_t s);
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s);
 cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s);
 constexpr int kNormaliseBlocks = 1216;  // 8 CTAs per SM

@@ -887,7 +887,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
 // (bulk-copy) proxy after it before the item's rows are copied in.
 // ---------------------------------------------------------------------------------
 static_assert(kBottomThreads == kTopThreads, "persistent CTAs run both item kinds");
-__global__ void __launch_bounds__(kTopThreads, 1) ffa_persistent_kernel(PersistentParams P) {
+__global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_kernel(PersistentParams P) {
     extern __shared__ __align__(16) float smem[];
     int* slot = reinterpret_cast<int*>(smem + P.smem_floats);  // queue broadcast
     const int tid = threadIdx.x;
@@ -1110,11 +1110,19 @@ cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_persistent(const PersistentParams& P, int nblocks, int smem_bytes,
-                              cudaStream_t s) {
-    if (nblocks <= 0 || P.nitems <= 0) return cudaSuccess;
+cudaError_t launch_persistent(const PersistentParams& P, int smem_bytes, cudaStream_t s) {
+    if (P.nitems <= 0) return cudaSuccess;
     allow_max_smem((const void*)ffa_persistent_kernel, 4);
-    ffa_persistent_kernel<<<nblocks, kTopThreads, smem_bytes, s>>>(P);
+    // as many CTAs as can be resident at once (the queue needs no more)
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        sms = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ffa_persistent_kernel, kTopThreads,
+                                                      smem_bytes) != cudaSuccess ||
+        per_sm <= 0)
+        per_sm = 1;
+    ffa_persistent_kernel<<<sms * per_sm, kTopThreads, smem_bytes, s>>>(P);
     return cudaGetLastError();
 }
 
