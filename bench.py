@@ -1,14 +1,22 @@
 #!/usr/bin/env python3
-"""Benchmark of the FFA periodogram on one series per GPU.
+"""Benchmark of the FFA periodogram.
 
-Workload (default): 2^23 samples at 64 us (the paper's benchmark series shape, Sec. 5.8),
-N(0,1) noise plus three Gaussian pulse trains, periods 0.2-20 s, 240-260 bins, 11 boxcar
-widths; synthetic data from a fixed seed.  One step = one whole periodogram (prefix sums,
-downsampling of all 55 pseudo-octaves, 1155 FFA transforms, boxcar S/N of 662,440 trials).
+Workload (default, --workload survey): 2^23 samples at 64 us (the paper's benchmark
+series shape, Sec. 5.8), N(0,1) noise plus three Gaussian pulse trains, periods
+0.2-20 s, 240-260 bins, 11 boxcar widths; synthetic data from a fixed seed.  One step =
+one whole periodogram (prefix sums, downsampling of all 55 pseudo-octaves, 1155 FFA
+transforms, boxcar S/N of 662,440 trials).
 
-metric: time-series samples searched per second = N / (device time of one step), summed
-over GPUs.  Each GPU runs its own replica (series are independent; no collective is in
-the data path).  Between timed steps the L2 is flushed by writing a 256 MB buffer.
+Other workloads: plain_small (2^18 samples at 1 ms, periods 1-10 s); batch_uneven (256
+series of U[2^20, 2^23] samples, each with its own period range in 0.1-30 s, one CUDA
+graph per step over all launch chunks); batch_int8 (1024 series of 2^21 samples,
+periods 0.1-10 s, bins 480-520, 16 widths, normalised and stored as int8).  --storage
+f16 / i8 stores the normalised input at reduced precision (sums stay FP32).
+
+metric: time-series samples searched per second = samples / (device time of one step),
+summed over GPUs.  Each GPU searches its own series (independent; no collective is in
+the data path; batches are split by cost).  Between timed steps the L2 is flushed by
+writing a 256 MB buffer.
 
 --impl reference times the CPU oracle instead (a bounded sample of the same workload per
 step, extrapolated to the whole periodogram); it is the slow reference program, not a
@@ -44,27 +52,30 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ffa", "reference"], default="ffa")
-    ap.add_argument("--workload", choices=["survey", "plain_small"], default="survey")
+    ap.add_argument("--workload", choices=["survey", "plain_small"] + list(BATCH_WORKLOADS),
+                    default="survey")
+    ap.add_argument("--storage", choices=["f32", "f16", "i8"], default=None,
+                    help="input storage (default f32; i8 for batch_int8)")
+    ap.add_argument("--ws-budget-gb", type=float, default=48.0,
+                    help="workspace budget of one launch chunk of a batch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-stride", type=int, default=8)
     return ap.parse_args()
 
 
-def workload(name):
-    return synth.survey() if name == "survey" else synth.plain_small()
-
-
-def recorded_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu record, or None if the
-    kernel source changed since it was taken."""
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu record, or
+    None if there is none or the kernel source changed since it was taken."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
         src = open(os.path.join(ROOT, "paper_2004_03701_gb300", "csrc", "ffa_kernels.cu"), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_prefix"]:
             return None
-        return rec["dram_bytes_per_launch"] if rec["kernel"] == kernel else None
+        if rec["kernel"] != kernel or rec.get("workload", workload) != workload:
+            return None
+        return rec["dram_bytes_per_launch"]
     except Exception:
         return None
 
@@ -139,7 +150,7 @@ def dist_env():
 
 # ------------------------------------------------------------------------- CPU oracle
 def oracle_sample_time(w, stride, offset=0):
-    """Times the CPU oracle on a bounded sample of the workload: all downsampling, plus
+    """Times the CPU oracle on a bounded sample of one series: all downsampling, plus
     the FFA and S/N of every `stride`-th transform; extrapolates the FFA + S/N time by
     the folded-sample ratio.  Returns (seconds per whole periodogram, description)."""
     import oracle
@@ -156,10 +167,10 @@ def oracle_sample_time(w, stride, offset=0):
     oracle.periodogram(w.x, *args, w.widths, select=sel)
     t_sel = time.perf_counter() - t0
     folded = (pl.tr_m * pl.tr_p).astype(np.float64)
-    ratio = folded.sum() / folded[sel].sum()
+    ratio = folded.sum() / max(folded[sel].sum(), 1.0)
     # the selected run downsampled every octave it touched again; remove that once
     touched = np.unique(pl.tr_octave[sel])
-    t_ds_sel = t_ds * len(touched) / pl.n_octaves
+    t_ds_sel = t_ds * len(touched) / max(pl.n_octaves, 1)
     est = t_ds + max(t_sel - t_ds_sel, 0.0) * ratio
     desc = ("oracle (1 thread, C, FP64): downsampling of all %d octaves timed in full, FFA + "
             "direct boxcar S/N of every %d-th of %d transforms (%.1f%% of folded samples) "
@@ -168,25 +179,184 @@ def oracle_sample_time(w, stride, offset=0):
     return est, desc
 
 
+def oracle_rate(job, stride, offset=0):
+    """(samples/s, description) of the CPU oracle on a bounded sample of the job."""
+    if job.batch is None:
+        est, desc = oracle_sample_time(job.single, stride, offset)
+        return job.single.n / est, desc
+    b = job.batch
+    pick = sorted({0, len(b.series) // 2, len(b.series) - 1})
+    tot_t, tot_n, descs = 0.0, 0, []
+    for i in pick:
+        s = b.series[i]
+        x = b.series_x(i)
+        if job.store != "f32":
+            x = job.dequantised(i)
+        w = synth.Workload("s%d" % i, x, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax, b.widths)
+        est, desc = oracle_sample_time(w, stride, offset)
+        tot_t += est
+        tot_n += s.n
+        descs.append("series %d (n=%d): %s" % (i, s.n, desc))
+    return tot_n / tot_t, "%d of %d series of the batch, rate = their samples / their " \
+        "estimated time; " % (len(pick), len(b.series)) + " | ".join(descs)
+
+
+# --------------------------------------------------------------------------- workloads
+BATCH_WORKLOADS = ("batch_uneven", "batch_int8")
+
+
+class Job:
+    """One benchmark workload: its inputs on the host and (after `to_device`) the
+    searcher, the device input and the step."""
+
+    def __init__(self, name, store, rank=0, world=1):
+        self.name = name
+        self.store = store
+        self.single = None
+        self.batch = None
+        if name == "survey":
+            self.single = synth.survey()
+        elif name == "plain_small":
+            self.single = synth.plain_small()
+        elif name == "batch_uneven":
+            self.batch = self._shard(synth.batch_uneven, 256, rank, world)
+        elif name == "batch_int8":
+            self.batch = self._shard(synth.batch_int8_stress, 1024, rank, world)
+        else:
+            raise ValueError(name)
+        self._deq = {}
+
+    @staticmethod
+    def _shard(make, per_rank, rank, world):
+        # weak scaling: world * per_rank series, each rank draws only its own share
+        b = make(per_rank * world)
+        if world == 1:
+            return b
+        import paper_2004_03701_gb300 as ffa
+        mine = ffa.shard_series([s.n for s in b.series], rank, world)
+        series, off = [], 0
+        xs = []
+        for i in mine:
+            s = b.series[i]
+            xs.append(b.series_x(i))
+            series.append(synth.SeriesParams(off, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax,
+                                             s.pulses))
+            off += s.n
+        return synth.BatchWorkload(b.name, np.concatenate(xs), series, b.widths)
+
+    @property
+    def n(self):
+        return self.single.n if self.batch is None else self.batch.n
+
+    def dequantised(self, i):
+        return self._deq[i]
+
+    # ------------------------------------------------------------------ device side
+    def to_device(self, ffa, torch, dev, ws_budget):
+        self.ffa, self.torch, self.dev = ffa, torch, dev
+        src = self.single.x if self.batch is None else self.batch.x
+        self.x32 = torch.from_numpy(src).to(dev)
+        self.x = self._store(self.x32)
+        if self.batch is None:
+            w = self.single
+            self.searcher = ffa.Searcher(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths,
+                                         device=dev)
+            self.widths = w.widths
+        else:
+            b = self.batch
+            ser = [ffa.Series(s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax)
+                   for s in b.series]
+            self.searcher = ffa.BatchSearcher(ser, b.widths, ws_budget=ws_budget, device=dev)
+            self.widths = b.widths
+        self.graph = None
+
+    def _store(self, x32):
+        """Normalised storage of the input (Sec. 3.1): FP16 or int8 (q/16) by the
+        library's own normalise call, whole series (each series of a batch alone)."""
+        if self.store == "f32":
+            return x32
+        ffa, torch = self.ffa, self.torch
+        out = torch.empty(x32.numel(), dtype=torch.float16 if self.store == "f16" else torch.int8,
+                          device=x32.device)
+        segs = [(0, x32.numel())] if self.batch is None else \
+            [(s.offset, s.n) for s in self.batch.series]
+        for i, (o, n) in enumerate(segs):
+            out[o:o + n] = ffa.normalise(x32[o:o + n], dtype=out.dtype)[0]
+        torch.cuda.synchronize()
+        if self.batch is not None:  # host copies of a few dequantised series for the oracle
+            host = out.cpu().numpy()
+            for i in sorted({0, len(segs) // 2, len(segs) - 1}):
+                o, n = segs[i]
+                v = host[o:o + n].astype(np.float32)
+                self._deq[i] = v / 16 if self.store == "i8" else v
+        return out
+
+    def capture(self):
+        """Batches run as one CUDA graph of the whole launch sequence."""
+        if self.batch is None:
+            return
+        torch = self.torch
+        self.searcher(self.x)
+        torch.cuda.synchronize()
+        self.ffa.profile_enable(False)
+        l0 = self.ffa.launch_count()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.searcher(self.x)
+        self.graph_launches = self.ffa.launch_count() - l0
+
+    def step(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.searcher(self.x)
+
+    def eager_step(self):
+        self.searcher(self.x)
+
+    @property
+    def ntrials(self):
+        return self.searcher.info.ntrials
+
+    def config(self):
+        if self.batch is None:
+            w = self.single
+            i = self.searcher.info
+            return {"workload": w.name, "n": w.n, "tsamp": w.tsamp, "pmin": w.pmin,
+                    "pmax": w.pmax, "bins": [w.bmin, w.bmax], "widths": list(w.widths),
+                    "ntrials": i.ntrials, "transforms": i.ntransforms, "octaves": i.noctaves,
+                    "storage": self.store}
+        b, i = self.batch, self.searcher.info
+        ns = [s.n for s in b.series]
+        return {"workload": b.name, "series": len(b.series), "n_total": b.n,
+                "n_min": min(ns), "n_max": max(ns), "tsamp": b.series[0].tsamp,
+                "pmin_range": [min(s.pmin for s in b.series), max(s.pmin for s in b.series)],
+                "pmax_range": [min(s.pmax for s in b.series), max(s.pmax for s in b.series)],
+                "bins": [b.series[0].bmin, b.series[0].bmax], "widths": list(b.widths),
+                "ntrials": i.ntrials, "transforms": i.ntransforms, "chunks": i.nchunks,
+                "workspace_gb": round(i.workspace_bytes / 1e9, 2), "storage": self.store,
+                "graph": "one CUDA graph per step (all chunks)"}
+
+
 def run_reference(a):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    w = workload(a.workload)
+    job = Job(a.workload, "f32")
     stride = 64
-    times = []
+    rates = []
+    desc = ""
     for i in range(a.warmup + a.steps):
-        est, desc = oracle_sample_time(w, stride, offset=i)
+        r, desc = oracle_rate(job, stride, offset=i)
         if i >= a.warmup:
-            times.append(est)
-    t = statistics.mean(times)
-    value = w.n / t
+            rates.append(r)
+    value = statistics.mean(rates)
+    cfg = {"workload": job.single.name if job.batch is None else job.batch.name, "n": job.n}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n": w.n, "tsamp": w.tsamp, "pmin": w.pmin,
-                   "pmax": w.pmax, "bins": [w.bmin, w.bmax], "widths": list(w.widths)},
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": job.n / value * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": desc.replace("every 64-th", "every 64-th (rotating)")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -211,9 +381,10 @@ def run_ffa(a):
     ffa.build()
     ffa.library()
 
-    w = workload(a.workload)
-    x = torch.from_numpy(w.x).to(dev)
-    s = ffa.Searcher(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths, device=dev)
+    store = a.storage or ("i8" if a.workload == "batch_int8" else "f32")
+    job = Job(a.workload, store, rank, world)
+    job.to_device(ffa, torch, dev, int(a.ws_budget_gb * (1 << 30)))
+    s = job.searcher
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
@@ -222,8 +393,9 @@ def run_ffa(a):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    job.capture()
     for _ in range(max(3, a.warmup)):
-        s(x)
+        job.step()
     s.check()
     barrier()
 
@@ -237,26 +409,34 @@ def run_ffa(a):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        s(x)
+        job.step()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     launches = ffa.launch_count() - launches0
+    if job.graph is not None:
+        launches = job.graph_launches * a.steps   # replays launch the captured kernels
     barrier()
     clk = clocks.stop()
+    s.check()
     t_step = sum(times) / len(times)
     if world > 1:
         tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_step = float(tt.item())
-    value = world * w.n / (t_step * 1e-3)
+        nn = torch.tensor([job.n], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(nn)
+        n_all = float(nn.item())
+    else:
+        n_all = float(job.n)
+    value = n_all / (t_step * 1e-3)
 
-    # ---- same steps with per-kernel CUDA events on the launching stream
+    # ---- same steps launched eagerly with per-kernel CUDA events on the stream
     ffa.profile_reset()
     ffa.profile_enable(True)
     for _ in range(a.steps):
         flush.zero_()
-        s(x)
+        job.eager_step()
     torch.cuda.synchronize()
     ffa.profile_enable(False)
     kern = {}
@@ -273,63 +453,86 @@ def run_ffa(a):
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / avg_s / 1e9
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": recorded_traffic(top),
+                "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(top, job.config()["workload"]),
                 "peak_source": peak_kind,
                 "share_of_step": kq["ms"] / tot_ms if tot_ms else None,
                 "launches_per_step": kq["launches"] / a.steps}
 
-    # ---- end to end through the host-buffer C-ABI call (copies inside the timed call)
+    # ---- end to end from pinned host buffers (copies inside the timed region)
     e2e = None
     if not a.no_e2e:
-        T, nw = s.info.ntrials, len(w.widths)
-        xh = torch.from_numpy(w.x).pin_memory()
-        per_h = torch.empty(T, dtype=torch.float64).pin_memory()
-        fb_h = torch.empty(T, dtype=torch.int32).pin_memory()
-        snr_h = torch.empty((T, nw), dtype=torch.float32).pin_memory()
-        xs, ps, fs, ss = xh.numpy(), per_h.numpy(), fb_h.numpy(), snr_h.numpy()
-        for _ in range(2):
-            s.run_host(xs, ps, fs, ss)
-        barrier()
-        et = []
-        for _ in range(a.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s.run_host(xs, ps, fs, ss)
-            et.append(time.perf_counter() - t0)
-        te = sum(et) / len(et)
-        if world > 1:
-            tt = torch.tensor([te], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": world * w.n / te, "unit": UNIT, "h2d_bytes_per_step": 4 * w.n,
-               "d2h_bytes_per_step": T * (8 + 4 + 4 * nw)}
+        e2e = run_e2e(job, a, torch, ffa, flush, barrier, world, dev, n_all)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        est, desc = oracle_sample_time(w, a.cpu_sample_stride)
-        cpu = {"value": w.n / est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        rate, desc = oracle_rate(job, a.cpu_sample_stride if job.batch is None else 32)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
 
     if rank == 0:
+        cfg = job.config()
+        cfg["l2"] = "flushed (256 MB write) between steps"
+        cfg["parallelism"] = "replicas" if world > 1 else "single"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": t_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "n": w.n, "tsamp": w.tsamp, "pmin": w.pmin,
-                       "pmax": w.pmax, "bins": [w.bmin, w.bmax], "widths": list(w.widths),
-                       "ntrials": s.info.ntrials, "transforms": s.info.ntransforms,
-                       "octaves": s.info.noctaves, "l2": "flushed (256 MB write) between steps",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roofline,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if store == "f32" else store + " storage, f32 sums",
+            "data": "synthetic", "config": cfg, "roofline": roofline,
             "kernels_ms_per_step": {k: v["ms"] / a.steps for k, v in kern.items()},
-            "e2e": e2e,
-            "cpu_baseline": cpu,
-            "clocks": clk,
-            "gpu_launches": launches,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_e2e(job, a, torch, ffa, flush, barrier, world, dev, n_all):
+    s = job.searcher
+    T, nw = job.ntrials, len(job.widths)
+    if job.batch is None and job.store == "f32":
+        # the library's host-buffer call: copies in, searches, copies out, synchronises
+        xh = torch.from_numpy(job.single.x).pin_memory()
+        per_h = torch.empty(max(T, 1), dtype=torch.float64).pin_memory()
+        fb_h = torch.empty(max(T, 1), dtype=torch.int32).pin_memory()
+        snr_h = torch.empty((max(T, 1), nw), dtype=torch.float32).pin_memory()
+        xs, ps, fs, ss = xh.numpy(), per_h.numpy(), fb_h.numpy(), snr_h.numpy()
+
+        def one():
+            s.run_host(xs, ps, fs, ss)
+        h2d = 4 * job.n
+    else:
+        # stored input in pinned host memory -> device, search, results -> pinned host
+        xh = job.x.cpu().pin_memory()
+        per_h = torch.empty_like(s.periods, device="cpu").pin_memory()
+        fb_h = torch.empty_like(s.foldbins, device="cpu").pin_memory()
+        snr_h = torch.empty_like(s.snr, device="cpu").pin_memory()
+
+        def one():
+            job.x.copy_(xh, non_blocking=True)
+            job.step()
+            per_h.copy_(s.periods, non_blocking=True)
+            fb_h.copy_(s.foldbins, non_blocking=True)
+            snr_h.copy_(s.snr, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        h2d = job.x.numel() * job.x.element_size()
+    for _ in range(2):
+        one()
+    barrier()
+    et = []
+    for _ in range(a.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one()
+        et.append(time.perf_counter() - t0)
+    te = sum(et) / len(et)
+    if world > 1:
+        tt = torch.tensor([te], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        te = float(tt.item())
+    return {"value": n_all / te, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": T * (8 + 4 + 4 * nw)}
 
 
 def main():

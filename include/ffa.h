@@ -178,6 +178,51 @@ ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double t
                            int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
                            void* d_ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------------
+ * Batched periodograms (many series, e.g. the dedispersed DM trials of an observation,
+ * searched like the paper's pipeline does per DM trial, Sec. 5.7).  Series i is
+ * samples [offset, offset + n) of d_x and has its own sampling time, period range and
+ * bins range; the widths are shared (each below every series' bmin).  Outputs are the
+ * periodograms of the series one after another (h_trial_offsets[i] = first trial of
+ * series i, h_trial_offsets[nseries] = total).  The series are cut into consecutive
+ * chunks whose workspace each fits ws_budget bytes (a series alone may exceed it);
+ * each chunk runs as prefix sums, downsampling and one persistent FFA launch over all
+ * its transforms, in the chunk order on `stream`, reusing one workspace of
+ * ffa_batch_info.workspace_bytes.  d_x must span max(offset + n) elements of dtype.
+ * ---------------------------------------------------------------------------- */
+typedef struct ffa_series {
+    int64_t offset;   /* first sample of the series in d_x (elements) */
+    int64_t n;        /* samples */
+    double tsamp;     /* seconds */
+    double pmin, pmax;
+    int32_t bmin, bmax;
+} ffa_series;
+
+typedef struct ffa_batch_info {
+    int64_t ntrials;          /* rows of all periodograms              */
+    int32_t nchunks;          /* launch sequences                      */
+    int32_t ntransforms;      /* FFA transforms over all series        */
+    int64_t folded_samples;   /* sum of m * p                          */
+    int64_t input_samples;    /* sum of n                              */
+    size_t workspace_bytes;   /* for ffa_periodogram_batch             */
+} ffa_batch_info;
+
+ffa_status ffa_batch_plan(const ffa_series* h_series, int32_t nseries, const int32_t* h_widths,
+                          int32_t nw, size_t ws_budget, int64_t* h_trial_offsets,
+                          ffa_batch_info* out);
+ffa_status ffa_periodogram_batch(const void* d_x, ffa_dtype dtype, const ffa_series* h_series,
+                                 int32_t nseries, const int32_t* h_widths, int32_t nw,
+                                 size_t ws_budget, double* d_periods, int32_t* d_foldbins,
+                                 float* d_snr, int64_t ntrials_cap, void* d_ws, size_t ws_bytes,
+                                 void* stream);
+
+/* Plans (single-series and batch) are built on first use and cached by their parameters
+ * for the life of the process: their page-locked tables are what the table copy of
+ * every call, and of every CUDA graph that captured a call, reads.  This releases them
+ * all; call it only when no call is in flight and no captured graph that contains one
+ * will be launched again. */
+ffa_status ffa_plan_cache_clear(void);
+
 /* Same search, end to end from and to HOST buffers: copies h_x (n floats) to the
  * device, runs the periodogram, copies the three outputs back, and synchronises
  * `stream` before returning.  Host buffers should be page-locked for speed.

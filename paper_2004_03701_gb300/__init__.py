@@ -12,6 +12,7 @@ Calls (names follow include/ffa.h and the paper, Morello et al. 2020):
   periodogram_plan(n, tsamp, pmin, pmax, bmin, bmax, widths)
   periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths)        Sec. 5.3, Fig. 4
   periodogram_host(x_host, ...)                 same, host buffers in and out
+  BatchSearcher(series, widths)                 many series in one buffer, Sec. 5.7
 """
 from __future__ import annotations
 
@@ -25,7 +26,8 @@ import numpy as np
 __all__ = [
     "FFAError", "library", "build", "normalise", "downsample", "ffa_transform", "boxcar_snr",
     "PlanInfo", "periodogram_plan", "periodogram", "periodogram_host", "Searcher",
-    "check", "launch_count", "kernel_names", "profile_enable", "profile_reset",
+    "Series", "BatchInfo", "batch_plan", "BatchSearcher", "periodogram_batch", "shard_series",
+    "check", "plan_cache_clear", "launch_count", "kernel_names", "profile_enable", "profile_reset",
     "profile_query",
 ]
 
@@ -49,6 +51,18 @@ class _PlanInfo(ctypes.Structure):
                 ("max_rows", ctypes.c_int32), ("downsampled_samples", ctypes.c_int64),
                 ("folded_samples", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
                 ("host_workspace_bytes", ctypes.c_size_t)]
+
+
+class _Series(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_int64), ("n", ctypes.c_int64), ("tsamp", ctypes.c_double),
+                ("pmin", ctypes.c_double), ("pmax", ctypes.c_double), ("bmin", ctypes.c_int32),
+                ("bmax", ctypes.c_int32)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("ntrials", ctypes.c_int64), ("nchunks", ctypes.c_int32),
+                ("ntransforms", ctypes.c_int32), ("folded_samples", ctypes.c_int64),
+                ("input_samples", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -84,6 +98,9 @@ def library() -> ctypes.CDLL:
     L.ffa_periodogram_host.argtypes = [vp, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
                                        i64, vp, sz, vp]
     L.ffa_check.argtypes = [vp, vp]
+    L.ffa_batch_plan.argtypes = [vp, i32, vp, i32, sz, vp, ctypes.POINTER(_BatchInfo)]
+    L.ffa_periodogram_batch.argtypes = [vp, i32, vp, i32, vp, i32, sz, vp, vp, vp, i64, vp,
+                                        sz, vp]
     L.ffa_normalise_workspace.argtypes = [i64, ctypes.POINTER(sz)]
     L.ffa_normalise.argtypes = [vp, i64, vp, i32, vp, vp, sz, vp]
     L.ffa_launch_count.restype = i64
@@ -96,7 +113,8 @@ def library() -> ctypes.CDLL:
     for f in ("ffa_downsample_workspace", "ffa_downsample", "ffa_transform_workspace",
               "ffa_transform", "ffa_boxcar_snr", "ffa_periodogram_plan", "ffa_periodogram",
               "ffa_periodogram_host", "ffa_check", "ffa_profile_enable", "ffa_profile_reset",
-              "ffa_normalise_workspace", "ffa_normalise",
+              "ffa_normalise_workspace", "ffa_normalise", "ffa_batch_plan",
+              "ffa_periodogram_batch", "ffa_plan_cache_clear",
               "ffa_profile_query"):
         getattr(L, f).restype = i32
     _lib = L
@@ -314,6 +332,128 @@ def periodogram_host(x: np.ndarray, tsamp, pmin, pmax, bmin, bmax, widths, devic
     snr = np.empty((max(T, 1), nw), np.float32)
     s.run_host(x, per, fb, snr)
     return per[:T], fb[:T], snr[:T]
+
+
+@dataclass(frozen=True)
+class Series:
+    """One series of a batch: samples [offset, offset + n) of the batch buffer."""
+    offset: int
+    n: int
+    tsamp: float
+    pmin: float
+    pmax: float
+    bmin: int
+    bmax: int
+
+
+@dataclass
+class BatchInfo:
+    ntrials: int
+    nchunks: int
+    ntransforms: int
+    folded_samples: int
+    input_samples: int
+    workspace_bytes: int
+
+
+def _series_array(series: Sequence[Series]):
+    arr = (_Series * max(len(series), 1))()
+    for i, s in enumerate(series):
+        arr[i] = _Series(int(s.offset), int(s.n), float(s.tsamp), float(s.pmin), float(s.pmax),
+                         int(s.bmin), int(s.bmax))
+    return arr
+
+
+# default workspace budget of one launch sequence of a batch (bytes)
+DEFAULT_BATCH_BUDGET = 1 << 30
+
+
+def batch_plan(series: Sequence[Series], widths: Sequence[int],
+               ws_budget: int = DEFAULT_BATCH_BUDGET):
+    """(BatchInfo, trial offsets int64 [len(series) + 1]) of a batch search."""
+    w = _widths_array(widths)
+    arr = _series_array(series)
+    offs = np.zeros(len(series) + 1, np.int64)
+    info = _BatchInfo()
+    _check(library().ffa_batch_plan(ctypes.cast(arr, ctypes.c_void_p), len(series), _vp(w),
+                                    len(w), int(ws_budget), _vp(offs), ctypes.byref(info)))
+    return BatchInfo(*(getattr(info, f) for f, _ in _BatchInfo._fields_)), offs
+
+
+class BatchSearcher:
+    """Periodograms of many series stored one after another in one device buffer.
+
+    Outputs of series i are rows trial_offsets[i]:trial_offsets[i+1] of periods,
+    foldbins and snr.  The call is a fixed sequence of launches on one stream, so it can
+    be captured into a CUDA graph once the searcher exists.
+    """
+
+    def __init__(self, series: Sequence[Series], widths: Sequence[int],
+                 ws_budget: int = DEFAULT_BATCH_BUDGET, device="cuda"):
+        torch = _torch()
+        self.series = list(series)
+        self.widths = _widths_array(widths)
+        self.ws_budget = int(ws_budget)
+        self._arr = _series_array(self.series)
+        self.info, self.trial_offsets = batch_plan(self.series, self.widths, self.ws_budget)
+        self.span = max(s.offset + s.n for s in self.series)
+        T, nw = self.info.ntrials, len(self.widths)
+        self.device = torch.device(device)
+        self.ws = _workspace(self.info.workspace_bytes, self.device)
+        self._per = torch.empty(max(T, 1), dtype=torch.float64, device=self.device)
+        self._fb = torch.empty(max(T, 1), dtype=torch.int32, device=self.device)
+        self._snr = torch.empty((max(T, 1), nw), dtype=torch.float32, device=self.device)
+        self.periods, self.foldbins, self.snr = self._per[:T], self._fb[:T], self._snr[:T]
+
+    def __call__(self, x, stream=None):
+        _dev_tensor(x, "x")
+        if x.numel() < self.span:
+            raise ValueError("batch buffer is shorter than the series span")
+        _check(library().ffa_periodogram_batch(
+            _vp(x), _dtype_code(x), ctypes.cast(self._arr, ctypes.c_void_p), len(self.series),
+            _vp(self.widths), len(self.widths), self.ws_budget, _vp(self._per), _vp(self._fb),
+            _vp(self._snr), self.periods.numel(), _vp(self.ws), self.ws.numel(),
+            _stream_handle(stream)))
+        return self.periods, self.foldbins, self.snr
+
+    def series_result(self, i: int):
+        a, b = int(self.trial_offsets[i]), int(self.trial_offsets[i + 1])
+        return self.periods[a:b], self.foldbins[a:b], self.snr[a:b]
+
+    def check(self, stream=None):
+        check(self.ws, stream)
+
+
+def periodogram_batch(x, series: Sequence[Series], widths: Sequence[int],
+                      ws_budget: int = DEFAULT_BATCH_BUDGET, stream=None):
+    """Batched periodograms; returns (periods, foldbins, snr, trial_offsets)."""
+    s = BatchSearcher(series, widths, ws_budget, device=x.device)
+    per, fb, snr = s(x, stream)
+    return per, fb, snr, s.trial_offsets
+
+
+def shard_series(costs: Sequence[float], rank: int, world: int):
+    """Indices of the series that rank `rank` of `world` searches.
+
+    Series are independent, so ranks split the list with no exchange of data: longest
+    first, each to the rank with the least total cost so far (ties to the lower rank).
+    Every rank computes the same assignment from the same cost list; the indices come
+    back in ascending order."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank/world")
+    load = [0.0] * world
+    mine = []
+    for i in sorted(range(len(costs)), key=lambda k: (-float(costs[k]), k)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += float(costs[i])
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def plan_cache_clear() -> None:
+    """Release every cached plan (only when no call or captured graph still uses one)."""
+    _check(library().ffa_plan_cache_clear())
 
 
 def check(ws, stream=None) -> None:

@@ -100,12 +100,23 @@ void drain_pending() {
 // ---------------------------------------------------------------------------------
 // Search plan.
 // ---------------------------------------------------------------------------------
+// One series of a search: samples [x_off, x_off + n) of the input.
+struct SeriesSpec {
+    int64_t x_off, n;
+    double tsamp, pmin, pmax;
+    int bmin, bmax;
+    bool operator<(const SeriesSpec& o) const {
+        return std::tie(x_off, n, tsamp, pmin, pmax, bmin, bmax) <
+               std::tie(o.x_off, o.n, o.tsamp, o.pmin, o.pmax, o.bmin, o.bmax);
+    }
+};
+
 struct Plan {
     // parameters
-    int64_t n = 0;
-    double tsamp = 0, pmin = 0, pmax = 0;
-    int bmin = 0, bmax = 0;
+    std::vector<SeriesSpec> series;
+    int64_t n = 0;       // input span: max over series of x_off + n
     std::vector<int> widths;
+    std::vector<int64_t> series_trial0;  // first trial of each series, + total
     // derived
     Widths W{};
     std::vector<OctaveDesc> oct;
@@ -113,6 +124,8 @@ struct Plan {
     std::vector<WorkItem> items;
     std::vector<int> top_tables;  // kTopTableInts per top-pass item (WorkItem::pad)
     std::vector<int2> ds_blocks;  // downsampling CTAs: {octave, first output}
+    std::vector<PrefixSeg> segs;  // prefix-sum pass: one per series
+    std::vector<int> blk_seg;     // series of each prefix chunk
     int bottom0_nmax = 0, bottom0_elems = 0, bottom0_snr_warps = 0;
     int bottom0_snr_floats = 0;
     int row_cap = kBottomMaxRows;  // sub-tree row limit (lowered if a launch's mix overflows)
@@ -124,9 +137,10 @@ struct Plan {
     size_t o_counters = 0, counter_bytes = 0;
     int64_t ntrials = 0, ds_total = 0, ds_floats = 0, scratch_floats = 0, folded = 0;
     int max_rows = 0, max_p = 0;
-    int64_t nchunks = 0;
+    int64_t nchunks = 0, prefix_len = 0, input_total = 0;
     // workspace layout (bytes)
     size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, o_toptab = 0, o_dsblk = 0, o_stcnt = 0;
+    size_t o_segs = 0, o_blkseg = 0;
     size_t tables_bytes = 0;
     size_t o_prefix = 0, o_partial = 0, o_ds = 0, o_s0 = 0, o_s1 = 0, ws_bytes = 0;
     size_t o_hx = 0, o_hper = 0, o_hfb = 0, o_hsnr = 0, ws_host_bytes = 0;
@@ -209,25 +223,77 @@ void fixed_point(double f, uint64_t* fi, uint64_t* ff) {
 }
 
 ffa_status build_plan(Plan& pl) {
-    const double tsamp = pl.tsamp;
-    const double f0 = pl.pmin / ((double)pl.bmin * tsamp);     // Sec. 5.6: tau = Pmin / bmin
-    const double fg = ((double)pl.bmax + 1.0) / (double)pl.bmin;  // Sec. 5.3
-    int64_t ds_off = 0, first = 0;
-    std::vector<double> fac;
-    for (int k = 0;; ++k) {
-        const double f = f0 * std::pow(fg, (double)k);
-        if ((double)pl.bmin * tsamp * f > pl.pmax) break;
-        if (k > 4096) return fail(FFA_ERR_UNSUPPORTED, "too many octaves");
-        OctaveDesc od{};
-        od.nk = (int64_t)std::floor((double)pl.n / f);
-        od.out_off = ds_off;
-        od.first = first;
-        fixed_point(f, &od.f_int, &od.f_frac);
-        pl.oct.push_back(od);
-        fac.push_back(f);
-        ds_off += (int64_t)align_up((size_t)std::max<int64_t>(od.nk, 0), 4) + 4;
-        first += od.nk;
+    int64_t ds_off = 0, first = 0, trial = 0;
+    pl.series_trial0.clear();
+    pl.segs.clear();
+    pl.blk_seg.clear();
+    pl.prefix_len = 0;
+    pl.input_total = 0;
+    for (const SeriesSpec& sp : pl.series) {
+        PrefixSeg sg{sp.x_off, pl.prefix_len, sp.n, (int64_t)pl.blk_seg.size()};
+        const int64_t nb = (sp.n + prefix_chunk() - 1) / prefix_chunk();
+        if ((int64_t)pl.blk_seg.size() + nb > INT32_MAX) return fail(FFA_ERR_UNSUPPORTED, "input too long");
+        pl.blk_seg.insert(pl.blk_seg.end(), (size_t)nb, (int)pl.segs.size());
+        pl.segs.push_back(sg);
+        pl.prefix_len += sp.n + 1;
+        pl.input_total += sp.n;
+        const double tsamp = sp.tsamp;
+        const double f0 = sp.pmin / ((double)sp.bmin * tsamp);        // Sec. 5.6: tau = Pmin / bmin
+        const double fg = ((double)sp.bmax + 1.0) / (double)sp.bmin;  // Sec. 5.3
+        const size_t oct0 = pl.oct.size();
+        std::vector<double> fac;
+        for (int k = 0;; ++k) {
+            const double f = f0 * std::pow(fg, (double)k);
+            if ((double)sp.bmin * tsamp * f > sp.pmax) break;
+            if (k > 4096) return fail(FFA_ERR_UNSUPPORTED, "too many octaves");
+            OctaveDesc od{};
+            od.nk = (int64_t)std::floor((double)sp.n / f);
+            od.out_off = ds_off;
+            od.x_off = sp.x_off;
+            od.x_n = sp.n;
+            od.pre_off = sg.pre_off;
+            fixed_point(f, &od.f_int, &od.f_frac);
+            pl.oct.push_back(od);
+            fac.push_back(f);
+            ds_off += (int64_t)align_up((size_t)std::max<int64_t>(od.nk, 0), 4) + 4;
+            first += od.nk;
+        }
+        pl.series_trial0.push_back(trial);
+        // Transforms in (octave, p) order (Sec. 5.3, Fig. 4).
+        for (size_t kk = 0; kk < fac.size(); ++kk) {
+            const OctaveDesc& od = pl.oct[oct0 + kk];
+            const double f = fac[kk];
+            const double var = (f == std::floor(f)) ? f : f - 1.0 / 3.0;  // App. A.4
+            for (int p = sp.bmin; p <= sp.bmax; ++p) {
+                const int64_t m64 = od.nk / p;
+                if (m64 < 2) continue;
+                if (m64 * p >= (int64_t(1) << 31))
+                    return fail(FFA_ERR_UNSUPPORTED, "transform too large");
+                const int m = (int)m64;
+                int64_t kept = 0;  // rows with s (p + 1) < p (m - 1)  (Sec. 2.3)
+                kept = (int64_t)p * (m - 1) > 0 ? ((int64_t)p * (m - 1) - 1) / (p + 1) + 1 : 0;
+                if (kept > m) kept = m;
+                TransformDesc t{};
+                t.src_off = od.out_off;
+                t.scratch_off = 0;
+                t.trial0 = trial;
+                t.tau = tsamp * f;
+                t.p = p;
+                t.m = m;
+                t.kept = (int)kept;
+                t.depth = depth_for(m, p, pl.row_cap);
+                t.chunk = top_chunk(p, pl.W.wmax, true);
+                if (t.chunk < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
+                t.inv_std = (float)(1.0 / std::sqrt((double)m * var));
+                pl.trs.push_back(t);
+                trial += kept;
+                pl.folded += (int64_t)m * p;
+                pl.max_rows = std::max(pl.max_rows, m);
+                pl.max_p = std::max(pl.max_p, p);
+            }
+        }
     }
+    pl.series_trial0.push_back(trial);
     pl.ds_total = first;
     pl.ds_floats = ds_off;
     for (size_t k = 0; k < pl.oct.size(); ++k)
@@ -235,38 +301,6 @@ ffa_status build_plan(Plan& pl) {
             if (s > INT32_MAX) return fail(FFA_ERR_UNSUPPORTED, "octave too long");
             pl.ds_blocks.push_back(make_int2((int)k, (int)s));
         }
-    // Transforms in (octave, p) order (Sec. 5.3, Fig. 4).
-    int64_t trial = 0;
-    for (size_t k = 0; k < pl.oct.size(); ++k) {
-        const double f = fac[k];
-        const double var = (f == std::floor(f)) ? f : f - 1.0 / 3.0;  // App. A.4
-        for (int p = pl.bmin; p <= pl.bmax; ++p) {
-            const int64_t m64 = pl.oct[k].nk / p;
-            if (m64 < 2) continue;
-            if (m64 * p >= (int64_t(1) << 31)) return fail(FFA_ERR_UNSUPPORTED, "transform too large");
-            const int m = (int)m64;
-            int64_t kept = 0;  // rows with s (p + 1) < p (m - 1)  (Sec. 2.3)
-            kept = (int64_t)p * (m - 1) > 0 ? ((int64_t)p * (m - 1) - 1) / (p + 1) + 1 : 0;
-            if (kept > m) kept = m;
-            TransformDesc t{};
-            t.src_off = pl.oct[k].out_off;
-            t.scratch_off = 0;
-            t.trial0 = trial;
-            t.tau = tsamp * f;
-            t.p = p;
-            t.m = m;
-            t.kept = (int)kept;
-            t.depth = depth_for(m, p, pl.row_cap);
-            t.chunk = top_chunk(p, pl.W.wmax, true);
-            if (t.chunk < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
-            t.inv_std = (float)(1.0 / std::sqrt((double)m * var));
-            pl.trs.push_back(t);
-            trial += kept;
-            pl.folded += (int64_t)m * p;
-            pl.max_rows = std::max(pl.max_rows, m);
-            pl.max_p = std::max(pl.max_p, p);
-        }
-    }
     pl.ntrials = trial;
     const int wmax = pl.W.wmax;
     const int nw = pl.W.nw;
@@ -393,15 +427,19 @@ ffa_status build_plan(Plan& pl) {
     o = align_up(o + pl.ds_blocks.size() * sizeof(int2), 256);
     pl.o_stcnt = o;
     o = align_up(o + pl.stage_count.size() * sizeof(int), 256);
+    pl.o_segs = o;
+    o = align_up(o + pl.segs.size() * sizeof(PrefixSeg), 256);
+    pl.o_blkseg = o;
+    o = align_up(o + pl.blk_seg.size() * sizeof(int), 256);
     pl.tables_bytes = std::max<size_t>(o, 256);
 
     // Workspace: status | tables | prefix | chunk sums | series | scratch 0 | scratch 1
-    pl.nchunks = (pl.n + prefix_chunk() - 1) / prefix_chunk();
+    pl.nchunks = (int64_t)pl.blk_seg.size();
     size_t w = kStatusBytes;
     pl.o_tables = w;
     w = align_up(w + pl.tables_bytes, 256);
     pl.o_prefix = w;
-    w = align_up(w + (size_t)(pl.n + 1) * sizeof(float2), 256);
+    w = align_up(w + (size_t)pl.prefix_len * sizeof(float2), 256);
     pl.o_partial = w;
     w = align_up(w + (size_t)pl.nchunks * sizeof(float2), 256);
     pl.o_ds = w;
@@ -443,61 +481,163 @@ ffa_status ensure_pinned(Plan& pl) {
     std::memcpy(h + pl.o_toptab, pl.top_tables.data(), pl.top_tables.size() * sizeof(int));
     std::memcpy(h + pl.o_dsblk, pl.ds_blocks.data(), pl.ds_blocks.size() * sizeof(int2));
     std::memcpy(h + pl.o_stcnt, pl.stage_count.data(), pl.stage_count.size() * sizeof(int));
+    std::memcpy(h + pl.o_segs, pl.segs.data(), pl.segs.size() * sizeof(PrefixSeg));
+    std::memcpy(h + pl.o_blkseg, pl.blk_seg.data(), pl.blk_seg.size() * sizeof(int));
     pl.pinned = p;
     return FFA_OK;
 }
 
-using PlanKey = std::tuple<int64_t, double, double, double, int, int, std::vector<int>>;
-std::map<PlanKey, std::unique_ptr<Plan>> g_plans;
-
-ffa_status get_plan(int64_t n, double tsamp, double pmin, double pmax, int bmin, int bmax,
-                    const int32_t* h_widths, int32_t nw, Plan** out) {
-    ffa_status st = check_search(n, tsamp, pmin, pmax, bmin, bmax);
-    if (st != FFA_OK) return st;
-    Widths W;
-    st = make_widths(h_widths, nw, bmin - 1, &W);  // widths below the smallest base period
-    if (st != FFA_OK) return st;
-    PlanKey key{n, tsamp, pmin, pmax, bmin, bmax, std::vector<int>(h_widths, h_widths + nw)};
-    std::lock_guard<std::mutex> lk(g_plan_mu);
-    auto it = g_plans.find(key);
-    if (it != g_plans.end()) {
-        *out = it->second.get();
-        return FFA_OK;
+// Plan of a list of series, built afresh.  Widths must lie below every series' bmin.
+ffa_status make_plan_series(const std::vector<SeriesSpec>& series, const int32_t* h_widths,
+                            int32_t nw, std::unique_ptr<Plan>* out) {
+    if (series.empty()) return fail(FFA_ERR_ARG, "no series");
+    int bmin_all = INT32_MAX;
+    int64_t span = 0;
+    for (const SeriesSpec& s : series) {
+        ffa_status st = check_search(s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax);
+        if (st != FFA_OK) return st;
+        if (s.x_off < 0) return fail(FFA_ERR_ARG, "negative series offset");
+        bmin_all = std::min(bmin_all, s.bmin);
+        span = std::max(span, s.x_off + s.n);
     }
-    auto pl = std::make_unique<Plan>();
-    pl->n = n;
-    pl->tsamp = tsamp;
-    pl->pmin = pmin;
-    pl->pmax = pmax;
-    pl->bmin = bmin;
-    pl->bmax = bmax;
-    pl->widths.assign(h_widths, h_widths + nw);
-    pl->W = W;
+    Widths W;
+    ffa_status st = make_widths(h_widths, nw, bmin_all - 1, &W);  // below the smallest base period
+    if (st != FFA_OK) return st;
+    std::unique_ptr<Plan> pl;
     for (int cap = kBottomMaxRows;;) {
+        pl = std::make_unique<Plan>();
+        pl->series = series;
+        pl->n = span;
+        pl->widths.assign(h_widths, h_widths + nw);
+        pl->W = W;
+        pl->row_cap = cap;
         st = build_plan(*pl);
         if (st != kRetrySmaller) break;
         // sub-trees of different widths share one launch: lower the row limit and replan
         cap = std::min(cap, pl->row_cap) - 1;
         if (cap < 2) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
-        auto fresh = std::make_unique<Plan>();
-        fresh->n = n; fresh->tsamp = tsamp; fresh->pmin = pmin; fresh->pmax = pmax;
-        fresh->bmin = bmin; fresh->bmax = bmax; fresh->widths = pl->widths; fresh->W = W;
-        fresh->row_cap = cap;
-        pl = std::move(fresh);
     }
     if (st != FFA_OK) return st;
-    if (g_plans.size() > 64) g_plans.clear();
-    *out = pl.get();
-    g_plans[key] = std::move(pl);
+    *out = std::move(pl);
+    return FFA_OK;
+}
+
+// Plans are cached by parameters for the life of the process (or until
+// ffa_plan_cache_clear): their page-locked tables are the source of copies that a
+// captured CUDA graph replays, so they are never evicted behind the caller's back.
+using PlanKey = std::pair<std::vector<SeriesSpec>, std::vector<int>>;
+std::map<PlanKey, std::unique_ptr<Plan>> g_plans;
+
+ffa_status get_plan_series(const std::vector<SeriesSpec>& series, const int32_t* h_widths,
+                           int32_t nw, Plan** out) {
+    if (nw > 0 && !h_widths) return fail(FFA_ERR_ARG, "widths is null");
+    PlanKey key{series, std::vector<int>(h_widths, h_widths + std::max(nw, 0))};
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        auto it = g_plans.find(key);
+        if (it != g_plans.end()) {
+            *out = it->second.get();
+            return FFA_OK;
+        }
+    }
+    std::unique_ptr<Plan> pl;
+    ffa_status st = make_plan_series(series, h_widths, nw, &pl);
+    if (st != FFA_OK) return st;
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto ins = g_plans.emplace(key, std::move(pl));  // a concurrent twin keeps the first
+    *out = ins.first->second.get();
+    return FFA_OK;
+}
+
+ffa_status get_plan(int64_t n, double tsamp, double pmin, double pmax, int bmin, int bmax,
+                    const int32_t* h_widths, int32_t nw, Plan** out) {
+    return get_plan_series({SeriesSpec{0, n, tsamp, pmin, pmax, bmin, bmax}}, h_widths, nw, out);
+}
+
+// A batch of series cut into chunks that each run as one periodogram launch sequence
+// within a workspace budget.
+struct BatchChunk {
+    int first, count;   // series [first, first + count)
+    int64_t x_lo;       // input offset of the chunk (its series' offsets are relative)
+    int64_t trial0;     // first trial of the chunk in the batch output
+    std::unique_ptr<Plan> plan;
+};
+struct Batch {
+    std::vector<BatchChunk> chunks;
+    std::vector<int64_t> trial0;  // per series, + total
+    size_t ws_bytes = 0;
+    int ntransforms = 0;
+    int64_t folded = 0, input = 0;
+};
+using BatchKey = std::tuple<std::vector<SeriesSpec>, std::vector<int>, size_t>;
+std::map<BatchKey, std::unique_ptr<Batch>> g_batches;
+
+ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t* h_widths,
+                     int32_t nw, size_t budget, Batch** out) {
+    if (!h_series || nseries < 1) return fail(FFA_ERR_ARG, "no series");
+    if (nw > 0 && !h_widths) return fail(FFA_ERR_ARG, "widths is null");
+    std::vector<SeriesSpec> all(nseries);
+    for (int i = 0; i < nseries; ++i) {
+        const ffa_series& s = h_series[i];
+        if (s.offset < 0) return fail(FFA_ERR_ARG, "series %d has a negative offset", i);
+        all[i] = SeriesSpec{s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax};
+    }
+    BatchKey key{all, std::vector<int>(h_widths, h_widths + std::max(nw, 0)), budget};
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        auto it = g_batches.find(key);
+        if (it != g_batches.end()) {
+            *out = it->second.get();
+            return FFA_OK;
+        }
+    }
+    auto B = std::make_unique<Batch>();
+    // workspace of each series searched alone, the unit of the chunk budget
+    std::vector<size_t> est(nseries);
+    for (int i = 0; i < nseries; ++i) {
+        SeriesSpec s = all[i];
+        s.x_off = 0;
+        std::unique_ptr<Plan> p1;
+        ffa_status st = make_plan_series({s}, h_widths, nw, &p1);
+        if (st != FFA_OK) return st;
+        est[i] = p1->ws_bytes;
+    }
+    int64_t trial = 0;
+    for (int i = 0; i < nseries;) {
+        int j = i;
+        size_t acc = 0;
+        while (j < nseries && (j == i || acc + est[j] <= budget)) acc += est[j++];
+        std::vector<SeriesSpec> part(all.begin() + i, all.begin() + j);
+        int64_t lo = part[0].x_off;
+        for (const SeriesSpec& s : part) lo = std::min(lo, s.x_off);
+        for (SeriesSpec& s : part) s.x_off -= lo;
+        BatchChunk c{i, j - i, lo, trial, nullptr};
+        ffa_status st = make_plan_series(part, h_widths, nw, &c.plan);
+        if (st != FFA_OK) return st;
+        for (int q = 0; q < j - i; ++q) B->trial0.push_back(trial + c.plan->series_trial0[q]);
+        trial += c.plan->ntrials;
+        B->ws_bytes = std::max(B->ws_bytes, c.plan->ws_bytes);
+        B->ntransforms += (int)c.plan->trs.size();
+        B->folded += c.plan->folded;
+        for (const SeriesSpec& s : part) B->input += s.n;
+        B->chunks.push_back(std::move(c));
+        i = j;
+    }
+    B->trial0.push_back(trial);
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto ins = g_batches.emplace(key, std::move(B));
+    *out = ins.first->second.get();
     return FFA_OK;
 }
 
 // Issues the whole periodogram on `st`: tables upload, prefix, downsampling, then
 // the FFA + S/N launches group by group.
 ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d_periods,
-                           int32_t* d_foldbins, float* d_snr, char* ws, cudaStream_t st) {
+                           int32_t* d_foldbins, float* d_snr, char* ws, cudaStream_t st,
+                           bool reset_status = true) {
     unsigned* status = reinterpret_cast<unsigned*>(ws);
-    FFA_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st), "cudaMemsetAsync");
+    if (reset_status)  // a batch keeps the status of its earlier chunks
+        FFA_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned), st), "cudaMemsetAsync");
     FFA_CUDA(cudaMemcpyAsync(ws + pl.o_tables, pl.pinned, pl.tables_bytes, cudaMemcpyHostToDevice,
                              st),
              "cudaMemcpyAsync(tables)");
@@ -510,8 +650,16 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     float* s0 = reinterpret_cast<float*>(ws + pl.o_s0);
     float* s1 = reinterpret_cast<float*>(ws + pl.o_s1);
 
-    PrefixParams xp{d_x, dtype, pl.n, reinterpret_cast<float2*>(ws + pl.o_partial), prefix,
-                    pl.nchunks};
+    PrefixParams xp{};
+    xp.x = d_x;
+    xp.dtype = dtype;
+    xp.segs = reinterpret_cast<const PrefixSeg*>(ws + pl.o_tables + pl.o_segs);
+    xp.blk_seg = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_blkseg);
+    xp.nsegs = (int)pl.segs.size();
+    xp.partial = reinterpret_cast<float2*>(ws + pl.o_partial);
+    xp.prefix = prefix;
+    xp.nchunks = pl.nchunks;
+    xp.total = pl.input_total;
     FFA_CUDA(launch_prefix(xp, st), "prefix launch");
     DownsampleParams dp{};
     dp.x = d_x;
@@ -664,7 +812,15 @@ ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_o
         reinterpret_cast<float2*>(ws + kStatusBytes + align_up((size_t)(n + 1) * sizeof(float2), 256));
     FFA_CUDA(cudaMemsetAsync(ws, 0, sizeof(unsigned), st), "cudaMemsetAsync");
     if (nk == 0) return FFA_OK;
-    PrefixParams pp{d_x, FFA_F32, n, partial, prefix, nch};
+    PrefixParams pp{};
+    pp.x = d_x;
+    pp.dtype = FFA_F32;
+    pp.single = PrefixSeg{0, 0, n, 0};
+    pp.nsegs = 1;
+    pp.partial = partial;
+    pp.prefix = prefix;
+    pp.nchunks = nch;
+    pp.total = n;
     FFA_CUDA(launch_prefix(pp, st), "prefix launch");
     DownsampleParams dp{};
     dp.x = d_x;
@@ -679,6 +835,9 @@ ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_o
     dp.total = nk;
     dp.out = d_out;
     dp.single.nk = nk;
+    dp.single.x_off = 0;
+    dp.single.x_n = n;
+    dp.single.pre_off = 0;
     fixed_point(factor, &dp.single.f_int, &dp.single.f_frac);
     FFA_CUDA(launch_downsample(dp, st), "downsample launch");
     return FFA_OK;
@@ -849,6 +1008,60 @@ ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double t
     if (st != FFA_OK) return st;
     return run_periodogram(*pl, d_x, dtype, d_periods, d_foldbins, d_snr, static_cast<char*>(d_ws),
                            static_cast<cudaStream_t>(stream));
+}
+
+ffa_status ffa_plan_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_batches.clear();
+    g_plans.clear();
+    return FFA_OK;
+}
+
+ffa_status ffa_batch_plan(const ffa_series* h_series, int32_t nseries, const int32_t* h_widths,
+                          int32_t nw, size_t ws_budget, int64_t* h_trial_offsets,
+                          ffa_batch_info* out) {
+    if (!out) return fail(FFA_ERR_ARG, "out is null");
+    Batch* B = nullptr;
+    ffa_status st = get_batch(h_series, nseries, h_widths, nw, ws_budget, &B);
+    if (st != FFA_OK) return st;
+    std::memset(out, 0, sizeof(*out));
+    out->ntrials = B->trial0.back();
+    out->nchunks = (int32_t)B->chunks.size();
+    out->ntransforms = B->ntransforms;
+    out->folded_samples = B->folded;
+    out->input_samples = B->input;
+    out->workspace_bytes = B->ws_bytes;
+    if (h_trial_offsets)
+        std::memcpy(h_trial_offsets, B->trial0.data(), B->trial0.size() * sizeof(int64_t));
+    return FFA_OK;
+}
+
+ffa_status ffa_periodogram_batch(const void* d_x, ffa_dtype dtype, const ffa_series* h_series,
+                                 int32_t nseries, const int32_t* h_widths, int32_t nw,
+                                 size_t ws_budget, double* d_periods, int32_t* d_foldbins,
+                                 float* d_snr, int64_t ntrials_cap, void* d_ws, size_t ws_bytes,
+                                 void* stream) {
+    if (!d_x || !d_periods || !d_foldbins || !d_snr || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
+    if (dtype != FFA_F32 && dtype != FFA_F16 && dtype != FFA_I8) return fail(FFA_ERR_ARG, "bad dtype");
+    if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
+    Batch* B = nullptr;
+    ffa_status st = get_batch(h_series, nseries, h_widths, nw, ws_budget, &B);
+    if (st != FFA_OK) return st;
+    if (ntrials_cap < B->trial0.back()) return fail(FFA_ERR_CAPACITY, "ntrials_cap too small");
+    if (ws_bytes < B->ws_bytes) return fail(FFA_ERR_CAPACITY, "workspace needs %zu bytes", B->ws_bytes);
+    const size_t esize = dtype == FFA_F32 ? 4 : (dtype == FFA_F16 ? 2 : 1);
+    bool first = true;
+    for (const BatchChunk& c : B->chunks) {
+        st = ensure_pinned(*c.plan);
+        if (st != FFA_OK) return st;
+        st = run_periodogram(*c.plan, static_cast<const char*>(d_x) + (size_t)c.x_lo * esize, dtype,
+                             d_periods + c.trial0, d_foldbins + c.trial0,
+                             d_snr + c.trial0 * c.plan->W.nw, static_cast<char*>(d_ws),
+                             static_cast<cudaStream_t>(stream), first);
+        first = false;
+        if (st != FFA_OK) return st;
+    }
+    return FFA_OK;
 }
 
 ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, double pmin,

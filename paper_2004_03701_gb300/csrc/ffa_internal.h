@@ -194,7 +194,9 @@ __host__ __device__ inline TopLayout top_layout(int K, int L, int p, int wmax, b
 struct OctaveDesc {
     int64_t out_off;   // float offset of the octave's series in the series buffer
     int64_t nk;        // samples: floor(n / f)
-    int64_t first;     // index of its first output in the flat launch
+    int64_t x_off;     // first raw sample of its series in the input
+    int64_t x_n;       // raw samples of its series
+    int64_t pre_off;   // first prefix sum of its series
     uint64_t f_int;    // floor(f)
     uint64_t f_frac;   // (f - floor(f)) * 2^64, exact
 };
@@ -224,13 +226,27 @@ enum KernelKind : int {
 // ------------------------------------------------------------------------------
 // Launch parameter blocks.
 // ------------------------------------------------------------------------------
+// One series of the prefix-sum pass.  Its prefix sums depend on its own samples only
+// (the scan restarts at every series), so a series downsamples to the same values
+// wherever it sits in the input and whatever else is searched with it.
+struct PrefixSeg {
+    int64_t x_off;    // first sample of the series in the input
+    int64_t pre_off;  // its n + 1 exclusive prefix sums start here
+    int64_t n;        // samples
+    int64_t blk0;     // its first chunk (CTA of the partial and final passes)
+};
+
 struct PrefixParams {
     const void* x;
-    int dtype;            // ffa_dtype
-    int64_t n;
-    float2* partial;      // per-chunk double-float sums
-    float2* prefix;       // n + 1 double-float exclusive prefix sums
-    int64_t nchunks;
+    int dtype;              // ffa_dtype
+    const PrefixSeg* segs;  // device table of nsegs series, or nullptr: `single`
+    const int* blk_seg;     // series of each chunk (nullptr: series 0)
+    PrefixSeg single;
+    int nsegs;
+    float2* partial;        // per-chunk double-float sums, then their per-series scan
+    float2* prefix;         // double-float exclusive prefix sums
+    int64_t nchunks;        // chunks over all series
+    int64_t total;          // samples over all series
 };
 
 constexpr int kDownsampleThreads = 256;

@@ -69,13 +69,19 @@ constexpr int kPrefixThreads = 256;
 constexpr int kPrefixPerThread = 16;
 constexpr int kPrefixChunk = kPrefixThreads * kPrefixPerThread;
 
-// Loads a chunk into shared memory (coalesced), returns this thread's 16 samples.
-__device__ __forceinline__ void prefix_load(const PrefixParams& P, int64_t base, float* sh,
-                                            float v[kPrefixPerThread]) {
+__device__ __forceinline__ PrefixSeg prefix_seg(const PrefixParams& P, int64_t chunk) {
+    if (!P.segs) return P.single;
+    return P.segs[P.blk_seg ? P.blk_seg[chunk] : 0];
+}
+
+// Loads the chunk [base, base + 4096) of a series ending at `end` into shared memory
+// (coalesced), returns this thread's 16 consecutive samples.
+__device__ __forceinline__ void prefix_load(const PrefixParams& P, int64_t base, int64_t end,
+                                            float* sh, float v[kPrefixPerThread]) {
     for (int q = 0; q < kPrefixPerThread; ++q) {
         int e = q * kPrefixThreads + threadIdx.x;
         int64_t g = base + e;
-        float val = g < P.n ? load_sample(P.x, P.dtype, g) : 0.f;
+        float val = g < end ? load_sample(P.x, P.dtype, g) : 0.f;
         sh[(e >> 4) * 17 + (e & 15)] = val;  // padded: conflict-free column reads
     }
     __syncthreads();
@@ -111,8 +117,10 @@ __device__ __forceinline__ float2 block_exclusive_df(float2 a, float2* warp_tot,
 __global__ void __launch_bounds__(kPrefixThreads) prefix_partial_kernel(PrefixParams P) {
     __shared__ float sh[kPrefixThreads * 17];
     __shared__ float2 wt[kPrefixThreads / 32];
+    const PrefixSeg sg = prefix_seg(P, blockIdx.x);
     float v[kPrefixPerThread];
-    prefix_load(P, (int64_t)blockIdx.x * kPrefixChunk, sh, v);
+    prefix_load(P, sg.x_off + ((int64_t)blockIdx.x - sg.blk0) * kPrefixChunk, sg.x_off + sg.n, sh,
+                v);
     float2 acc = make_float2(0.f, 0.f);
     for (int q = 0; q < kPrefixPerThread; ++q) acc = df_add(acc, make_float2(v[q], 0.f));
     float2 tot;
@@ -120,36 +128,67 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_partial_kernel(PrefixPa
     if (threadIdx.x == 0) P.partial[blockIdx.x] = tot;
 }
 
-// One CTA: exclusive scan of the chunk sums, in place.
+// One warp per series: exclusive scan of the series' chunk sums, in place; each lane
+// takes kTopPerLane consecutive chunks per round.
+constexpr int kTopPerLane = 4;
 __global__ void __launch_bounds__(kPrefixThreads) prefix_top_kernel(PrefixParams P) {
-    __shared__ float2 wt[kPrefixThreads / 32];
+    const int lane = threadIdx.x & 31;
+    const int64_t s = (int64_t)blockIdx.x * (kPrefixThreads / 32) + (threadIdx.x >> 5);
+    if (s >= P.nsegs) return;  // whole warps leave; no block-wide barrier follows
+    const PrefixSeg sg = P.segs ? P.segs[s] : P.single;
+    const int64_t nb = (sg.n + kPrefixChunk - 1) / kPrefixChunk;
+    float2* part = P.partial + sg.blk0;
     float2 carry = make_float2(0.f, 0.f);
-    for (int64_t b0 = 0; b0 < P.nchunks; b0 += kPrefixThreads) {
-        int64_t b = b0 + threadIdx.x;
-        float2 a = b < P.nchunks ? P.partial[b] : make_float2(0.f, 0.f);
+    for (int64_t b0 = 0; b0 < nb; b0 += 32 * kTopPerLane) {
+        const int64_t i0 = b0 + (int64_t)lane * kTopPerLane;
+        float2 v[kTopPerLane];
+        float2 loc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < kTopPerLane; ++q) {
+            v[q] = i0 + q < nb ? part[i0 + q] : make_float2(0.f, 0.f);
+            loc = df_add(loc, v[q]);
+        }
+        float2 inc = loc;
+        for (int o = 1; o < 32; o <<= 1) {
+            float2 u;
+            u.x = __shfl_up_sync(kFull, inc.x, o);
+            u.y = __shfl_up_sync(kFull, inc.y, o);
+            if (lane >= o) inc = df_add(u, inc);
+        }
+        float2 ex;
+        ex.x = __shfl_up_sync(kFull, inc.x, 1);
+        ex.y = __shfl_up_sync(kFull, inc.y, 1);
+        if (lane == 0) ex = make_float2(0.f, 0.f);
+        float2 run = df_add(carry, ex);
+#pragma unroll
+        for (int q = 0; q < kTopPerLane; ++q) {
+            if (i0 + q < nb) part[i0 + q] = run;
+            run = df_add(run, v[q]);
+        }
         float2 tot;
-        float2 ex = block_exclusive_df(a, wt, &tot);
-        if (b < P.nchunks) P.partial[b] = df_add(carry, ex);
+        tot.x = __shfl_sync(kFull, inc.x, 31);
+        tot.y = __shfl_sync(kFull, inc.y, 31);
         carry = df_add(carry, tot);
-        __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(kPrefixThreads) prefix_final_kernel(PrefixParams P) {
     __shared__ float sh[kPrefixThreads * 17];
     __shared__ float2 wt[kPrefixThreads / 32];
-    const int64_t base = (int64_t)blockIdx.x * kPrefixChunk;
+    const PrefixSeg sg = prefix_seg(P, blockIdx.x);
+    const int64_t local0 = ((int64_t)blockIdx.x - sg.blk0) * kPrefixChunk;  // in the series
     float v[kPrefixPerThread];
-    prefix_load(P, base, sh, v);
+    prefix_load(P, sg.x_off + local0, sg.x_off + sg.n, sh, v);
     float2 acc = make_float2(0.f, 0.f);
     for (int q = 0; q < kPrefixPerThread; ++q) acc = df_add(acc, make_float2(v[q], 0.f));
     float2 tot;
     float2 run = df_add(P.partial[blockIdx.x], block_exclusive_df(acc, wt, &tot));
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.prefix[0] = make_float2(0.f, 0.f);
-    const int64_t g0 = base + (int64_t)threadIdx.x * kPrefixPerThread;
+    float2* pre = P.prefix + sg.pre_off;
+    if (local0 == 0 && threadIdx.x == 0) pre[0] = make_float2(0.f, 0.f);
+    const int64_t g0 = local0 + (int64_t)threadIdx.x * kPrefixPerThread;
     for (int q = 0; q < kPrefixPerThread; ++q) {
         run = df_add(run, make_float2(v[q], 0.f));
-        if (g0 + q < P.n) P.prefix[g0 + q + 1] = run;
+        if (g0 + q < sg.n) pre[g0 + q + 1] = run;
     }
 }
 
@@ -170,25 +209,28 @@ __global__ void __launch_bounds__(kDownsampleThreads) downsample_kernel(Downsamp
         if (i64 >= od.nk) break;
         const uint64_t i = (uint64_t)i64;
         float out;
+        // window edges local to the series; prefix and samples indexed from its start
+        const int64_t xo = od.x_off;
         if (od.f_int == 1 && od.f_frac == 0) {
-            out = load_sample(P.x, P.dtype, (int64_t)i);
+            out = load_sample(P.x, P.dtype, xo + (int64_t)i);
         } else {
             const uint64_t a_frac = i * od.f_frac;
             const uint64_t a_int = i * od.f_int + __umul64hi(i, od.f_frac);
             uint64_t b_frac = a_frac + od.f_frac;
             uint64_t b_int = a_int + od.f_int + (b_frac < a_frac ? 1 : 0);
-            if (b_int >= (uint64_t)P.n) {  // the series ends inside the window
-                b_int = (uint64_t)P.n;
+            if (b_int >= (uint64_t)od.x_n) {  // the series ends inside the window
+                b_int = (uint64_t)od.x_n;
                 b_frac = 0;
             }
-            out = df_sub_to_float(P.prefix[b_int], P.prefix[a_int]);
+            const float2* pre = P.prefix + od.pre_off;
+            out = df_sub_to_float(pre[(int64_t)b_int], pre[(int64_t)a_int]);
             if (a_frac != 0) {
                 float al = __ull2float_rn(a_frac) * 5.42101086242752217e-20f;  // 2^-64
-                out = __fsub_rn(out, __fmul_rn(al, load_sample(P.x, P.dtype, (int64_t)a_int)));
+                out = __fsub_rn(out, __fmul_rn(al, load_sample(P.x, P.dtype, xo + (int64_t)a_int)));
             }
             if (b_frac != 0) {
                 float be = __ull2float_rn(b_frac) * 5.42101086242752217e-20f;
-                out = __fadd_rn(out, __fmul_rn(be, load_sample(P.x, P.dtype, (int64_t)b_int)));
+                out = __fadd_rn(out, __fmul_rn(be, load_sample(P.x, P.dtype, xo + (int64_t)b_int)));
             }
         }
         P.out[od.out_off + i64] = out;
@@ -1029,17 +1071,20 @@ int prefix_chunk() { return kPrefixChunk; }
 // Launchers.
 // ---------------------------------------------------------------------------------
 cudaError_t launch_prefix(const PrefixParams& P, cudaStream_t s) {
-    const double n = (double)P.n;
+    if (P.nchunks <= 0 || P.nsegs <= 0) return cudaSuccess;
+    const double n = (double)P.total;
+    const double es = P.dtype == 0 ? 4.0 : (P.dtype == 1 ? 2.0 : 1.0);
     {
-        LaunchScope ls(kPrefixPartial, 4.0 * n + 8.0 * P.nchunks, s);
+        LaunchScope ls(kPrefixPartial, es * n + 8.0 * P.nchunks, s);
         prefix_partial_kernel<<<(unsigned)P.nchunks, kPrefixThreads, 0, s>>>(P);
     }
     {
         LaunchScope ls(kPrefixTop, 16.0 * P.nchunks, s);
-        prefix_top_kernel<<<1, kPrefixThreads, 0, s>>>(P);
+        const int per = kPrefixThreads / 32;
+        prefix_top_kernel<<<(unsigned)((P.nsegs + per - 1) / per), kPrefixThreads, 0, s>>>(P);
     }
     {
-        LaunchScope ls(kPrefixFinal, 4.0 * n + 8.0 * (n + 1) + 8.0 * P.nchunks, s);
+        LaunchScope ls(kPrefixFinal, es * n + 8.0 * (n + P.nsegs) + 8.0 * P.nchunks, s);
         prefix_final_kernel<<<(unsigned)P.nchunks, kPrefixThreads, 0, s>>>(P);
     }
     return cudaGetLastError();

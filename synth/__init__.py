@@ -12,8 +12,9 @@ amplitude a is the Z-statistic (S/N) of a perfectly matched template.
 """
 from __future__ import annotations
 
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
-from typing import List, Optional, Tuple
+from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -115,3 +116,97 @@ def small_integer_block(m: int, p: int, seed: int, lo: int = -8, hi: int = 8) ->
 
 def normal_block(m: int, p: int, seed: int) -> np.ndarray:
     return rng(seed).standard_normal((m, p)).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------------
+# Batches of series (many dedispersed time series searched together)
+
+@dataclass
+class SeriesParams:
+    offset: int        # first sample in the batch buffer
+    n: int
+    tsamp: float
+    pmin: float
+    pmax: float
+    bmin: int
+    bmax: int
+    pulses: List[Pulse] = field(default_factory=list)
+
+
+@dataclass
+class BatchWorkload:
+    name: str
+    x: np.ndarray                   # float32, all series one after another
+    series: List[SeriesParams]
+    widths: Tuple[int, ...]
+
+    @property
+    def n(self) -> int:
+        return int(sum(s.n for s in self.series))
+
+    def series_x(self, i: int) -> np.ndarray:
+        s = self.series[i]
+        return self.x[s.offset:s.offset + s.n]
+
+
+def _fill_batch(series: Sequence[SeriesParams], seeds: Sequence[int], threads: int) -> np.ndarray:
+    """Concatenated float32 buffer of the series' noise + pulses, drawn in parallel
+    (each series from its own seeded generator, so the result does not depend on
+    the number of threads)."""
+    total = max((s.offset + s.n for s in series), default=0)
+    x = np.zeros(total, np.float32)
+
+    def one(k):
+        s = series[k]
+        x[s.offset:s.offset + s.n] = make_series(s.n, s.tsamp, seeds[k], s.pulses)
+
+    with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
+        list(ex.map(one, range(len(series))))
+    return x
+
+
+def batch_uneven(nseries: int = 256, nmin: int = 2 ** 20, nmax: int = 2 ** 23,
+                 seed: Optional[int] = None, threads: int = 16) -> BatchWorkload:
+    """Series of uneven length n ~ U[nmin, nmax] at 64 us, each N(0,1) noise plus one
+    Gaussian pulse train, each with its own period range inside 0.1-30 s (log-uniform
+    Pmin in [0.1, 3] s, Pmax/Pmin log-uniform in [3, 100], capped at 30 s); bins
+    240-260, 11 widths.  Series are stored back to back in one buffer."""
+    seed = SEED_BASE + 3 if seed is None else seed
+    r = rng(seed)
+    tsamp = 64e-6
+    series, seeds, off = [], [], 0
+    for i in range(nseries):
+        n = int(r.integers(nmin, nmax + 1))
+        pmin = float(np.exp(r.uniform(np.log(0.1), np.log(3.0))))
+        pmax = min(30.0, pmin * float(np.exp(r.uniform(np.log(3.0), np.log(100.0)))))
+        per = float(np.exp(r.uniform(np.log(pmin), np.log(pmax))))
+        pulse = Pulse(per, float(r.uniform(0.01, 0.05)), float(r.uniform(8.0, 20.0)),
+                      float(r.uniform()))
+        series.append(SeriesParams(off, n, tsamp, pmin, pmax, 240, 260, [pulse]))
+        seeds.append(seed * 7919 + i)
+        off += n
+    return BatchWorkload("batch_uneven_%dx2^20-2^23_64us" % nseries if (nmin, nmax) ==
+                         (2 ** 20, 2 ** 23) else "batch_uneven_%d" % nseries,
+                         _fill_batch(series, seeds, threads), series, WIDTHS_11)
+
+
+def batch_int8_stress(nseries: int = 1024, n: int = 2 ** 21, seed: Optional[int] = None,
+                      threads: int = 16) -> BatchWorkload:
+    """nseries series of n samples at 64 us, N(0,1) noise (the white series left after
+    red-noise removal), one Gaussian pulse train in every tenth series; periods
+    0.1-10 s, bins 480-520, the 16-width set.  Meant to be normalised and stored as
+    int8 before the search."""
+    seed = SEED_BASE + 5 if seed is None else seed
+    r = rng(seed)
+    tsamp = 64e-6
+    series, seeds = [], []
+    for i in range(nseries):
+        pulses = []
+        if i % 10 == 0:
+            pulses = [Pulse(float(np.exp(r.uniform(np.log(0.1), np.log(10.0)))),
+                            float(r.uniform(0.01, 0.05)), float(r.uniform(8.0, 20.0)),
+                            float(r.uniform()))]
+        series.append(SeriesParams(i * n, n, tsamp, 0.1, 10.0, 480, 520, pulses))
+        seeds.append(seed * 7919 + i)
+    return BatchWorkload("batch_int8_%dx2^21_64us" % nseries, _fill_batch(series, seeds, threads),
+                         series, WIDTHS_16)

@@ -108,3 +108,49 @@ def test_width_sets_fit_the_plan(lib):
     for wl in (synth.WIDTHS_11, synth.WIDTHS_16):
         info = ffa.periodogram_plan(2 ** 21, 64e-6, 0.1, 10.0, 480, 520, wl)
         assert info.nwidths == len(wl)
+
+
+def _batch_series(nseries=6, seed=11):
+    b = synth.batch_uneven(nseries, 2 ** 15, 2 ** 17, seed=seed, threads=1)
+    return b, [ffa.Series(s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax)
+               for s in b.series]
+
+
+def test_batch_plan_matches_per_series_oracle_plans(lib):
+    b, ser = _batch_series()
+    info, offs = ffa.batch_plan(ser, b.widths)
+    plans = [oracle.plan(s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax) for s in ser]
+    assert list(np.diff(offs)) == [pl.n_trials for pl in plans]
+    assert offs[0] == 0 and info.ntrials == offs[-1]
+    assert info.ntransforms == sum(pl.n_transforms for pl in plans)
+    assert info.folded_samples == sum(int((pl.tr_m * pl.tr_p).sum()) for pl in plans)
+    assert info.input_samples == sum(s.n for s in ser)
+
+
+def test_batch_chunks_follow_the_budget(lib):
+    b, ser = _batch_series()
+    one, offs1 = ffa.batch_plan(ser, b.widths, ws_budget=1 << 40)
+    each, offs2 = ffa.batch_plan(ser, b.widths, ws_budget=1)
+    assert one.nchunks == 1 and each.nchunks == len(ser)
+    assert np.array_equal(offs1, offs2)
+    alone = [ffa.periodogram_plan(s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax, b.widths)
+             for s in ser]
+    # one series per chunk: the workspace of the largest series searched alone
+    assert each.workspace_bytes == max(a.workspace_bytes for a in alone)
+    assert one.workspace_bytes >= each.workspace_bytes
+    mid, _ = ffa.batch_plan(ser, b.widths, ws_budget=2 * each.workspace_bytes)
+    assert 1 < mid.nchunks < len(ser)
+
+
+def test_batch_rejects_bad_series(lib):
+    b, ser = _batch_series(3)
+    bad = list(ser)
+    bad[1] = ffa.Series(-5, ser[1].n, ser[1].tsamp, ser[1].pmin, ser[1].pmax, 240, 260)
+    with pytest.raises(ffa.FFAError):
+        ffa.batch_plan(bad, b.widths)
+    bad = list(ser)
+    bad[2] = ffa.Series(ser[2].offset, ser[2].n, ser[2].tsamp, ser[2].pmin, ser[2].pmax, 40, 44)
+    with pytest.raises(ffa.FFAError):   # width 63 is not below bmin = 40
+        ffa.batch_plan(bad, b.widths)
+    with pytest.raises(ffa.FFAError):
+        ffa.batch_plan([], b.widths)
