@@ -49,7 +49,7 @@ UNIT = "samples/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ffa", "reference"], default="ffa")
     ap.add_argument("--workload", choices=["survey", "plain_small"] + list(BATCH_WORKLOADS),

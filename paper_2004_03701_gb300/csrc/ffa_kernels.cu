@@ -128,47 +128,33 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_partial_kernel(PrefixPa
     if (threadIdx.x == 0) P.partial[blockIdx.x] = tot;
 }
 
-// One warp per series: exclusive scan of the series' chunk sums, in place; each lane
-// takes kTopPerLane consecutive chunks per round.
-constexpr int kTopPerLane = 4;
+// One CTA per series: exclusive scan of the series' chunk sums, in place; each thread
+// takes kTopPerThread consecutive chunks per round.
+constexpr int kTopPerThread = 4;
 __global__ void __launch_bounds__(kPrefixThreads) prefix_top_kernel(PrefixParams P) {
-    const int lane = threadIdx.x & 31;
-    const int64_t s = (int64_t)blockIdx.x * (kPrefixThreads / 32) + (threadIdx.x >> 5);
-    if (s >= P.nsegs) return;  // whole warps leave; no block-wide barrier follows
-    const PrefixSeg sg = P.segs ? P.segs[s] : P.single;
+    __shared__ float2 wt[kPrefixThreads / 32];
+    const PrefixSeg sg = P.segs ? P.segs[blockIdx.x] : P.single;
     const int64_t nb = (sg.n + kPrefixChunk - 1) / kPrefixChunk;
     float2* part = P.partial + sg.blk0;
     float2 carry = make_float2(0.f, 0.f);
-    for (int64_t b0 = 0; b0 < nb; b0 += 32 * kTopPerLane) {
-        const int64_t i0 = b0 + (int64_t)lane * kTopPerLane;
-        float2 v[kTopPerLane];
+    for (int64_t b0 = 0; b0 < nb; b0 += kPrefixThreads * kTopPerThread) {
+        const int64_t i0 = b0 + (int64_t)threadIdx.x * kTopPerThread;
+        float2 v[kTopPerThread];
         float2 loc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int q = 0; q < kTopPerLane; ++q) {
+        for (int q = 0; q < kTopPerThread; ++q) {
             v[q] = i0 + q < nb ? part[i0 + q] : make_float2(0.f, 0.f);
             loc = df_add(loc, v[q]);
         }
-        float2 inc = loc;
-        for (int o = 1; o < 32; o <<= 1) {
-            float2 u;
-            u.x = __shfl_up_sync(kFull, inc.x, o);
-            u.y = __shfl_up_sync(kFull, inc.y, o);
-            if (lane >= o) inc = df_add(u, inc);
-        }
-        float2 ex;
-        ex.x = __shfl_up_sync(kFull, inc.x, 1);
-        ex.y = __shfl_up_sync(kFull, inc.y, 1);
-        if (lane == 0) ex = make_float2(0.f, 0.f);
-        float2 run = df_add(carry, ex);
+        float2 tot;
+        float2 run = df_add(carry, block_exclusive_df(loc, wt, &tot));
 #pragma unroll
-        for (int q = 0; q < kTopPerLane; ++q) {
+        for (int q = 0; q < kTopPerThread; ++q) {
             if (i0 + q < nb) part[i0 + q] = run;
             run = df_add(run, v[q]);
         }
-        float2 tot;
-        tot.x = __shfl_sync(kFull, inc.x, 31);
-        tot.y = __shfl_sync(kFull, inc.y, 31);
         carry = df_add(carry, tot);
+        __syncthreads();  // wt is reused by the next round
     }
 }
 
@@ -1080,8 +1066,7 @@ cudaError_t launch_prefix(const PrefixParams& P, cudaStream_t s) {
     }
     {
         LaunchScope ls(kPrefixTop, 16.0 * P.nchunks, s);
-        const int per = kPrefixThreads / 32;
-        prefix_top_kernel<<<(unsigned)((P.nsegs + per - 1) / per), kPrefixThreads, 0, s>>>(P);
+        prefix_top_kernel<<<(unsigned)P.nsegs, kPrefixThreads, 0, s>>>(P);
     }
     {
         LaunchScope ls(kPrefixFinal, es * n + 8.0 * (n + P.nsegs) + 8.0 * P.nchunks, s);
