@@ -70,7 +70,7 @@ ProfAcc g_acc[kNumKinds];
 const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top",     "prefix_final",
                                      "downsample",     "ffa_bottom",     "ffa_bottom_snr",
                                      "ffa_top",        "boxcar_snr",     "normalise",
-                                     "ffa_persistent"};
+                                     "ffa_persistent", "top_prep"};
 
 cudaEvent_t pool_get() {
     if (!g_pool.empty()) {
@@ -122,7 +122,7 @@ struct Plan {
     std::vector<OctaveDesc> oct;
     std::vector<TransformDesc> trs;
     std::vector<WorkItem> items;
-    std::vector<int> top_tables;  // kTopTableInts per top-pass item (WorkItem::pad)
+    int ntop = 0;                 // top-pass items (records in the workspace)
     std::vector<int2> ds_blocks;  // downsampling CTAs: {octave, first output}
     std::vector<PrefixSeg> segs;  // prefix-sum pass: one per series
     std::vector<int> blk_seg;     // series of each prefix chunk
@@ -139,7 +139,7 @@ struct Plan {
     int max_rows = 0, max_p = 0;
     int64_t nchunks = 0, prefix_len = 0, input_total = 0;
     // workspace layout (bytes)
-    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, o_toptab = 0, o_dsblk = 0, o_stcnt = 0;
+    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, o_dsblk = 0, o_stcnt = 0, o_recs = 0;
     size_t o_segs = 0, o_blkseg = 0;
     size_t tables_bytes = 0;
     size_t o_prefix = 0, o_partial = 0, o_ds = 0, o_s0 = 0, o_s1 = 0, ws_bytes = 0;
@@ -378,23 +378,8 @@ ffa_status build_plan(Plan& pl) {
                 const int lim = score ? d.kept : nmax;
                 const int nb = (lim + K - 1) / K;
                 const int cnt = score ? nb : (1 << dout) * nb;
-                for (int i = 0; i < cnt; ++i) {
-                    // the item's target node and row block, as the kernel derives them
-                    const int node = i / nb, blk = i - node * nb;
-                    int st0 = 0, n0 = d.m;
-                    for (int bb = dout - 1; bb >= 0; --bb) {
-                        const int nh = n0 >> 1;
-                        if ((node >> bb) & 1) { st0 += nh; n0 -= nh; } else { n0 = nh; }
-                    }
-                    const int lo0 = blk * K;
-                    const int hi0 = std::min(lo0 + K, score ? d.kept : n0) - 1;
-                    const int tix = (int)(pl.top_tables.size() / kTopTableInts);
-                    pl.top_tables.resize(pl.top_tables.size() + kTopTableInts, 0);
-                    if (lo0 <= hi0)
-                        top_intervals(st0, n0, lo0, hi0, L,
-                                      pl.top_tables.data() + (size_t)tix * kTopTableInts);
-                    sv[j + 1].push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, tix});
-                }
+                for (int i = 0; i < cnt; ++i)  // pad: the item's record (built on the device)
+                    sv[j + 1].push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, pl.ntop++});
                 pl.stage_count[(size_t)t * kMaxStages + j + 1] = cnt;
                 pl.ffa_bytes += 4.0 * d.m * d.p + (score ? out_row_bytes * d.kept : 4.0 * d.m * d.p);
             }
@@ -421,8 +406,6 @@ ffa_status build_plan(Plan& pl) {
     o = align_up(o + pl.trs.size() * sizeof(TransformDesc), 256);
     pl.o_items = o;
     o = align_up(o + pl.items.size() * sizeof(WorkItem), 256);
-    pl.o_toptab = o;
-    o = align_up(o + pl.top_tables.size() * sizeof(int), 256);
     pl.o_dsblk = o;
     o = align_up(o + pl.ds_blocks.size() * sizeof(int2), 256);
     pl.o_stcnt = o;
@@ -451,6 +434,8 @@ ffa_status build_plan(Plan& pl) {
     pl.o_counters = w;  // queue counter, then per transform and stage completions
     pl.counter_bytes = (1 + pl.trs.size() * kMaxStages) * sizeof(int);
     w = align_up(w + pl.counter_bytes, 256);
+    pl.o_recs = w;  // top-pass item records
+    w = align_up(w + (size_t)pl.ntop * kTopRecInts * sizeof(int), 256);
     pl.ws_bytes = w;
     // host-buffer variant: + input and outputs
     pl.o_hx = w;
@@ -478,7 +463,6 @@ ffa_status ensure_pinned(Plan& pl) {
     std::memcpy(h + pl.o_oct, pl.oct.data(), pl.oct.size() * sizeof(OctaveDesc));
     std::memcpy(h + pl.o_trs, pl.trs.data(), pl.trs.size() * sizeof(TransformDesc));
     std::memcpy(h + pl.o_items, pl.items.data(), pl.items.size() * sizeof(WorkItem));
-    std::memcpy(h + pl.o_toptab, pl.top_tables.data(), pl.top_tables.size() * sizeof(int));
     std::memcpy(h + pl.o_dsblk, pl.ds_blocks.data(), pl.ds_blocks.size() * sizeof(int2));
     std::memcpy(h + pl.o_stcnt, pl.stage_count.data(), pl.stage_count.size() * sizeof(int));
     std::memcpy(h + pl.o_segs, pl.segs.data(), pl.segs.size() * sizeof(PrefixSeg));
@@ -703,13 +687,16 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     tp.foldbins = d_foldbins;
     tp.snr = d_snr;
     tp.status = status;
-    tp.tables = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_toptab);
+    int* recs = reinterpret_cast<int*>(ws + pl.o_recs);
+    tp.recs = recs;
+    tp.items = d_items;
     pp.items = d_items;
     pp.nitems = pl.nitems;
     pp.queue = counters;
     pp.done = counters + 1;
     pp.stage_count = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt);
     pp.smem_floats = pl.smem_floats;
+    FFA_CUDA(launch_top_prep(tp, pl.nitems, pl.ntop, recs, st), "top_prep launch");
     {
         LaunchScope ls(kFfaPersistent, pl.ffa_bytes, st);
         FFA_CUDA(launch_persistent(pp, (pl.smem_floats + 4) * 4, st), "ffa_persistent launch");

@@ -66,19 +66,27 @@ __host__ __device__ inline Split merge_split(int n, int s) {
 }
 
 // Interval table of a top-pass work item, heap order (node e at level l is 2^l - 1 + j,
-// children 2e + 1 and 2e + 2): per node {absolute start row, rows, lo, hi}, where rows
-// lo..hi of the node are the ones the item needs.  Node 0 is the output block.
-constexpr int kTopTableInts = 64;
+// children 2e + 1 and 2e + 2): node e at t[8 e]: {absolute start row, rows, lo, hi},
+// where rows lo..hi of the node are the ones the item needs.  Node 0 is the output
+// block.
+//
+// The item's record (kTopRecInts ints, built on the device before the FFA launch)
+// is that table with the shared-memory layout added: t[8 e + 4] = float offset of the
+// node's row lo in shared memory; at kRecLvl the first row descriptor of each level
+// L-1 .. 0 and their end; at kRecBytes the bytes its bulk copies move.
+constexpr int kTopRecInts = 128;
+constexpr int kRecLvl = 120;
+constexpr int kRecBytes = 125;
 __host__ __device__ inline void top_intervals(int st0, int n0, int lo0, int hi0, int L, int* t) {
     t[0] = st0; t[1] = n0; t[2] = lo0; t[3] = hi0;
     for (int l = 0; l < L; ++l) {
         for (int j = 0; j < (1 << l); ++j) {
             const int e = (1 << l) - 1 + j;
-            const int st = t[4 * e], n = t[4 * e + 1], lo = t[4 * e + 2], hi = t[4 * e + 3];
+            const int st = t[8 * e], n = t[8 * e + 1], lo = t[8 * e + 2], hi = t[8 * e + 3];
             const int nh = n >> 1;
             const Split a = merge_split(n, lo), z = merge_split(n, hi);
-            int* h = t + 4 * (2 * e + 1);
-            int* q = t + 4 * (2 * e + 2);
+            int* h = t + 8 * (2 * e + 1);
+            int* q = t + 8 * (2 * e + 2);
             h[0] = st; h[1] = nh; h[2] = a.i; h[3] = z.i;
             q[0] = st + nh; q[1] = n - nh; q[2] = a.j; q[3] = z.j;
         }
@@ -220,6 +228,7 @@ enum KernelKind : int {
     kBoxcarSnr,
     kNormalise,
     kFfaPersistent,
+    kTopPrep,
     kNumKinds
 };
 
@@ -294,7 +303,7 @@ struct TopParams {
     int32_t* foldbins;
     float* snr;                     // null: the last pass stores the transform instead
     unsigned* status;
-    const int* tables;              // per-item interval tables (WorkItem::pad), or null
+    const int* recs;                // per-item records (WorkItem::pad), or null: built in the CTA
     int single_pass;                // pass and rows per block when items is null
     int single_rows;
 };
@@ -340,6 +349,7 @@ cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bo
                           cudaStream_t s);
 cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s);
 cudaError_t launch_persistent(const PersistentParams& P, int smem_bytes, cudaStream_t s);
+cudaError_t launch_top_prep(const TopParams& P, int nitems, int ntop, int* recs, cudaStream_t s);
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s);
 cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s);
 constexpr int kNormaliseBlocks = 1216;  // 8 CTAs per SM

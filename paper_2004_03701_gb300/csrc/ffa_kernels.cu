@@ -449,14 +449,14 @@ __device__ __forceinline__ double trial_period(double tau, int p, int m, int s) 
 //   sm[o + x] = sm[a + x] + sm[b + (x + k) mod p],   0 <= k < p.
 // Offsets are in floats from the shared-memory base; lanes take consecutive columns.
 __device__ __forceinline__ void merge_row(float* sm, int o, int a, int b, int k, int p, int lane) {
-    int y = lane + k;
-    if (y >= p) y -= p;
+    // columns x < p - k read T[x + k], the others T[x + k - p]: two plain strided loops
+    const int split = p - k;
+    const int bk = b + k;
+    int x = lane;
 #pragma unroll 4
-    for (int x = lane; x < p; x += 32) {
-        sm[o + x] = __fadd_rn(sm[a + x], sm[b + y]);
-        y += 32;
-        if (y >= p) y -= p;
-    }
+    for (; x < split; x += 32) sm[o + x] = __fadd_rn(sm[a + x], sm[bk + x]);
+#pragma unroll 4
+    for (; x < p; x += 32) sm[o + x] = __fadd_rn(sm[a + x], sm[bk - p + x]);
 }
 __device__ __forceinline__ void copy_row(float* sm, int o, int a, int p, int lane) {
 #pragma unroll 4
@@ -708,6 +708,74 @@ __global__ void __launch_bounds__(kBottomThreads, kBottomMinBlocks) ffa_bottom_k
 // per interval) and merged in shared memory.  The last pass of a periodogram scores
 // its rows with the boxcar filters instead of storing them.
 // ---------------------------------------------------------------------------------
+// Fills the record of top-pass item `item` (see kTopRecInts) in one thread.
+__device__ void top_record(const TopParams& P, const TransformDesc& tr, const WorkItem item,
+                           int* r) {
+    const int p = tr.p, m = tr.m;
+    const int npass = top_passes(tr.depth, tr.chunk);
+    const int pass = item.pass;
+    const int d_in = top_pass_in_depth(tr.depth, tr.chunk, pass);
+    const int d_out = top_pass_out_depth(tr.depth, tr.chunk, pass);
+    const int L = d_in - d_out;
+    const int K = item.rows;
+    const bool score = pass == npass - 1 && P.snr != nullptr;
+    const float* in = ((npass - pass) & 1 ? P.buf1 : P.buf0) + tr.scratch_off;
+    const TopLayout lay = top_layout(K, L, p, P.widths.wmax, score);
+    // target node (depth d_out) and its row block
+    const int nmax = (m + (1 << d_out) - 1) >> d_out;
+    const int nb = ((score ? tr.kept : nmax) + K - 1) / K;
+    const int node = item.idx / nb, blk = item.idx - node * nb;
+    int st0 = 0, n0 = m;
+    for (int b = d_out - 1; b >= 0; --b) {
+        const int nh = n0 >> 1;
+        if ((node >> b) & 1) { st0 += nh; n0 -= nh; } else { n0 = nh; }
+    }
+    const int lo0 = blk * K;
+    const int hi0 = min(lo0 + K, score ? tr.kept : n0) - 1;
+    r[0] = st0; r[1] = n0; r[2] = lo0; r[3] = hi0;
+    r[kRecBytes] = 0;
+    if (lo0 > hi0) return;  // block past the end of a smaller node: nothing to do
+    top_intervals(st0, n0, lo0, hi0, L, r);
+    // level L: each interval in a 16-byte-aligned region, data at +h so that the bulk
+    // copy of its aligned interior lands aligned
+    int acc = 0;
+    unsigned bytes = 0;
+    for (int j = 0; j < (1 << L); ++j) {
+        const int e = (1 << L) - 1 + j;
+        const float* g = in + (int64_t)(r[8 * e] + r[8 * e + 2]) * p;
+        const int total = (r[8 * e + 3] - r[8 * e + 2] + 1) * p;
+        const int h = (int)((reinterpret_cast<uintptr_t>(g) >> 2) & 3);
+        r[8 * e + 4] = lay.buf_a + acc + h;
+        acc += round4(h + total);
+        bytes += bulk_bytes(g, total);
+    }
+    // levels L-1 .. 0: compact, one row after another, alternating buffers
+    int nd = 0;
+    for (int l = L - 1; l >= 0; --l) {
+        const int base = (((L - l) & 1) == 0) ? lay.buf_a : lay.buf_b;
+        r[kRecLvl + L - 1 - l] = nd;
+        int rows = 0;
+        for (int j = 0; j < (1 << l); ++j) {
+            const int e = (1 << l) - 1 + j;
+            r[8 * e + 4] = base + rows * p;
+            rows += r[8 * e + 3] - r[8 * e + 2] + 1;
+        }
+        nd += rows;
+    }
+    r[kRecLvl + L] = nd;
+    r[kRecBytes] = (int)bytes;
+}
+
+// Records of all top-pass items of a queue, one thread each.
+constexpr int kPrepThreads = 64;  // small CTAs: the work is one latency-bound chain per item
+__global__ void __launch_bounds__(kPrepThreads) top_prep_kernel(TopParams P, int nitems, int* recs) {
+    const int q = blockIdx.x * kPrepThreads + threadIdx.x;
+    if (q >= nitems) return;
+    const WorkItem item = P.items[q];
+    if (item.pass < 0) return;
+    top_record(P, P.trs[item.tr], item, recs + (int64_t)item.pad * kTopRecInts);
+}
+
 __device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item, float* smem) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -727,85 +795,27 @@ __device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item
     float* out = ((npass - pass - 1) & 1 ? P.buf1 : P.buf0) + tr.scratch_off;
     const TopLayout lay = top_layout(K, L, p, P.widths.wmax, score);
 
-    // target node (depth d_out) and its row block
-    const int nmax = (m + (1 << d_out) - 1) >> d_out;
-    const int limit_rows = score ? tr.kept : nmax;
-    const int nb = (limit_rows + K - 1) / K;
-    const int node = item.idx / nb, blk = item.idx - node * nb;
-    int st0 = 0, n0 = m;
-    for (int b = d_out - 1; b >= 0; --b) {
-        const int nh = n0 >> 1;
-        if ((node >> b) & 1) { st0 += nh; n0 -= nh; } else { n0 = nh; }
-    }
-    const int lo0 = blk * K;
-    const int hi0 = min(lo0 + K, score ? tr.kept : n0) - 1;
-    if (lo0 > hi0) return;  // uniform: block past the end of a smaller node
-
-    // ---- interval table, heap order: node e at level l is e = 2^l - 1 + j.
-    //      per node: [0] abs start row, [1] size, [2] lo, [3] hi, [4] smem offset of row lo
-    //      Intervals come precomputed with the plan (or are built here for a single
-    //      transform); warp 0 lays them out in shared memory with prefix sums.
+    // ---- the item's record: intervals, shared-memory layout, descriptor counts
     int* tab = reinterpret_cast<int*>(smem + lay.table);
-    int* lvl_desc = tab + 120;  // first descriptor of each level, levels L-1..0, + end
-    const int nnodes = (2 << L) - 1;
-    if (P.tables) {
-        const int* src = P.tables + (int64_t)item.pad * kTopTableInts;
-        if (tid < 4 * nnodes) tab[8 * (tid >> 2) + (tid & 3)] = src[tid];
+    const int* lvl_desc = tab + kRecLvl;  // first descriptor of each level, levels L-1..0, + end
+    if (P.recs) {
+        const int* src = P.recs + (int64_t)item.pad * kTopRecInts;
+        if (tid < kTopRecInts) tab[tid] = src[tid];
     } else if (tid == 0) {
-        int t4[4 * 15];
-        top_intervals(st0, n0, lo0, hi0, L, t4);
-        for (int e = 0; e < nnodes; ++e)
-            for (int c = 0; c < 4; ++c) tab[8 * e + c] = t4[4 * e + c];
+        top_record(P, tr, item, tab);
     }
+    if (tid == 0) mbar_init(bar, 1);
     __syncthreads();
-    if (warp == 0) {
-        // level L: each interval in a 16-byte-aligned region, data at +h so that the bulk
-        // copy of its aligned interior lands aligned
-        {
-            const int j = lane, e = (1 << L) - 1 + j;
-            int h = 0, region = 0;
-            if (j < (1 << L)) {
-                const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
-                h = (int)((reinterpret_cast<uintptr_t>(g) >> 2) & 3);
-                region = round4(h + (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p);
-            }
-            int inc = region;
-            for (int o = 1; o < 8; o <<= 1) {
-                const int u = __shfl_up_sync(kFull, inc, o);
-                if (lane >= o) inc += u;
-            }
-            if (j < (1 << L)) tab[8 * e + 4] = lay.buf_a + inc - region + h;
-        }
-        // levels L-1 .. 0: compact, one row after another
-        int nd = 0;
-        for (int l = L - 1; l >= 0; --l) {
-            const int base = (((L - l) & 1) == 0) ? lay.buf_a : lay.buf_b;
-            const int j = lane, e = (1 << l) - 1 + j;
-            const int rows = j < (1 << l) ? tab[8 * e + 3] - tab[8 * e + 2] + 1 : 0;
-            int inc = rows;
-            for (int o = 1; o < 4; o <<= 1) {
-                const int u = __shfl_up_sync(kFull, inc, o);
-                if (lane >= o) inc += u;
-            }
-            if (j < (1 << l)) tab[8 * e + 4] = base + (inc - rows) * p;
-            if (lane == 0) lvl_desc[L - 1 - l] = nd;
-            nd += __shfl_sync(kFull, inc, (1 << l) - 1);
-        }
-        if (lane == 0) {
-            lvl_desc[L] = nd;
-            mbar_init(bar, 1);
-        }
+    const int st0 = tab[0], lo0 = tab[2], hi0 = tab[3];
+    if (lo0 > hi0) {  // uniform: block past the end of a smaller node
+        if (tid == 0) mbar_inval(bar);
+        return;
     }
-    __syncthreads();
 
     // ---- gather the needed rows of the depth-d_in transforms: one bulk copy per interval,
-    //      all counted by a single arrival on the barrier
-    unsigned bytes = 0;
-    for (int j = 0; j < (1 << L); ++j) {
-        const int e = (1 << L) - 1 + j;
-        const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
-        bytes += bulk_bytes(g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p);
-    }
+    //      all counted by a single arrival on the barrier; the unaligned ends of all
+    //      intervals by plain loads, one element per thread
+    const unsigned bytes = (unsigned)tab[kRecBytes];
     if (tid == 0 && bytes) {
         mbar_expect_tx(bar, bytes);
         for (int j = 0; j < (1 << L); ++j) {
@@ -814,11 +824,16 @@ __device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item
             issue_rows_copy(smem, tab[8 * e + 4], g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p, bar);
         }
     }
-    for (int j = 0; j < (1 << L); ++j) {
-        const int e = (1 << L) - 1 + j;
+    for (int u = tid; u < (8 << L); u += kTopThreads) {
+        const int e = (1 << L) - 1 + (u >> 3), c = u & 7;
         const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
-        load_row_ends(smem, tab[8 * e + 4], g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p, tid,
-                      kTopThreads);
+        const int total = (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p;
+        const int lead = bulk_lead(g);
+        const int tail0 = lead + (int)(bulk_bytes(g, total) / 4);
+        if (c < lead + (total - tail0)) {  // at most 3 + 3 ends per interval
+            const int q = c < lead ? c : tail0 + (c - lead);
+            smem[tab[8 * e + 4] + q] = g[q];
+        }
     }
     // ---- row descriptors {out, head row, tail row, shift} for levels L-1 .. 0, made
     //      while the bulk copies are in flight
@@ -919,9 +934,14 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
     extern __shared__ __align__(16) float smem[];
     int* slot = reinterpret_cast<int*>(smem + P.smem_floats);  // queue broadcast
     const int tid = threadIdx.x;
+    // Thread 0 claims the next item while the current one runs, so the atomic's latency
+    // is hidden.  The claimed item is always listed after the running one, so the
+    // smallest unfinished item is always running and every wait still ends.
+    int next = 0;
+    if (tid == 0) next = atomicAdd(P.queue, 1);
     for (;;) {
         if (tid == 0) {
-            int q = atomicAdd(P.queue, 1);
+            int q = next;
             if (*reinterpret_cast<volatile unsigned*>(P.bottom.status) & kDevTimeout) q = P.nitems;
             slot[0] = q;
         }
@@ -929,6 +949,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
         const int q = slot[0];
         __syncthreads();
         if (q >= P.nitems) break;
+        if (tid == 0) next = atomicAdd(P.queue, 1);
         const WorkItem item = P.items[q];
         const int stage = item.pass < 0 ? 0 : item.pass + 1;
         if (stage > 0) {
@@ -1137,6 +1158,14 @@ cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s) {
         LaunchScope ls(kNormalise, (4.0 + out_bytes) * P.n, s);
         normalise_write_kernel<<<P.nblocks, 256, 0, s>>>(P);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_top_prep(const TopParams& P, int nitems, int ntop, int* recs, cudaStream_t s) {
+    if (nitems <= 0 || ntop <= 0) return cudaSuccess;
+    LaunchScope ls(kTopPrep, 16.0 * nitems + 4.0 * kTopRecInts * ntop, s);
+    top_prep_kernel<<<(unsigned)((nitems + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
+        P, nitems, recs);
     return cudaGetLastError();
 }
 
