@@ -452,12 +452,23 @@ def run_ffa(a):
     bytes_per_launch = kq["alg_bytes"] / kq["launches"]
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / avg_s / 1e9
+    traffic = recorded_traffic(top, job.config()["workload"])
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(top, job.config()["workload"]),
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "alg_bytes_per_launch": bytes_per_launch,
+                "alg_bytes_def": "B_ref FFA+S/N term: sum over transforms of 4 m p + 4 n_w kept",
                 "peak_source": peak_kind,
+                "dram_frac": (traffic / avg_s / 1e9 / peak) if traffic else None,
                 "share_of_step": kq["ms"] / tot_ms if tot_ms else None,
                 "launches_per_step": kq["launches"] / a.steps}
+    if job.batch is None and top == "ffa_persistent":
+        # whole-step effective fraction: B_ref = sum_k (read the raw series + write
+        # octave k) + the FFA + S/N term, over the device time of one step
+        i = s.info
+        es = job.x.element_size()
+        b_ref = i.noctaves * es * job.n + 4.0 * i.downsampled_samples + bytes_per_launch
+        roofline["step_b_ref_bytes"] = b_ref
+        roofline["step_b_ref_frac"] = b_ref / (t_step * 1e-3) / 1e9 / peak
 
     # ---- end to end from pinned host buffers (copies inside the timed region)
     e2e = None

@@ -133,7 +133,7 @@ struct Plan {
     int bottom_nmax = 0, bottom_elems = 0;
     int smem_floats = 0;
     int nitems = 0;
-    double ffa_bytes = 0;
+    double ffa_bytes = 0;  // algorithmic bytes of the FFA + S/N: per transform 4 m p + 4 nw kept
     size_t o_counters = 0, counter_bytes = 0;
     int64_t ntrials = 0, ds_total = 0, ds_floats = 0, scratch_floats = 0, folded = 0;
     int max_rows = 0, max_p = 0;
@@ -304,7 +304,6 @@ ffa_status build_plan(Plan& pl) {
     pl.ntrials = trial;
     const int wmax = pl.W.wmax;
     const int nw = pl.W.nw;
-    const double out_row_bytes = 4.0 * nw + 12.0;
 
     // ---- persistent work queue.  Whole-tree transforms (scored inside one CTA) come
     //      first; the others are cut into batches of consecutive transforms, and the
@@ -320,7 +319,7 @@ ffa_status build_plan(Plan& pl) {
         pl.bottom0_nmax = std::max(pl.bottom0_nmax, d.m);
         pl.bottom0_elems = std::max(pl.bottom0_elems, d.m * d.p);
         p0 = std::max(p0, d.p);
-        pl.ffa_bytes += 4.0 * d.m * d.p + out_row_bytes * d.kept;
+        pl.ffa_bytes += 4.0 * d.m * d.p + 4.0 * nw * d.kept;
     }
     if (pl.bottom0_nmax) {
         const int per_warp = snr_warp_floats(p0, wmax);
@@ -363,7 +362,7 @@ ffa_status build_plan(Plan& pl) {
             const int rows = (d.m + (1 << d.depth) - 1) >> d.depth;
             pl.bottom_nmax = std::max(pl.bottom_nmax, rows);
             pl.bottom_elems = std::max(pl.bottom_elems, rows * d.p);
-            pl.ffa_bytes += 8.0 * d.m * d.p;
+            pl.ffa_bytes += 4.0 * d.m * d.p + 4.0 * nw * d.kept;
             const int np = top_passes(d.depth, d.chunk);
             if (np + 1 > kMaxStages) return fail(FFA_ERR_UNSUPPORTED, "tree too deep");
             for (int j = 0; j < np; ++j) {
@@ -381,7 +380,6 @@ ffa_status build_plan(Plan& pl) {
                 for (int i = 0; i < cnt; ++i)  // pad: the item's record (built on the device)
                     sv[j + 1].push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, pl.ntop++});
                 pl.stage_count[(size_t)t * kMaxStages + j + 1] = cnt;
-                pl.ffa_bytes += 4.0 * d.m * d.p + (score ? out_row_bytes * d.kept : 4.0 * d.m * d.p);
             }
         }
         max_stage = std::max(max_stage, (int)sv.size());

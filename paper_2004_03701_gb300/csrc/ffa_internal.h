@@ -140,15 +140,28 @@ struct TopLayout {
     int desc_cap;
     int buf_a;      // levels L, L-2, ...   (level L with per-interval alignment slack)
     int buf_b;      // levels L-1, L-3, ...
-    int sbuf;       // per-warp prefix-sum rows of the boxcar S/N
+    int sbuf;       // per-warp prefix-sum rows of the boxcar S/N (scoring passes)
     int sbuf_warp;  // floats per warp
     int total;      // floats
 };
 __host__ __device__ inline int round4(int v) { return (v + 3) & ~3; }
 
-// Prefix-sum row of the boxcar S/N of a p-bin profile: S[0 .. 32 ceil(p/32) + wmax].
+// Shared memory of the boxcar S/N.  Profiles of p <= kSnrHalfMaxP bins are scored two
+// per warp, one per half-warp: lane h of a half owns the Q = snr_q(p) consecutive
+// phases Q h .. Q h + Q - 1 (Q odd and 16 Q >= p, so that the 16 lanes' rows of reads
+// fall in 16 different banks), and the half's prefix-sum row holds 16 Q + wmax floats.
+// The second half's row starts snr_half_stride floats after the first: 16 more than a
+// multiple of 32, so that the two halves never share a bank either.  Longer profiles
+// are scored one per warp, with a row of p + wmax + 1 floats.
+constexpr int kSnrMaxQ = 35;
+constexpr int kSnrHalfMaxP = 16 * kSnrMaxQ;  // 560 bins
+__host__ __device__ inline int snr_q(int p) { return ((p + 15) / 16) | 1; }
+__host__ __device__ inline int snr_half_stride(int p, int wmax) {
+    const int need = 16 * snr_q(p) + wmax;
+    return need + (((16 - need) % 32) + 32) % 32;
+}
 __host__ __device__ inline int snr_warp_floats(int p, int wmax) {
-    return round4(((p + 31) & ~31) + wmax + 1);
+    return p <= kSnrHalfMaxP ? 2 * snr_half_stride(p, wmax) : round4(p + wmax + 1);
 }
 
 // Shared-memory layout (in floats) of a sub-tree CTA: barrier, two row-descriptor
@@ -187,13 +200,26 @@ __host__ __device__ inline TopLayout top_layout(int K, int L, int p, int wmax, b
         if (((L - l) & 1) == 0) cap_a = cap_a > sz ? cap_a : sz;
         else cap_b = cap_b > sz ? cap_b : sz;
     }
+    t.sbuf_warp = snr ? snr_warp_floats(p, wmax) : 0;
+    const int s_need = (kTopThreads / 32) * t.sbuf_warp;
+    // half-warp scoring reads level 0 straight from level 1 (level 0 is never stored):
+    // its buffer, whose earlier contents are consumed by then, holds the S rows
+    const bool fused = snr && p <= kSnrHalfMaxP;
+    const bool zero_in_a = (L & 1) == 0;
+    if (fused) {
+        if (zero_in_a) cap_a = cap_a > s_need ? cap_a : s_need;
+        else cap_b = cap_b > s_need ? cap_b : s_need;
+    }
     t.buf_a = off;
     off += round4(cap_a);
     t.buf_b = off;
     off += round4(cap_b);
-    t.sbuf = off;
-    t.sbuf_warp = snr ? snr_warp_floats(p, wmax) : 0;
-    off += (kTopThreads / 32) * t.sbuf_warp;
+    if (fused) {
+        t.sbuf = zero_in_a ? t.buf_a : t.buf_b;
+    } else {
+        t.sbuf = off;
+        off += s_need;
+    }
     t.total = off;
     return t;
 }

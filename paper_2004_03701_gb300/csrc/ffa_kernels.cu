@@ -270,89 +270,121 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 }
 
 // ---------------------------------------------------------------------------------
-// Boxcar S/N of one profile by one warp (Sec. 5.4): S = exclusive prefix sum of the
-// profile over two concatenated repeats, then for each width w the largest
-// C_k = S[k + w] - S[k] over phases k, scaled by 1 / (stdnoise sqrt(w)).
-//
-// Register form (p <= 32 * 17): lane holds v[t] = F[lane + 32 t].  The prefix sums are
-// a warp scan per slot with a running carry; S lives in shared memory (the wmax
-// entries past p are S[p] + S[j]); lanes keep S[k] for their own phases in registers
-// (+inf for k >= p, so that padding phases never win) and read S[k + w] once per width.
 // ---------------------------------------------------------------------------------
-constexpr int kSnrMaxSlots = 17;
-
-template <int T>
-__device__ __forceinline__ void snr_from_regs(const float (&v)[T], int p, float* S,
-                                              const Widths& W, float inv_std, float* out,
-                                              int lane) {
-    float carry = 0.f;
+// Boxcar S/N (Sec. 5.4).  For a profile F of p bins, S is the exclusive prefix sum of F
+// over two concatenated repeats; for each width w the score is the largest
+// C_k = S[k + w] - S[k] over phases k, times inv_std / sqrt(w).
+//
+// Half-warp form (p <= kSnrHalfMaxP): a warp scores two profiles, one per half.  Lane h
+// of a half owns the Q consecutive phases Q h .. Q h + Q - 1: it forms their F (a merge
+// F = A[x] + B[(x + k) mod p] of two shared-memory rows, or a stored row A), sums them
+// in registers, and after a 16-lane scan of the lane totals holds S[k] of its phases in
+// registers (+inf past p, so that those phases never win) and writes them to the
+// half's row in shared memory; the row is extended by the second repeat, and each
+// width reads S[k + w] once per phase.  A 16-lane transposed butterfly reduces 16
+// widths at a time with 15 shuffles.  `write` false: the half only takes part in the
+// shuffles (an odd row count) and stores nothing.
+// ---------------------------------------------------------------------------------
+template <int Q>
+__device__ __forceinline__ void snr_half(const float* A, const float* B, int k, int p, float* S,
+                                         const Widths& W, float inv_std, float* out, bool write,
+                                         int h) {
+    const int x0 = Q * h;
+    float sk[Q];
+    float run = 0.f;
+    if (B) {
+        int y = (x0 + k) % p;
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-        float inc = v[t];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float u = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o) inc += u;
+        for (int i = 0; i < Q; ++i) {
+            sk[i] = run;
+            if (x0 + i < p) run = __fadd_rn(run, __fadd_rn(A[x0 + i], B[y]));
+            y = y + 1 == p ? 0 : y + 1;
         }
-        const int x = lane + 32 * t;
-        if (x < p) S[x + 1] = carry + inc;
-        carry += __shfl_sync(kFull, inc, 31);
-    }
-    if (lane == 0) S[0] = 0.f;
-    __syncwarp();
-    const float total = S[p];
-    const int jmax = 32 * T - 1 + W.wmax - p;  // S is read up to index 32 T - 1 + wmax
-    for (int j = lane + 1; j <= jmax; j += 32)
-        S[p + j] = j <= p ? total + S[j] : 0.f;  // second repeat; finite padding beyond
-    __syncwarp();
-    float sk[T];
+    } else {
 #pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int x = lane + 32 * t;
-        sk[t] = x < p ? S[x] : INFINITY;
+        for (int i = 0; i < Q; ++i) {
+            sk[i] = run;
+            if (x0 + i < p) run = __fadd_rn(run, A[x0 + i]);
+        }
     }
-    // 16 widths at a time: per-lane maxima, then one transposed butterfly reduction
-    // (16 shuffles for 16 widths); afterwards lane pair (2v, 2v+1) holds width v.
+    float inc = run;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const float u = __shfl_up_sync(kFull, inc, o, 16);
+        if (h >= o) inc = __fadd_rn(inc, u);
+    }
+    float ex = __shfl_up_sync(kFull, inc, 1, 16);
+    if (h == 0) ex = 0.f;
+    const float total = __shfl_sync(kFull, inc, 15, 16);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (x0 + i < p) {
+            sk[i] = __fadd_rn(ex, sk[i]);
+            S[x0 + i] = sk[i];
+        } else {
+            sk[i] = INFINITY;
+        }
+    }
+    __syncwarp();
+    for (int j = h; j < W.wmax; j += 16) S[p + j] = __fadd_rn(total, S[j]);  // second repeat
+    __syncwarp();
     for (int w0 = 0; w0 < W.nw; w0 += 16) {
         float b[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            b[i] = -INFINITY;
-            if (w0 + i < W.nw) {
-                const float* Sw = S + W.w[w0 + i] + lane;
+        for (int iw = 0; iw < 16; ++iw) {
+            b[iw] = -INFINITY;
+            if (w0 + iw < W.nw) {
+                const float* Sw = S + x0 + W.w[w0 + iw];
 #pragma unroll
-                for (int t = 0; t < T; ++t) b[i] = fmaxf(b[i], Sw[32 * t] - sk[t]);
+                for (int i = 0; i < Q; ++i) b[iw] = fmaxf(b[iw], __fsub_rn(Sw[i], sk[i]));
             }
         }
-        const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+        const bool h8 = h & 8, h4 = h & 4, h2 = h & 2, h1 = h & 1;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float keep = h16 ? b[i + 8] : b[i], send = h16 ? b[i] : b[i + 8];
-            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 16));
+            const float keep = h8 ? b[i + 8] : b[i], send = h8 ? b[i] : b[i + 8];
+            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 8, 16));
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const float keep = h8 ? b[i + 4] : b[i], send = h8 ? b[i] : b[i + 4];
-            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 8));
+            const float keep = h4 ? b[i + 4] : b[i], send = h4 ? b[i] : b[i + 4];
+            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 4, 16));
         }
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
-            const float keep = h4 ? b[i + 2] : b[i], send = h4 ? b[i] : b[i + 2];
-            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 4));
+            const float keep = h2 ? b[i + 2] : b[i], send = h2 ? b[i] : b[i + 2];
+            b[i] = fmaxf(keep, __shfl_xor_sync(kFull, send, 2, 16));
         }
         {
-            const float keep = h2 ? b[1] : b[0], send = h2 ? b[0] : b[1];
-            b[0] = fmaxf(keep, __shfl_xor_sync(kFull, send, 2));
+            const float keep = h1 ? b[1] : b[0], send = h1 ? b[0] : b[1];
+            b[0] = fmaxf(keep, __shfl_xor_sync(kFull, send, 1, 16));
         }
-        b[0] = fmaxf(b[0], __shfl_xor_sync(kFull, b[0], 1));
-        const int v = (h16 ? 8 : 0) + (h8 ? 4 : 0) + (h4 ? 2 : 0) + (h2 ? 1 : 0);
-        if ((lane & 1) == 0 && w0 + v < W.nw)
-            out[w0 + v] = b[0] * inv_std * W.inv_sqrt_w[w0 + v];
+        // lane h now holds width w0 + h
+        if (write && w0 + h < W.nw) out[w0 + h] = b[0] * inv_std * W.inv_sqrt_w[w0 + h];
     }
     __syncwarp();
 }
 
-// Profiles of more than 32 * kSnrMaxSlots bins: sequential per-lane chunks.
+#define FFA_SNR_Q(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) \
+    X(25) X(27) X(29) X(31) X(33) X(35)
+
+// Two profiles per warp (p <= kSnrHalfMaxP): this lane's half scores F = A + (B << k)
+// (B null: F = A) with its prefix-sum row in `S_warp` (snr_warp_floats of the warp).
+__device__ __forceinline__ void snr_pair(const float* A, const float* B, int k, int p,
+                                         float* S_warp, const Widths& W, float inv_std,
+                                         float* out, bool write, int lane) {
+    float* S = S_warp + (lane >> 4) * snr_half_stride(p, W.wmax);
+    const int h = lane & 15;
+    switch (snr_q(p)) {
+#define FFA_CASE(Q) case Q: snr_half<Q>(A, B, k, p, S, W, inv_std, out, write, h); return;
+        FFA_SNR_Q(FFA_CASE)
+#undef FFA_CASE
+        default: return;
+    }
+}
+
+// Boxcar S/N of one long profile (p > kSnrHalfMaxP) by one warp: sequential per-lane
+// chunks of the prefix sums, then strided phases per width.
 __device__ __noinline__ void snr_row_any(const float* prof, int p, float* S, const Widths& W,
                                          float inv_std, float* out, int lane) {
     const int L = p + W.wmax;
@@ -384,60 +416,6 @@ __device__ __noinline__ void snr_row_any(const float* prof, int p, float* S, con
         if (lane == 0) out[iw] = best * inv_std * W.inv_sqrt_w[iw];
     }
     __syncwarp();
-}
-
-// Scores a stored row (shared or global memory).
-template <int T>
-__device__ __forceinline__ void snr_row_t(const float* prof, int p, float* S, const Widths& W,
-                                          float inv_std, float* out, int lane) {
-    float v[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int x = lane + 32 * t;
-        v[t] = x < p ? prof[x] : 0.f;
-    }
-    snr_from_regs<T>(v, p, S, W, inv_std, out, lane);
-}
-
-// Merges F_s = H + (T << k) straight into registers and scores it (row never stored).
-template <int T>
-__device__ __forceinline__ void snr_merge_t(const float* sm, int a, int b, int k, int p, float* S,
-                                            const Widths& W, float inv_std, float* out, int lane) {
-    float v[T];
-    int y = lane + k;
-    if (y >= p) y -= p;
-#pragma unroll
-    for (int t = 0; t < T; ++t) {
-        const int x = lane + 32 * t;
-        v[t] = x < p ? __fadd_rn(sm[a + x], sm[b + y]) : 0.f;
-        y += 32;
-        if (y >= p) y -= p;
-    }
-    snr_from_regs<T>(v, p, S, W, inv_std, out, lane);
-}
-
-#define FFA_SNR_SLOTS(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) \
-    X(13) X(14) X(15) X(16) X(17)
-
-__device__ __forceinline__ void snr_row(const float* prof, int p, float* S, const Widths& W,
-                                        float inv_std, float* out, int lane) {
-    switch ((p + 31) >> 5) {
-#define FFA_CASE(T) case T: snr_row_t<T>(prof, p, S, W, inv_std, out, lane); return;
-        FFA_SNR_SLOTS(FFA_CASE)
-#undef FFA_CASE
-        default: snr_row_any(prof, p, S, W, inv_std, out, lane); return;
-    }
-}
-
-// Returns false (nothing done) if p needs the generic path.
-__device__ __forceinline__ bool snr_merge(const float* sm, int a, int b, int k, int p, float* S,
-                                          const Widths& W, float inv_std, float* out, int lane) {
-    switch ((p + 31) >> 5) {
-#define FFA_CASE(T) case T: snr_merge_t<T>(sm, a, b, k, p, S, W, inv_std, out, lane); return true;
-        FFA_SNR_SLOTS(FFA_CASE)
-#undef FFA_CASE
-        default: return false;
-    }
 }
 
 __device__ __forceinline__ double trial_period(double tau, int p, int m, int s) {
@@ -680,9 +658,17 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     } else {
         // The sub-tree is the whole transform: score rows s < kept (Sec. 2.3).
         float* S = smem + out + warp * snr_warp_floats(p, P.widths.wmax);
-        for (int s = warp; warp < P.snr_warps && s < tr.kept; s += P.snr_warps) {
-            const int64_t t = tr.trial0 + s;
-            snr_row(smem + in + s * p, p, S, P.widths, tr.inv_std, P.snr + t * P.widths.nw, lane);
+        const int nw = P.widths.nw;
+        if (p <= kSnrHalfMaxP) {
+            for (int s0 = 2 * warp; warp < P.snr_warps && s0 < tr.kept; s0 += 2 * P.snr_warps) {
+                const int s = min(s0 + (lane >> 4), (int)tr.kept - 1);
+                snr_pair(smem + in + s * p, nullptr, 0, p, S, P.widths, tr.inv_std,
+                         P.snr + (tr.trial0 + s) * nw, s0 + (lane >> 4) < tr.kept, lane);
+            }
+        } else {
+            for (int s = warp; warp < P.snr_warps && s < tr.kept; s += P.snr_warps)
+                snr_row_any(smem + in + s * p, p, S, P.widths, tr.inv_std,
+                            P.snr + (tr.trial0 + s) * nw, lane);
         }
         for (int s = tid; s < tr.kept; s += kBottomThreads) {
             P.periods[tr.trial0 + s] = trial_period(tr.tau, p, tr.m, s);
@@ -868,8 +854,8 @@ __device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item
         return;
     }
 
-    // ---- merge levels L-1 .. 1, and level 0 unless it is scored straight from registers
-    const bool fused = score && ((p + 31) >> 5) <= kSnrMaxSlots;
+    // ---- merge levels L-1 .. 1, and level 0 unless it is scored straight from level 1
+    const bool fused = score && p <= kSnrHalfMaxP;
     for (int l = L - 1; l >= (fused ? 1 : 0); --l) {
         const int q1 = lvl_desc[L - l];
         for (int q = lvl_desc[L - 1 - l] + warp; q < q1; q += nwarps) {
@@ -884,17 +870,19 @@ __device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item
     const int rows0 = hi0 - lo0 + 1;
     if (score) {
         float* S = smem + lay.sbuf + warp * lay.sbuf_warp;
-        const int q0 = lvl_desc[L - 1];
-        for (int r = warp; r < rows0; r += nwarps) {
-            const int s = lo0 + r;
-            const int64_t t = tr.trial0 + s;
-            float* dst = P.snr + t * P.widths.nw;
-            if (fused) {
+        const int nw = P.widths.nw;
+        if (fused) {  // two rows per warp, the last merge level formed on the fly
+            const int q0 = lvl_desc[L - 1];
+            for (int r0 = 2 * warp; r0 < rows0; r0 += 2 * nwarps) {
+                const int r = min(r0 + (lane >> 4), rows0 - 1);
                 const int4 d = desc[q0 + r];
-                snr_merge(smem, d.y, d.z, d.w, p, S, P.widths, tr.inv_std, dst, lane);
-            } else {
-                snr_row(smem + o0 + r * p, p, S, P.widths, tr.inv_std, dst, lane);
+                snr_pair(smem + d.y, smem + d.z, d.w, p, S, P.widths, tr.inv_std,
+                         P.snr + (tr.trial0 + lo0 + r) * nw, r0 + (lane >> 4) < rows0, lane);
             }
+        } else {
+            for (int r = warp; r < rows0; r += nwarps)
+                snr_row_any(smem + o0 + r * p, p, S, P.widths, tr.inv_std,
+                            P.snr + (tr.trial0 + lo0 + r) * nw, lane);
         }
         for (int r = tid; r < rows0; r += kTopThreads) {
             P.periods[tr.trial0 + lo0 + r] = trial_period(tr.tau, p, m, lo0 + r);
@@ -982,14 +970,23 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
     }
 }
 
-// Standalone boxcar S/N of stored profiles: one warp per row.
+// Standalone boxcar S/N of stored profiles: two rows per warp (one per half-warp), or
+// one per warp for long profiles.
 __global__ void __launch_bounds__(256) boxcar_snr_kernel(SnrParams P) {
     extern __shared__ __align__(16) float smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* S = smem + warp * P.warp_floats;
-    const int64_t stride = (int64_t)gridDim.x * 8;
-    for (int64_t r = (int64_t)blockIdx.x * 8 + warp; r < P.rows; r += stride) {
-        snr_row(P.prof + r * P.cols, P.cols, S, P.widths, P.inv_std, P.snr + r * P.widths.nw, lane);
+    const int64_t nwarps = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + warp;
+    const int nw = P.widths.nw;
+    if (P.cols <= kSnrHalfMaxP) {
+        for (int64_t r0 = 2 * gw; r0 < P.rows; r0 += 2 * nwarps) {
+            const int64_t r = min(r0 + (lane >> 4), P.rows - 1);
+            snr_pair(P.prof + r * P.cols, nullptr, 0, P.cols, S, P.widths, P.inv_std,
+                     P.snr + r * nw, r0 + (lane >> 4) < P.rows, lane);
+        }
+    } else {
+        for (int64_t r = gw; r < P.rows; r += nwarps)
+            snr_row_any(P.prof + r * P.cols, P.cols, S, P.widths, P.inv_std, P.snr + r * nw, lane);
     }
 }
 
