@@ -164,12 +164,24 @@ __host__ __device__ inline int snr_warp_floats(int p, int wmax) {
     return p <= kSnrHalfMaxP ? 2 * snr_half_stride(p, wmax) : round4(p + wmax + 1);
 }
 
-// Shared-memory layout (in floats) of a sub-tree CTA: barrier, two row-descriptor
-// buffers of nmax int2 (merge level l uses one while level l+1's are computed into the
-// other), and two ping-pong row buffers of buf_floats.
+// Shared-memory layout (in floats) of a sub-tree CTA: barrier and two ints, the row
+// descriptors of every shared-memory merge level (nmax int2 per level, all made while
+// the rows are in flight), the register-stage node list (nmax ints), and two ping-pong
+// row buffers of buf_floats.
 constexpr int kBottomMaxRows = 1024;
+constexpr int kRegLevels = 4;  // merge levels done in registers: nodes of <= 16 rows
+__host__ __device__ inline int height_of(int n) {
+    int h = 0;
+    while ((1 << h) < n) ++h;
+    return h;
+}
+__host__ __device__ inline int bottom_smem_levels(int nmax) {
+    const int l = height_of(nmax) - kRegLevels;
+    return l > 0 ? l : 0;
+}
 struct BottomLayout {
     int desc;
+    int nodes;
     int buf_a;
     int buf_b;
     int buf_floats;
@@ -178,7 +190,8 @@ struct BottomLayout {
 __host__ __device__ inline BottomLayout bottom_layout(int nmax, int elems_max, int snr_need) {
     BottomLayout b;
     b.desc = 4;
-    b.buf_a = round4(b.desc + 4 * nmax);
+    b.nodes = b.desc + 2 * bottom_smem_levels(nmax) * nmax;
+    b.buf_a = round4(b.nodes + nmax);
     int need = elems_max + 4;
     if (snr_need > need) need = snr_need;
     b.buf_floats = round4(need);

@@ -555,7 +555,6 @@ __device__ __forceinline__ void reg_strip_any(float* sm, int in, int out, int st
     }
 }
 
-constexpr int kRegLevels = 4;          // levels done in registers: nodes of <= 16 rows
 
 template <bool kSnr>
 __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkItem item, float* smem) {
@@ -563,7 +562,7 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kBottomThreads / 32;
     const BottomLayout lay = bottom_layout(P.nmax, P.elems_max, P.snr_floats);
-    int2* desc = reinterpret_cast<int2*>(smem + lay.desc);  // 2 x nmax
+    int2* desc = reinterpret_cast<int2*>(smem + lay.desc);  // nmax per shared-memory level
 
     const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
     const int p = tr.p;
@@ -589,7 +588,7 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     load_row_ends(smem, a0, src, total, tid, kBottomThreads);
     const int H = tree_height(n);
     // nodes of the register stage: height <= kRegLevels, parent higher (one per start row)
-    int* rnodes = reinterpret_cast<int*>(desc + P.nmax);  // second descriptor buffer, for now
+    int* rnodes = reinterpret_cast<int*>(smem + lay.nodes);
     int& nreg = reinterpret_cast<int*>(smem)[2];           // header: barrier, then 2 ints
     int& regmax = reinterpret_cast<int*>(smem)[3];
     if (tid == 0) { nreg = 0; regmax = 1; }
@@ -606,8 +605,12 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
             atomicMax(&regmax, sz);
         }
     }
-    if (H > kRegLevels)
-        for (int r = tid; r < n; r += kBottomThreads) desc[r] = bottom_desc(n, kRegLevels + 1, r, p);
+    // row descriptors of every shared-memory level, made while the rows are in flight
+    const int nlev = H - kRegLevels;
+    for (int e = tid; e < nlev * n; e += kBottomThreads) {
+        const int l = e / n, r = e - l * n;
+        desc[l * P.nmax + r] = bottom_desc(n, kRegLevels + 1 + l, r, p);
+    }
     const bool landed = bytes == 0 || mbar_wait_bounded(bar, 0);
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
@@ -631,14 +634,9 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
         __syncthreads();
     }
 
-    // ---- merge levels kRegLevels+1 .. H in shared memory; level lev+1's descriptors
-    //      are made while level lev merges
+    // ---- merge levels kRegLevels+1 .. H in shared memory
     for (int lev = kRegLevels + 1; lev <= H; ++lev) {
-        const int2* dc = desc + ((lev - kRegLevels - 1) & 1) * P.nmax;
-        if (lev < H) {
-            int2* dn = desc + ((lev - kRegLevels) & 1) * P.nmax;
-            for (int r = tid; r < n; r += kBottomThreads) dn[r] = bottom_desc(n, lev + 1, r, p);
-        }
+        const int2* dc = desc + (lev - kRegLevels - 1) * P.nmax;
         for (int r = warp; r < n; r += nwarps) {
             const int2 d = dc[r];
             const int ha = d.x & 0xffff, tb = (d.x >> 16) & 0xffff;
