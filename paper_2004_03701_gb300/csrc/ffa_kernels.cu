@@ -426,19 +426,42 @@ __device__ __forceinline__ double trial_period(double tau, int p, int m, int s) 
 // One merge (Eq. ffa_merge_rule) of shared-memory rows by one warp:
 //   sm[o + x] = sm[a + x] + sm[b + (x + k) mod p],   0 <= k < p.
 // Offsets are in floats from the shared-memory base; lanes take consecutive columns.
+// A lane's columns are taken in groups of 4, all 8 loads of a group before its adds,
+// so that a warp keeps many shared-memory loads in flight.
 __device__ __forceinline__ void merge_row(float* sm, int o, int a, int b, int k, int p, int lane) {
-    // columns x < p - k read T[x + k], the others T[x + k - p]: two plain strided loops
-    const int split = p - k;
-    const int bk = b + k;
-    int x = lane;
-#pragma unroll 4
-    for (; x < split; x += 32) sm[o + x] = __fadd_rn(sm[a + x], sm[bk + x]);
-#pragma unroll 4
-    for (; x < p; x += 32) sm[o + x] = __fadd_rn(sm[a + x], sm[bk - p + x]);
+    const float* pa = sm + a + lane;
+    const float* pb = sm + b + k + lane;  // T[(x + k) mod p] = pb[32 t], or pb[32 t - p] once wrapped
+    float* po = sm + o + lane;
+    const int wrap = p - k - lane;        // column slot t has wrapped once 32 t >= wrap
+    const int nslot = (p - lane + 31) >> 5;
+    for (int t0 = 0; t0 < nslot; t0 += 4) {
+        float hv[4], tv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u;
+            if (t < nslot) {
+                hv[u] = pa[32 * t];
+                tv[u] = pb[32 * t - (32 * t >= wrap ? p : 0)];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (t0 + u < nslot) po[32 * (t0 + u)] = __fadd_rn(hv[u], tv[u]);
+    }
 }
 __device__ __forceinline__ void copy_row(float* sm, int o, int a, int p, int lane) {
-#pragma unroll 4
-    for (int x = lane; x < p; x += 32) sm[o + x] = sm[a + x];
+    const float* pa = sm + a + lane;
+    float* po = sm + o + lane;
+    const int nslot = (p - lane + 31) >> 5;
+    for (int t0 = 0; t0 < nslot; t0 += 4) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (t0 + u < nslot) v[u] = pa[32 * (t0 + u)];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (t0 + u < nslot) po[32 * (t0 + u)] = v[u];
+    }
 }
 
 // Rows [0, total) of `src` (global) into shared memory at sm + dst (a float offset whose
