@@ -42,6 +42,14 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
+_T0 = time.perf_counter()
+
+
+def _log(msg):
+    """Progress on stderr (stdout carries only the JSON line)."""
+    print("[bench %7.1f s] %s" % (time.perf_counter() - _T0, msg), file=sys.stderr, flush=True)
+
+
 METRIC = "time-series samples searched/s (FFA periodogram)"
 UNIT = "samples/s"
 
@@ -149,18 +157,25 @@ def dist_env():
 
 
 # ------------------------------------------------------------------------- CPU oracle
-def oracle_sample_time(w, stride, offset=0):
-    """Times the CPU oracle on a bounded sample of one series: all downsampling, plus
-    the FFA and S/N of every `stride`-th transform; extrapolates the FFA + S/N time by
-    the folded-sample ratio.  Returns (seconds per whole periodogram, description)."""
+def oracle_sample_time(w, stride, offset=0, full_ds=True):
+    """Times the CPU oracle on a bounded sample of one series and extrapolates to the
+    whole periodogram.  Downsampling: all octaves timed (full_ds), or one octave timed
+    and multiplied by the octave count (every octave reads the whole raw series, so
+    each costs the same).  FFA + S/N: every `stride`-th transform, extrapolated by the
+    folded-sample ratio.  Returns (seconds per whole periodogram, description)."""
     import oracle
     oracle.build()
     args = (w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax)
     pl = oracle.plan(w.n, *args)
+    no = max(pl.n_octaves, 1)
     t0 = time.perf_counter()
-    for f in pl.oct_factor:
-        oracle.downsample(w.x, float(f))
-    t_ds = time.perf_counter() - t0
+    if full_ds:
+        for f in pl.oct_factor:
+            oracle.downsample(w.x, float(f))
+    elif pl.n_octaves:
+        oracle.downsample(w.x, float(pl.oct_factor[offset % pl.n_octaves]))
+    t_ds_meas = time.perf_counter() - t0
+    t_oct = t_ds_meas / (no if full_ds else 1)
     sel = np.zeros(pl.n_transforms, bool)
     sel[offset % stride::stride] = True
     t0 = time.perf_counter()
@@ -169,20 +184,21 @@ def oracle_sample_time(w, stride, offset=0):
     folded = (pl.tr_m * pl.tr_p).astype(np.float64)
     ratio = folded.sum() / max(folded[sel].sum(), 1.0)
     # the selected run downsampled every octave it touched again; remove that once
-    touched = np.unique(pl.tr_octave[sel])
-    t_ds_sel = t_ds * len(touched) / max(pl.n_octaves, 1)
-    est = t_ds + max(t_sel - t_ds_sel, 0.0) * ratio
-    desc = ("oracle (1 thread, C, FP64): downsampling of all %d octaves timed in full, FFA + "
-            "direct boxcar S/N of every %d-th of %d transforms (%.1f%% of folded samples) "
-            "extrapolated by folded samples; %.1f s measured" %
-            (pl.n_octaves, stride, pl.n_transforms, 100.0 / ratio, t_ds + t_sel))
+    touched = len(np.unique(pl.tr_octave[sel]))
+    est = t_oct * pl.n_octaves + max(t_sel - t_oct * touched, 0.0) * ratio
+    desc = ("oracle (1 thread, C, FP64): downsampling %s, FFA + direct boxcar S/N of every "
+            "%d-th of %d transforms (%.1f%% of folded samples) extrapolated by folded "
+            "samples; %.1f s measured" %
+            ("of all %d octaves timed in full" % pl.n_octaves if full_ds else
+             "timed on 1 of %d octaves" % pl.n_octaves,
+             stride, pl.n_transforms, 100.0 / ratio, t_ds_meas + t_sel))
     return est, desc
 
 
-def oracle_rate(job, stride, offset=0):
+def oracle_rate(job, stride, offset=0, full_ds=True):
     """(samples/s, description) of the CPU oracle on a bounded sample of the job."""
     if job.batch is None:
-        est, desc = oracle_sample_time(job.single, stride, offset)
+        est, desc = oracle_sample_time(job.single, stride, offset, full_ds)
         return job.single.n / est, desc
     b = job.batch
     pick = sorted({0, len(b.series) // 2, len(b.series) - 1})
@@ -193,7 +209,7 @@ def oracle_rate(job, stride, offset=0):
         if job.store != "f32":
             x = job.dequantised(i)
         w = synth.Workload("s%d" % i, x, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax, b.widths)
-        est, desc = oracle_sample_time(w, stride, offset)
+        est, desc = oracle_sample_time(w, stride, offset, full_ds)
         tot_t += est
         tot_n += s.n
         descs.append("series %d (n=%d): %s" % (i, s.n, desc))
@@ -343,11 +359,17 @@ def run_reference(a):
     if rank != 0:
         return
     job = Job(a.workload, "f32")
-    stride = 64
+    # each step a rotating sample sized so that the whole run takes about 2-3 minutes:
+    # ~0.15 s per sampled transform of a 2^23-sample series on one core
+    import oracle
+    w0 = job.single if job.batch is None else job.batch.series[0]
+    ntr = oracle.plan(w0.n, w0.tsamp, w0.pmin, w0.pmax, w0.bmin, w0.bmax).n_transforms
+    per_step = max(1, int(150.0 / (a.steps + a.warmup) / 0.15))
+    stride = max(1, -(-ntr // per_step))
     rates = []
     desc = ""
     for i in range(a.warmup + a.steps):
-        r, desc = oracle_rate(job, stride, offset=i)
+        r, desc = oracle_rate(job, stride, offset=i, full_ds=False)
         if i >= a.warmup:
             rates.append(r)
     value = statistics.mean(rates)
@@ -358,7 +380,7 @@ def run_reference(a):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": desc.replace("every 64-th", "every 64-th (rotating)")},
+                         "sample": "per step, rotating: " + desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -382,8 +404,11 @@ def run_ffa(a):
     ffa.library()
 
     store = a.storage or ("i8" if a.workload == "batch_int8" else "f32")
+    _log("generating %s" % a.workload)
     job = Job(a.workload, store, rank, world)
+    _log("inputs to the device, plan")
     job.to_device(ffa, torch, dev, int(a.ws_budget_gb * (1 << 30)))
+    _log("planned")
     s = job.searcher
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -394,12 +419,14 @@ def run_ffa(a):
         torch.cuda.synchronize()
 
     job.capture()
+    _log("warm-up")
     for _ in range(max(3, a.warmup)):
         job.step()
     s.check()
     barrier()
 
     # ---- timed region (no profiling events): headline device time per step
+    _log("timed steps")
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ffa.launch_count()
@@ -432,6 +459,7 @@ def run_ffa(a):
     value = n_all / (t_step * 1e-3)
 
     # ---- same steps launched eagerly with per-kernel CUDA events on the stream
+    _log("per-kernel events pass")
     ffa.profile_reset()
     ffa.profile_enable(True)
     for _ in range(a.steps):
@@ -473,6 +501,7 @@ def run_ffa(a):
     # ---- end to end from pinned host buffers (copies inside the timed region)
     e2e = None
     if not a.no_e2e:
+        _log("end-to-end pass")
         e2e = run_e2e(job, a, torch, ffa, flush, barrier, world, dev, n_all)
 
     cpu = None
@@ -513,19 +542,52 @@ def run_e2e(job, a, torch, ffa, flush, barrier, world, dev, n_all):
             s.run_host(xs, ps, fs, ss)
         h2d = 4 * job.n
     else:
-        # stored input in pinned host memory -> device, search, results -> pinned host
-        xh = job.x.cpu().pin_memory()
-        per_h = torch.empty_like(s.periods, device="cpu").pin_memory()
-        fb_h = torch.empty_like(s.foldbins, device="cpu").pin_memory()
-        snr_h = torch.empty_like(s.snr, device="cpu").pin_memory()
+        # stored input in pinned host memory -> device, search, results -> host
+        xh = torch.empty(job.x.shape, dtype=job.x.dtype, pin_memory=True)
+        xh.copy_(job.x)
+        outs = (s.periods, s.foldbins, s.snr)
+        out_bytes = sum(t.numel() * t.element_size() for t in outs)
+        if out_bytes <= (8 << 30):
+            hosts = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs]
+
+            def read_back():
+                for h, t in zip(hosts, outs):
+                    h.copy_(t, non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+        else:
+            # tens of GB of S/N: pageable host arrays filled through two 512 MB pinned
+            # staging buffers (pinning the whole output would take longer than the search)
+            hosts = [torch.empty(t.shape, dtype=t.dtype) for t in outs]
+            stage = [torch.empty(512 << 20, dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+            evs = [torch.cuda.Event(), torch.cuda.Event()]
+
+            def read_back():
+                k = 0
+                pend = [None, None]
+                for h, t in zip(hosts, outs):
+                    src = t.reshape(-1).view(torch.uint8)
+                    dst = h.reshape(-1).view(torch.uint8)
+                    for o in range(0, src.numel(), 512 << 20):
+                        n = min(512 << 20, src.numel() - o)
+                        b = k % 2
+                        if pend[b] is not None:  # drain this buffer's previous chunk
+                            evs[b].synchronize()
+                            pd, po, pn = pend[b]
+                            pd[po:po + pn].copy_(stage[b][:pn])
+                        stage[b][:n].copy_(src[o:o + n], non_blocking=True)
+                        evs[b].record()
+                        pend[b] = (dst, o, n)
+                        k += 1
+                for b in range(2):
+                    if pend[b] is not None:
+                        evs[b].synchronize()
+                        pd, po, pn = pend[b]
+                        pd[po:po + pn].copy_(stage[b][:pn])
 
         def one():
             job.x.copy_(xh, non_blocking=True)
             job.step()
-            per_h.copy_(s.periods, non_blocking=True)
-            fb_h.copy_(s.foldbins, non_blocking=True)
-            snr_h.copy_(s.snr, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+            read_back()
         h2d = job.x.numel() * job.x.element_size()
     for _ in range(2):
         one()
