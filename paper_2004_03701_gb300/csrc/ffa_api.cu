@@ -495,8 +495,9 @@ ffa_status make_plan_series(const std::vector<SeriesSpec>& series, const int32_t
         pl->row_cap = cap;
         st = build_plan(*pl);
         if (st != kRetrySmaller) break;
-        // sub-trees of different widths share one launch: lower the row limit and replan
-        cap = std::min(cap, pl->row_cap) - 1;
+        // sub-trees of different widths share one launch: lower the row limit below the
+        // largest sub-tree of this plan and replan
+        cap = std::min(cap, std::max(pl->bottom_nmax, pl->bottom0_nmax)) - 1;
         if (cap < 2) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
     }
     if (st != FFA_OK) return st;
@@ -542,7 +543,7 @@ struct BatchChunk {
     int first, count;   // series [first, first + count)
     int64_t x_lo;       // input offset of the chunk (its series' offsets are relative)
     int64_t trial0;     // first trial of the chunk in the batch output
-    std::unique_ptr<Plan> plan;
+    std::shared_ptr<Plan> plan;  // chunks of the same shape share one plan
 };
 struct Batch {
     std::vector<BatchChunk> chunks;
@@ -576,14 +577,20 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
     auto B = std::make_unique<Batch>();
     // workspace of each series searched alone, the unit of the chunk budget
     std::vector<size_t> est(nseries);
+    std::map<SeriesSpec, size_t> alone;  // series of the same shape plan alike
     for (int i = 0; i < nseries; ++i) {
         SeriesSpec s = all[i];
         s.x_off = 0;
-        std::unique_ptr<Plan> p1;
-        ffa_status st = make_plan_series({s}, h_widths, nw, &p1);
-        if (st != FFA_OK) return st;
-        est[i] = p1->ws_bytes;
+        auto it = alone.find(s);
+        if (it == alone.end()) {
+            std::unique_ptr<Plan> p1;
+            ffa_status st = make_plan_series({s}, h_widths, nw, &p1);
+            if (st != FFA_OK) return st;
+            it = alone.emplace(s, p1->ws_bytes).first;
+        }
+        est[i] = it->second;
     }
+    std::map<std::vector<SeriesSpec>, std::shared_ptr<Plan>> shapes;
     int64_t trial = 0;
     for (int i = 0; i < nseries;) {
         int j = i;
@@ -594,8 +601,14 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
         for (const SeriesSpec& s : part) lo = std::min(lo, s.x_off);
         for (SeriesSpec& s : part) s.x_off -= lo;
         BatchChunk c{i, j - i, lo, trial, nullptr};
-        ffa_status st = make_plan_series(part, h_widths, nw, &c.plan);
-        if (st != FFA_OK) return st;
+        auto sh = shapes.find(part);
+        if (sh == shapes.end()) {
+            std::unique_ptr<Plan> pc;
+            ffa_status st = make_plan_series(part, h_widths, nw, &pc);
+            if (st != FFA_OK) return st;
+            sh = shapes.emplace(part, std::shared_ptr<Plan>(std::move(pc))).first;
+        }
+        c.plan = sh->second;
         for (int q = 0; q < j - i; ++q) B->trial0.push_back(trial + c.plan->series_trial0[q]);
         trial += c.plan->ntrials;
         B->ws_bytes = std::max(B->ws_bytes, c.plan->ws_bytes);
