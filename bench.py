@@ -179,7 +179,7 @@ def oracle_sample_time(w, stride, offset=0, full_ds=True):
     sel = np.zeros(pl.n_transforms, bool)
     sel[offset % stride::stride] = True
     t0 = time.perf_counter()
-    oracle.periodogram(w.x, *args, w.widths, select=sel)
+    ref = oracle.periodogram(w.x, *args, w.widths, select=sel)
     t_sel = time.perf_counter() - t0
     folded = (pl.tr_m * pl.tr_p).astype(np.float64)
     ratio = folded.sum() / max(folded[sel].sum(), 1.0)
@@ -192,29 +192,60 @@ def oracle_sample_time(w, stride, offset=0, full_ds=True):
             ("of all %d octaves timed in full" % pl.n_octaves if full_ds else
              "timed on 1 of %d octaves" % pl.n_octaves,
              stride, pl.n_transforms, 100.0 / ratio, t_ds_meas + t_sel))
-    return est, desc
+    rows = (np.concatenate([np.arange(pl.tr_first_trial[t], pl.tr_first_trial[t] + pl.tr_kept[t])
+                            for t in np.flatnonzero(sel)]) if sel.any() else np.zeros(0, np.int64))
+    return est, desc, (rows, ref)
 
 
 def oracle_rate(job, stride, offset=0, full_ds=True):
-    """(samples/s, description) of the CPU oracle on a bounded sample of the job."""
+    """(samples/s, description, checks) of the CPU oracle on a bounded sample of the job;
+    checks = [(series index or None, sampled trial rows, oracle periodogram of them)]."""
     if job.batch is None:
-        est, desc = oracle_sample_time(job.single, stride, offset, full_ds)
-        return job.single.n / est, desc
+        w = job.single
+        if job.store != "f32":
+            w = synth.Workload(w.name, job.dequantised(0), w.tsamp, w.pmin, w.pmax, w.bmin,
+                               w.bmax, w.widths)
+        est, desc, chk = oracle_sample_time(w, stride, offset, full_ds)
+        return job.single.n / est, desc, [(None,) + chk]
     b = job.batch
     pick = sorted({0, len(b.series) // 2, len(b.series) - 1})
-    tot_t, tot_n, descs = 0.0, 0, []
+    tot_t, tot_n, descs, checks = 0.0, 0, [], []
     for i in pick:
         s = b.series[i]
         x = b.series_x(i)
         if job.store != "f32":
             x = job.dequantised(i)
         w = synth.Workload("s%d" % i, x, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax, b.widths)
-        est, desc = oracle_sample_time(w, stride, offset, full_ds)
+        est, desc, chk = oracle_sample_time(w, stride, offset, full_ds)
         tot_t += est
         tot_n += s.n
         descs.append("series %d (n=%d): %s" % (i, s.n, desc))
+        checks.append((i,) + chk)
     return tot_n / tot_t, "%d of %d series of the batch, rate = their samples / their " \
-        "estimated time; " % (len(pick), len(b.series)) + " | ".join(descs)
+        "estimated time; " % (len(pick), len(b.series)) + " | ".join(descs), checks
+
+
+def accuracy(job, checks):
+    """Max S/N error of the device periodogram against the FP64 oracle on the sampled
+    trials (the oracle searched the same stored values), periods and fold bins
+    compared exactly, and whether the strongest sampled trial is the same."""
+    err, n, same_best, exact = 0.0, 0, True, True
+    for i, rows, ref in checks:
+        if len(rows) == 0:
+            continue
+        got = job.searcher.series_result(i) if i is not None else \
+            (job.searcher.periods, job.searcher.foldbins, job.searcher.snr)
+        per, fb, snr = (t.cpu().numpy() for t in got)
+        per, fb, snr = per[rows], fb[rows], snr[rows].astype(np.float64)
+        exact &= bool(np.array_equal(per, ref.periods) and np.array_equal(fb, ref.foldbins))
+        err = max(err, float(np.abs(snr - ref.snr).max()))
+        n += len(rows)
+        same_best &= bool(np.unravel_index(snr.argmax(), snr.shape) ==
+                          np.unravel_index(ref.snr.argmax(), ref.snr.shape))
+    return {"max_snr_error": err, "trials_compared": n, "periods_foldbins_identical": exact,
+            "top_candidate_identical": same_best,
+            "reference": "FP64 oracle on the values the GPU searched (dequantised for f16/i8 "
+                         "storage), on the cpu_baseline sample of trials"}
 
 
 # --------------------------------------------------------------------------- workloads
@@ -299,12 +330,11 @@ class Job:
         for i, (o, n) in enumerate(segs):
             out[o:o + n] = ffa.normalise(x32[o:o + n], dtype=out.dtype)[0]
         torch.cuda.synchronize()
-        if self.batch is not None:  # host copies of a few dequantised series for the oracle
-            host = out.cpu().numpy()
-            for i in sorted({0, len(segs) // 2, len(segs) - 1}):
-                o, n = segs[i]
-                v = host[o:o + n].astype(np.float32)
-                self._deq[i] = v / 16 if self.store == "i8" else v
+        host = out.cpu().numpy()  # host copies of the dequantised series the oracle checks
+        for i in sorted({0, len(segs) // 2, len(segs) - 1}):
+            o, n = segs[i]
+            v = host[o:o + n].astype(np.float32)
+            self._deq[i] = v / 16 if self.store == "i8" else v
         return out
 
     def capture(self):
@@ -369,7 +399,7 @@ def run_reference(a):
     rates = []
     desc = ""
     for i in range(a.warmup + a.steps):
-        r, desc = oracle_rate(job, stride, offset=i, full_ds=False)
+        r, desc, _ = oracle_rate(job, stride, offset=i, full_ds=False)
         if i >= a.warmup:
             rates.append(r)
     value = statistics.mean(rates)
@@ -504,10 +534,12 @@ def run_ffa(a):
         _log("end-to-end pass")
         e2e = run_e2e(job, a, torch, ffa, flush, barrier, world, dev, n_all)
 
-    cpu = None
+    cpu = acc = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        rate, desc = oracle_rate(job, a.cpu_sample_stride if job.batch is None else 32)
+        _log("CPU oracle sample")
+        rate, desc, checks = oracle_rate(job, a.cpu_sample_stride if job.batch is None else 32)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        acc = accuracy(job, checks)
 
     if rank == 0:
         cfg = job.config()
@@ -520,7 +552,8 @@ def run_ffa(a):
             "dtype": "f32" if store == "f32" else store + " storage, f32 sums",
             "data": "synthetic", "config": cfg, "roofline": roofline,
             "kernels_ms_per_step": {k: v["ms"] / a.steps for k, v in kern.items()},
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+            "e2e": e2e, "cpu_baseline": cpu, "accuracy": acc, "clocks": clk,
+            "gpu_launches": launches,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
