@@ -64,6 +64,8 @@ def parse():
                     default="survey")
     ap.add_argument("--storage", choices=["f32", "f16", "i8"], default=None,
                     help="input storage (default f32; i8 for batch_int8)")
+    ap.add_argument("--tune", action="store_true",
+                    help="time a small grid of tile shapes first and bench the fastest")
     ap.add_argument("--ws-budget-gb", type=float, default=48.0,
                     help="workspace budget of one launch chunk of a batch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -304,18 +306,37 @@ class Job:
         src = self.single.x if self.batch is None else self.batch.x
         self.x32 = torch.from_numpy(src).to(dev)
         self.x = self._store(self.x32)
+        self.ws_budget = ws_budget
+        self.tiles, self.tune_ms = None, None
+        self.widths = self.single.widths if self.batch is None else self.batch.widths
+        self.searcher = self._make(None)
+        self.graph = None
+
+    def _make(self, tiles):
+        ffa, dev = self.ffa, self.dev
         if self.batch is None:
             w = self.single
-            self.searcher = ffa.Searcher(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths,
-                                         device=dev)
-            self.widths = w.widths
-        else:
-            b = self.batch
-            ser = [ffa.Series(s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax)
-                   for s in b.series]
-            self.searcher = ffa.BatchSearcher(ser, b.widths, ws_budget=ws_budget, device=dev)
-            self.widths = b.widths
-        self.graph = None
+            return ffa.Searcher(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths,
+                                device=dev, tiles=tiles)
+        ser = [ffa.Series(s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax)
+               for s in self.batch.series]
+        return ffa.BatchSearcher(ser, self.batch.widths, ws_budget=self.ws_budget, device=dev,
+                                 tiles=tiles)
+
+    def tune(self, repeats=2):
+        """Picks the fastest tile shape of a small grid around the automatic one (every
+        shape gives the same periodogram) and rebuilds the searcher with it."""
+        ffa = self.ffa
+        w = self.single if self.batch is None else self.batch.series[0]
+        auto = ffa.periodogram_plan(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax,
+                                    self.widths).tiles
+        self.searcher = None
+        best, timings = ffa.tune(self._make, lambda s: s(self.x), ffa.tile_candidates(auto),
+                                 repeats)
+        self.tiles = best
+        self.tune_ms = [[t.subtree_rows, t.top_levels, t.top_rows, round(ms, 4)]
+                        for t, ms in timings]
+        self.searcher = self._make(best)
 
     def _store(self, x32):
         """Normalised storage of the input (Sec. 3.1): FP16 or int8 (q/16) by the
@@ -365,6 +386,16 @@ class Job:
         return self.searcher.info.ntrials
 
     def config(self):
+        c = self._config()
+        if self.tiles is not None:
+            t = self.tiles
+            c["tiles"] = {"subtree_rows": t.subtree_rows, "top_levels": t.top_levels,
+                          "top_rows": t.top_rows, "tuned_ms": self.tune_ms}
+        else:
+            c["tiles"] = "automatic (largest that fits shared memory)"
+        return c
+
+    def _config(self):
         if self.batch is None:
             w = self.single
             i = self.searcher.info
@@ -439,6 +470,9 @@ def run_ffa(a):
     _log("inputs to the device, plan")
     job.to_device(ffa, torch, dev, int(a.ws_budget_gb * (1 << 30)))
     _log("planned")
+    if a.tune:
+        _log("tuning tiles")
+        job.tune()
     s = job.searcher
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)

@@ -141,6 +141,22 @@ ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out
  *   (Sec. 2.3); P_s = tau_k p^2 / (p - s / (m - 1)).
  * Host only.  Widths: 1 <= w < bmin, strictly increasing, at most 64.
  * ---------------------------------------------------------------------------- */
+/* Tile shape of a plan: the work-item sizes of the persistent FFA launch.  Any field 0
+ * means "the largest that fits shared memory" (the default of every call without
+ * tiles).  Every tile shape gives the same results, bit for bit: the merges and the S/N
+ * of each row do not depend on how rows are grouped.  The Python binding's `tune`
+ * times a few shapes on the caller's data and keeps the fastest.
+ *   subtree_rows  rows of a shared-memory sub-tree item, 2..1024
+ *   top_levels    merge levels per gathered top pass, 1..3
+ *   top_rows      output rows per top-pass item, 1..128
+ * Out-of-range values give FFA_ERR_ARG.  No counterpart in the paper: its CPU code
+ * recurses depth first and has no tiles. */
+typedef struct ffa_tiles {
+    int32_t subtree_rows;
+    int32_t top_levels;
+    int32_t top_rows;
+} ffa_tiles;
+
 typedef struct ffa_plan_info {
     int64_t ntrials;                  /* rows of the periodogram                     */
     int32_t noctaves;                 /* pseudo-octaves                              */
@@ -151,11 +167,17 @@ typedef struct ffa_plan_info {
     int64_t folded_samples;           /* sum over transforms of m * p                */
     size_t workspace_bytes;           /* for ffa_periodogram                         */
     size_t host_workspace_bytes;      /* for ffa_periodogram_host (includes I/O)     */
+    ffa_tiles tiles;                  /* tiles in effect: largest sub-tree, levels per
+                                         top pass and rows per top item of the plan  */
 } ffa_plan_info;
 
 ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pmax,
                                 int32_t bmin, int32_t bmax, const int32_t* h_widths,
                                 int32_t nw, ffa_plan_info* out);
+/* Same with a tile shape (NULL = automatic). */
+ffa_status ffa_periodogram_plan_tiles(int64_t n, double tsamp, double pmin, double pmax,
+                                      int32_t bmin, int32_t bmax, const int32_t* h_widths,
+                                      int32_t nw, const ffa_tiles* tiles, ffa_plan_info* out);
 
 /* ------------------------------------------------------------------------------
  * FFA periodogram (paper Sec. 5.3, Fig. 4; Sec. 5.5 for the two-dimensional output).
@@ -177,6 +199,13 @@ ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double t
                            const int32_t* h_widths, int32_t nw, double* d_periods,
                            int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
                            void* d_ws, size_t ws_bytes, void* stream);
+/* Same with a tile shape (NULL = automatic); the workspace is the one that
+ * ffa_periodogram_plan_tiles reports for the same tiles. */
+ffa_status ffa_periodogram_tiles(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp,
+                                 double pmin, double pmax, int32_t bmin, int32_t bmax,
+                                 const int32_t* h_widths, int32_t nw, const ffa_tiles* tiles,
+                                 double* d_periods, int32_t* d_foldbins, float* d_snr,
+                                 int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Batched periodograms (many series, e.g. the dedispersed DM trials of an observation,
@@ -215,6 +244,17 @@ ffa_status ffa_periodogram_batch(const void* d_x, ffa_dtype dtype, const ffa_ser
                                  size_t ws_budget, double* d_periods, int32_t* d_foldbins,
                                  float* d_snr, int64_t ntrials_cap, void* d_ws, size_t ws_bytes,
                                  void* stream);
+/* Same two calls with a tile shape for every chunk (NULL = automatic). */
+ffa_status ffa_batch_plan_tiles(const ffa_series* h_series, int32_t nseries,
+                                const int32_t* h_widths, int32_t nw, size_t ws_budget,
+                                const ffa_tiles* tiles, int64_t* h_trial_offsets,
+                                ffa_batch_info* out);
+ffa_status ffa_periodogram_batch_tiles(const void* d_x, ffa_dtype dtype,
+                                       const ffa_series* h_series, int32_t nseries,
+                                       const int32_t* h_widths, int32_t nw, size_t ws_budget,
+                                       const ffa_tiles* tiles, double* d_periods,
+                                       int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
+                                       void* d_ws, size_t ws_bytes, void* stream);
 
 /* Plans (single-series and batch) are built on first use and cached by their parameters
  * for the life of the process: their page-locked tables are what the table copy of

@@ -27,6 +27,7 @@ __all__ = [
     "FFAError", "library", "build", "normalise", "downsample", "ffa_transform", "boxcar_snr",
     "PlanInfo", "periodogram_plan", "periodogram", "periodogram_host", "Searcher",
     "Series", "BatchInfo", "batch_plan", "BatchSearcher", "periodogram_batch", "shard_series",
+    "Tiles", "tile_candidates", "tune", "tune_periodogram",
     "check", "plan_cache_clear", "launch_count", "kernel_names", "profile_enable", "profile_reset",
     "profile_query",
 ]
@@ -45,12 +46,17 @@ class FFAError(RuntimeError):
         self.status = status
 
 
+class _Tiles(ctypes.Structure):
+    _fields_ = [("subtree_rows", ctypes.c_int32), ("top_levels", ctypes.c_int32),
+                ("top_rows", ctypes.c_int32)]
+
+
 class _PlanInfo(ctypes.Structure):
     _fields_ = [("ntrials", ctypes.c_int64), ("noctaves", ctypes.c_int32),
                 ("ntransforms", ctypes.c_int32), ("nwidths", ctypes.c_int32),
                 ("max_rows", ctypes.c_int32), ("downsampled_samples", ctypes.c_int64),
                 ("folded_samples", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
-                ("host_workspace_bytes", ctypes.c_size_t)]
+                ("host_workspace_bytes", ctypes.c_size_t), ("tiles", _Tiles)]
 
 
 class _Series(ctypes.Structure):
@@ -93,6 +99,13 @@ def library() -> ctypes.CDLL:
     L.ffa_boxcar_snr.argtypes = [vp, i32, i32, vp, i32, dbl, vp, vp]
     L.ffa_periodogram_plan.argtypes = [i64, dbl, dbl, dbl, i32, i32, vp, i32,
                                        ctypes.POINTER(_PlanInfo)]
+    L.ffa_periodogram_plan_tiles.argtypes = [i64, dbl, dbl, dbl, i32, i32, vp, i32, vp,
+                                             ctypes.POINTER(_PlanInfo)]
+    L.ffa_periodogram_tiles.argtypes = [vp, i32, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp,
+                                        vp, vp, i64, vp, sz, vp]
+    L.ffa_batch_plan_tiles.argtypes = [vp, i32, vp, i32, sz, vp, vp, ctypes.POINTER(_BatchInfo)]
+    L.ffa_periodogram_batch_tiles.argtypes = [vp, i32, vp, i32, vp, i32, sz, vp, vp, vp, vp,
+                                              i64, vp, sz, vp]
     L.ffa_periodogram.argtypes = [vp, i32, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
                                   i64, vp, sz, vp]
     L.ffa_periodogram_host.argtypes = [vp, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
@@ -114,7 +127,8 @@ def library() -> ctypes.CDLL:
               "ffa_transform", "ffa_boxcar_snr", "ffa_periodogram_plan", "ffa_periodogram",
               "ffa_periodogram_host", "ffa_check", "ffa_profile_enable", "ffa_profile_reset",
               "ffa_normalise_workspace", "ffa_normalise", "ffa_batch_plan",
-              "ffa_periodogram_batch", "ffa_plan_cache_clear",
+              "ffa_periodogram_batch", "ffa_plan_cache_clear", "ffa_periodogram_plan_tiles",
+              "ffa_periodogram_tiles", "ffa_batch_plan_tiles", "ffa_periodogram_batch_tiles",
               "ffa_profile_query"):
         getattr(L, f).restype = i32
     _lib = L
@@ -246,15 +260,34 @@ class PlanInfo:
     folded_samples: int
     workspace_bytes: int
     host_workspace_bytes: int
+    tiles: "Tiles"
+
+
+@dataclass(frozen=True)
+class Tiles:
+    """Tile shape of a plan (0 = the largest that fits shared memory); see ffa_tiles."""
+    subtree_rows: int = 0
+    top_levels: int = 0
+    top_rows: int = 0
+
+
+def _tiles_arg(tiles: Optional[Tiles]):
+    if tiles is None:
+        return None, ctypes.c_void_p(None)
+    t = _Tiles(int(tiles.subtree_rows), int(tiles.top_levels), int(tiles.top_rows))
+    return t, ctypes.cast(ctypes.byref(t), ctypes.c_void_p)
 
 
 def periodogram_plan(n: int, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,
-                     widths: Sequence[int]) -> PlanInfo:
+                     widths: Sequence[int], tiles: Optional[Tiles] = None) -> PlanInfo:
     w = _widths_array(widths)
     info = _PlanInfo()
-    _check(library().ffa_periodogram_plan(n, tsamp, pmin, pmax, bmin, bmax, _vp(w), len(w),
-                                          ctypes.byref(info)))
-    return PlanInfo(*(getattr(info, f) for f, _ in _PlanInfo._fields_))
+    keep, tp = _tiles_arg(tiles)
+    _check(library().ffa_periodogram_plan_tiles(n, tsamp, pmin, pmax, bmin, bmax, _vp(w), len(w),
+                                                tp, ctypes.byref(info)))
+    vals = [getattr(info, f) for f, _ in _PlanInfo._fields_[:-1]]
+    t = info.tiles
+    return PlanInfo(*vals, Tiles(t.subtree_rows, t.top_levels, t.top_rows))
 
 
 def _dtype_code(t) -> int:
@@ -271,11 +304,14 @@ def _dtype_code(t) -> int:
 class Searcher:
     """Holds the workspace and outputs of one search configuration for repeated calls."""
 
-    def __init__(self, n, tsamp, pmin, pmax, bmin, bmax, widths, device="cuda"):
+    def __init__(self, n, tsamp, pmin, pmax, bmin, bmax, widths, device="cuda",
+                 tiles: Optional[Tiles] = None):
         torch = _torch()
         self.args = (int(n), float(tsamp), float(pmin), float(pmax), int(bmin), int(bmax))
         self.widths = _widths_array(widths)
-        self.info = periodogram_plan(*self.args, self.widths)
+        self.tiles = tiles
+        self._tiles_keep, self._tiles_ptr = _tiles_arg(tiles)
+        self.info = periodogram_plan(*self.args, self.widths, tiles)
         T, nw = self.info.ntrials, len(self.widths)
         self.device = torch.device(device)
         self.ws = _workspace(self.info.workspace_bytes, self.device)
@@ -291,16 +327,18 @@ class Searcher:
         if x.numel() != self.args[0]:
             raise ValueError("series length differs from the plan")
         n, tsamp, pmin, pmax, bmin, bmax = self.args
-        _check(library().ffa_periodogram(
+        _check(library().ffa_periodogram_tiles(
             _vp(x), _dtype_code(x), n, tsamp, pmin, pmax, bmin, bmax, _vp(self.widths),
-            len(self.widths), _vp(self._per), _vp(self._fb), _vp(self._snr),
+            len(self.widths), self._tiles_ptr, _vp(self._per), _vp(self._fb), _vp(self._snr),
             self.periods.numel(), _vp(self.ws), self.ws.numel(), _stream_handle(stream)))
         return self.periods, self.foldbins, self.snr
 
     def run_host(self, x_host, periods_h, foldbins_h, snr_h, stream=None):
-        """End to end from host memory: copies in, searches, copies out, synchronises."""
+        """End to end from host memory: copies in, searches, copies out, synchronises
+        (with the automatic tile shape)."""
         if self._host_ws is None:
-            self._host_ws = _workspace(self.info.host_workspace_bytes, self.device)
+            info0 = self.info if self.tiles is None else periodogram_plan(*self.args, self.widths)
+            self._host_ws = _workspace(info0.host_workspace_bytes, self.device)
         n, tsamp, pmin, pmax, bmin, bmax = self.args
         _check(library().ffa_periodogram_host(
             _vp(x_host), n, tsamp, pmin, pmax, bmin, bmax, _vp(self.widths), len(self.widths),
@@ -369,14 +407,16 @@ DEFAULT_BATCH_BUDGET = 1 << 30
 
 
 def batch_plan(series: Sequence[Series], widths: Sequence[int],
-               ws_budget: int = DEFAULT_BATCH_BUDGET):
+               ws_budget: int = DEFAULT_BATCH_BUDGET, tiles: Optional[Tiles] = None):
     """(BatchInfo, trial offsets int64 [len(series) + 1]) of a batch search."""
     w = _widths_array(widths)
     arr = _series_array(series)
     offs = np.zeros(len(series) + 1, np.int64)
     info = _BatchInfo()
-    _check(library().ffa_batch_plan(ctypes.cast(arr, ctypes.c_void_p), len(series), _vp(w),
-                                    len(w), int(ws_budget), _vp(offs), ctypes.byref(info)))
+    keep, tp = _tiles_arg(tiles)
+    _check(library().ffa_batch_plan_tiles(ctypes.cast(arr, ctypes.c_void_p), len(series), _vp(w),
+                                          len(w), int(ws_budget), tp, _vp(offs),
+                                          ctypes.byref(info)))
     return BatchInfo(*(getattr(info, f) for f, _ in _BatchInfo._fields_)), offs
 
 
@@ -389,13 +429,17 @@ class BatchSearcher:
     """
 
     def __init__(self, series: Sequence[Series], widths: Sequence[int],
-                 ws_budget: int = DEFAULT_BATCH_BUDGET, device="cuda"):
+                 ws_budget: int = DEFAULT_BATCH_BUDGET, device="cuda",
+                 tiles: Optional[Tiles] = None):
         torch = _torch()
         self.series = list(series)
         self.widths = _widths_array(widths)
         self.ws_budget = int(ws_budget)
+        self.tiles = tiles
+        self._tiles_keep, self._tiles_ptr = _tiles_arg(tiles)
         self._arr = _series_array(self.series)
-        self.info, self.trial_offsets = batch_plan(self.series, self.widths, self.ws_budget)
+        self.info, self.trial_offsets = batch_plan(self.series, self.widths, self.ws_budget,
+                                                   tiles)
         self.span = max(s.offset + s.n for s in self.series)
         T, nw = self.info.ntrials, len(self.widths)
         self.device = torch.device(device)
@@ -409,10 +453,10 @@ class BatchSearcher:
         _dev_tensor(x, "x")
         if x.numel() < self.span:
             raise ValueError("batch buffer is shorter than the series span")
-        _check(library().ffa_periodogram_batch(
+        _check(library().ffa_periodogram_batch_tiles(
             _vp(x), _dtype_code(x), ctypes.cast(self._arr, ctypes.c_void_p), len(self.series),
-            _vp(self.widths), len(self.widths), self.ws_budget, _vp(self._per), _vp(self._fb),
-            _vp(self._snr), self.periods.numel(), _vp(self.ws), self.ws.numel(),
+            _vp(self.widths), len(self.widths), self.ws_budget, self._tiles_ptr, _vp(self._per),
+            _vp(self._fb), _vp(self._snr), self.periods.numel(), _vp(self.ws), self.ws.numel(),
             _stream_handle(stream)))
         return self.periods, self.foldbins, self.snr
 
@@ -430,6 +474,47 @@ def periodogram_batch(x, series: Sequence[Series], widths: Sequence[int],
     s = BatchSearcher(series, widths, ws_budget, device=x.device)
     per, fb, snr = s(x, stream)
     return per, fb, snr, s.trial_offsets
+
+
+def tile_candidates(auto: Tiles):
+    """A small grid around the automatic tile shape `auto` (the effective tiles that a
+    plan reports): each size as is or halved, one merge level fewer per top pass."""
+    rows = sorted({auto.subtree_rows, max(2, auto.subtree_rows // 2)}, reverse=True)
+    levels = sorted({auto.top_levels, max(1, auto.top_levels - 1)}, reverse=True)
+    krows = sorted({auto.top_rows, max(1, auto.top_rows // 2)}, reverse=True)
+    return [Tiles(r, l, k) for r in rows for l in levels for k in krows]
+
+
+def tune(make, run, candidates: Sequence[Tiles], repeats: int = 3, stream=None):
+    """Times `run(make(tiles))` on the device for every candidate tile shape and returns
+    (fastest tiles, [(tiles, ms per call)]).  `make(tiles)` builds a searcher (plans and
+    workspace), `run(searcher)` launches one search on the current stream.  Every shape
+    gives bit-identical results, so only time decides."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    timings = []
+    for t in candidates:
+        searcher = make(t)
+        run(searcher)  # warm-up: plan tables pinned, caches filled
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(repeats):
+            run(searcher)
+        e1.record(s)
+        e1.synchronize()
+        timings.append((t, e0.elapsed_time(e1) / repeats))
+        del searcher
+    best = min(timings, key=lambda tm: tm[1])[0]
+    return best, timings
+
+
+def tune_periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths, candidates=None, repeats=3):
+    """Fastest tile shape for periodograms of series like `x` (see `tune`)."""
+    args = (x.numel(), tsamp, pmin, pmax, bmin, bmax, widths)
+    if candidates is None:
+        candidates = tile_candidates(periodogram_plan(*args).tiles)
+    return tune(lambda t: Searcher(*args, device=x.device, tiles=t), lambda s: s(x),
+                candidates, repeats)
 
 
 def shard_series(costs: Sequence[float], rank: int, world: int):

@@ -111,7 +111,30 @@ struct SeriesSpec {
     }
 };
 
+// Tile shape of a plan (0 = the largest that fits shared memory).
+struct Tiles {
+    int subtree_rows = 0, top_levels = 0, top_rows = 0;
+    bool operator<(const Tiles& o) const {
+        return std::tie(subtree_rows, top_levels, top_rows) <
+               std::tie(o.subtree_rows, o.top_levels, o.top_rows);
+    }
+};
+
+ffa_status read_tiles(const ffa_tiles* t, Tiles* out) {
+    *out = Tiles{};
+    if (!t) return FFA_OK;
+    if (t->subtree_rows < 0 || t->subtree_rows == 1 || t->subtree_rows > kBottomMaxRows)
+        return fail(FFA_ERR_ARG, "subtree_rows must be 0 or 2..%d", kBottomMaxRows);
+    if (t->top_levels < 0 || t->top_levels > kTopMaxLevels)
+        return fail(FFA_ERR_ARG, "top_levels must be 0..%d", kTopMaxLevels);
+    if (t->top_rows < 0 || t->top_rows > kTopMaxRows)
+        return fail(FFA_ERR_ARG, "top_rows must be 0..%d", kTopMaxRows);
+    *out = Tiles{t->subtree_rows, t->top_levels, t->top_rows};
+    return FFA_OK;
+}
+
 struct Plan {
+    Tiles tiles;
     // parameters
     std::vector<SeriesSpec> series;
     int64_t n = 0;       // input span: max over series of x_off + n
@@ -283,6 +306,7 @@ ffa_status build_plan(Plan& pl) {
                 t.kept = (int)kept;
                 t.depth = depth_for(m, p, pl.row_cap);
                 t.chunk = top_chunk(p, pl.W.wmax, true);
+                if (pl.tiles.top_levels) t.chunk = std::min(t.chunk, pl.tiles.top_levels);
                 if (t.chunk < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
                 t.inv_std = (float)(1.0 / std::sqrt((double)m * var));
                 pl.trs.push_back(t);
@@ -370,7 +394,8 @@ ffa_status build_plan(Plan& pl) {
                 const int dout = top_pass_out_depth(d.depth, d.chunk, j);
                 const int L = top_pass_in_depth(d.depth, d.chunk, j) - dout;
                 const bool score = j == np - 1;
-                const int K = top_rows(d.p, L, score, wmax);
+                int K = top_rows(d.p, L, score, wmax);
+                if (pl.tiles.top_rows) K = std::min(K, pl.tiles.top_rows);
                 if (K < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
                 pl.smem_floats = std::max(pl.smem_floats, top_layout(K, L, d.p, wmax, score).total);
                 const int nmax = (d.m + (1 << dout) - 1) >> dout;
@@ -471,7 +496,7 @@ ffa_status ensure_pinned(Plan& pl) {
 
 // Plan of a list of series, built afresh.  Widths must lie below every series' bmin.
 ffa_status make_plan_series(const std::vector<SeriesSpec>& series, const int32_t* h_widths,
-                            int32_t nw, std::unique_ptr<Plan>* out) {
+                            int32_t nw, const Tiles& tiles, std::unique_ptr<Plan>* out) {
     if (series.empty()) return fail(FFA_ERR_ARG, "no series");
     int bmin_all = INT32_MAX;
     int64_t span = 0;
@@ -486,8 +511,9 @@ ffa_status make_plan_series(const std::vector<SeriesSpec>& series, const int32_t
     ffa_status st = make_widths(h_widths, nw, bmin_all - 1, &W);  // below the smallest base period
     if (st != FFA_OK) return st;
     std::unique_ptr<Plan> pl;
-    for (int cap = kBottomMaxRows;;) {
+    for (int cap = tiles.subtree_rows ? tiles.subtree_rows : kBottomMaxRows;;) {
         pl = std::make_unique<Plan>();
+        pl->tiles = tiles;
         pl->series = series;
         pl->n = span;
         pl->widths.assign(h_widths, h_widths + nw);
@@ -508,13 +534,13 @@ ffa_status make_plan_series(const std::vector<SeriesSpec>& series, const int32_t
 // Plans are cached by parameters for the life of the process (or until
 // ffa_plan_cache_clear): their page-locked tables are the source of copies that a
 // captured CUDA graph replays, so they are never evicted behind the caller's back.
-using PlanKey = std::pair<std::vector<SeriesSpec>, std::vector<int>>;
+using PlanKey = std::tuple<std::vector<SeriesSpec>, std::vector<int>, Tiles>;
 std::map<PlanKey, std::unique_ptr<Plan>> g_plans;
 
 ffa_status get_plan_series(const std::vector<SeriesSpec>& series, const int32_t* h_widths,
-                           int32_t nw, Plan** out) {
+                           int32_t nw, const Tiles& tiles, Plan** out) {
     if (nw > 0 && !h_widths) return fail(FFA_ERR_ARG, "widths is null");
-    PlanKey key{series, std::vector<int>(h_widths, h_widths + std::max(nw, 0))};
+    PlanKey key{series, std::vector<int>(h_widths, h_widths + std::max(nw, 0)), tiles};
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         auto it = g_plans.find(key);
@@ -524,7 +550,7 @@ ffa_status get_plan_series(const std::vector<SeriesSpec>& series, const int32_t*
         }
     }
     std::unique_ptr<Plan> pl;
-    ffa_status st = make_plan_series(series, h_widths, nw, &pl);
+    ffa_status st = make_plan_series(series, h_widths, nw, tiles, &pl);
     if (st != FFA_OK) return st;
     std::lock_guard<std::mutex> lk(g_plan_mu);
     auto ins = g_plans.emplace(key, std::move(pl));  // a concurrent twin keeps the first
@@ -533,8 +559,9 @@ ffa_status get_plan_series(const std::vector<SeriesSpec>& series, const int32_t*
 }
 
 ffa_status get_plan(int64_t n, double tsamp, double pmin, double pmax, int bmin, int bmax,
-                    const int32_t* h_widths, int32_t nw, Plan** out) {
-    return get_plan_series({SeriesSpec{0, n, tsamp, pmin, pmax, bmin, bmax}}, h_widths, nw, out);
+                    const int32_t* h_widths, int32_t nw, const Tiles& tiles, Plan** out) {
+    return get_plan_series({SeriesSpec{0, n, tsamp, pmin, pmax, bmin, bmax}}, h_widths, nw, tiles,
+                           out);
 }
 
 // A batch of series cut into chunks that each run as one periodogram launch sequence
@@ -552,11 +579,11 @@ struct Batch {
     int ntransforms = 0;
     int64_t folded = 0, input = 0;
 };
-using BatchKey = std::tuple<std::vector<SeriesSpec>, std::vector<int>, size_t>;
+using BatchKey = std::tuple<std::vector<SeriesSpec>, std::vector<int>, size_t, Tiles>;
 std::map<BatchKey, std::unique_ptr<Batch>> g_batches;
 
 ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t* h_widths,
-                     int32_t nw, size_t budget, Batch** out) {
+                     int32_t nw, size_t budget, const Tiles& tiles, Batch** out) {
     if (!h_series || nseries < 1) return fail(FFA_ERR_ARG, "no series");
     if (nw > 0 && !h_widths) return fail(FFA_ERR_ARG, "widths is null");
     std::vector<SeriesSpec> all(nseries);
@@ -565,7 +592,7 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
         if (s.offset < 0) return fail(FFA_ERR_ARG, "series %d has a negative offset", i);
         all[i] = SeriesSpec{s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax};
     }
-    BatchKey key{all, std::vector<int>(h_widths, h_widths + std::max(nw, 0)), budget};
+    BatchKey key{all, std::vector<int>(h_widths, h_widths + std::max(nw, 0)), budget, tiles};
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
         auto it = g_batches.find(key);
@@ -584,7 +611,7 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
         auto it = alone.find(s);
         if (it == alone.end()) {
             std::unique_ptr<Plan> p1;
-            ffa_status st = make_plan_series({s}, h_widths, nw, &p1);
+            ffa_status st = make_plan_series({s}, h_widths, nw, tiles, &p1);
             if (st != FFA_OK) return st;
             it = alone.emplace(s, p1->ws_bytes).first;
         }
@@ -604,7 +631,7 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
         auto sh = shapes.find(part);
         if (sh == shapes.end()) {
             std::unique_ptr<Plan> pc;
-            ffa_status st = make_plan_series(part, h_widths, nw, &pc);
+            ffa_status st = make_plan_series(part, h_widths, nw, tiles, &pc);
             if (st != FFA_OK) return st;
             sh = shapes.emplace(part, std::shared_ptr<Plan>(std::move(pc))).first;
         }
@@ -968,12 +995,15 @@ ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out
 }
 
 // ---------------------------------------------------------------------------------
-ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pmax, int32_t bmin,
-                                int32_t bmax, const int32_t* h_widths, int32_t nw,
-                                ffa_plan_info* out) {
+ffa_status ffa_periodogram_plan_tiles(int64_t n, double tsamp, double pmin, double pmax,
+                                      int32_t bmin, int32_t bmax, const int32_t* h_widths,
+                                      int32_t nw, const ffa_tiles* tiles, ffa_plan_info* out) {
     if (!out) return fail(FFA_ERR_ARG, "out is null");
+    Tiles T;
+    ffa_status st = read_tiles(tiles, &T);
+    if (st != FFA_OK) return st;
     Plan* pl = nullptr;
-    ffa_status st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, &pl);
+    st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, T, &pl);
     if (st != FFA_OK) return st;
     std::memset(out, 0, sizeof(*out));
     out->ntrials = pl->ntrials;
@@ -985,18 +1015,33 @@ ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pma
     out->folded_samples = pl->folded;
     out->workspace_bytes = pl->ws_bytes;
     out->host_workspace_bytes = pl->ws_host_bytes;
+    out->tiles = ffa_tiles{std::max(pl->bottom_nmax, pl->bottom0_nmax), 0, 0};
+    for (const TransformDesc& t : pl->trs)
+        if (t.depth > 0) out->tiles.top_levels = std::max(out->tiles.top_levels, (int32_t)t.chunk);
+    for (const WorkItem& it : pl->items)
+        if (it.pass >= 0) out->tiles.top_rows = std::max(out->tiles.top_rows, (int32_t)it.rows);
     return FFA_OK;
 }
 
-ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp, double pmin,
-                           double pmax, int32_t bmin, int32_t bmax, const int32_t* h_widths,
-                           int32_t nw, double* d_periods, int32_t* d_foldbins, float* d_snr,
-                           int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream) {
+ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pmax, int32_t bmin,
+                                int32_t bmax, const int32_t* h_widths, int32_t nw,
+                                ffa_plan_info* out) {
+    return ffa_periodogram_plan_tiles(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, nullptr, out);
+}
+
+ffa_status ffa_periodogram_tiles(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp,
+                                 double pmin, double pmax, int32_t bmin, int32_t bmax,
+                                 const int32_t* h_widths, int32_t nw, const ffa_tiles* tiles,
+                                 double* d_periods, int32_t* d_foldbins, float* d_snr,
+                                 int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream) {
     if (!d_x || !d_periods || !d_foldbins || !d_snr || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
     if (dtype != FFA_F32 && dtype != FFA_F16 && dtype != FFA_I8) return fail(FFA_ERR_ARG, "bad dtype");
     if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
+    Tiles T;
+    ffa_status st = read_tiles(tiles, &T);
+    if (st != FFA_OK) return st;
     Plan* pl = nullptr;
-    ffa_status st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, &pl);
+    st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, T, &pl);
     if (st != FFA_OK) return st;
     if (ntrials_cap < pl->ntrials)
         return fail(FFA_ERR_CAPACITY, "ntrials_cap %lld < %lld", (long long)ntrials_cap,
@@ -1008,6 +1053,15 @@ ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double t
                            static_cast<cudaStream_t>(stream));
 }
 
+ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp, double pmin,
+                           double pmax, int32_t bmin, int32_t bmax, const int32_t* h_widths,
+                           int32_t nw, double* d_periods, int32_t* d_foldbins, float* d_snr,
+                           int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream) {
+    return ffa_periodogram_tiles(d_x, dtype, n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw,
+                                 nullptr, d_periods, d_foldbins, d_snr, ntrials_cap, d_ws,
+                                 ws_bytes, stream);
+}
+
 ffa_status ffa_plan_cache_clear(void) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_batches.clear();
@@ -1015,12 +1069,16 @@ ffa_status ffa_plan_cache_clear(void) {
     return FFA_OK;
 }
 
-ffa_status ffa_batch_plan(const ffa_series* h_series, int32_t nseries, const int32_t* h_widths,
-                          int32_t nw, size_t ws_budget, int64_t* h_trial_offsets,
-                          ffa_batch_info* out) {
+ffa_status ffa_batch_plan_tiles(const ffa_series* h_series, int32_t nseries,
+                                const int32_t* h_widths, int32_t nw, size_t ws_budget,
+                                const ffa_tiles* tiles, int64_t* h_trial_offsets,
+                                ffa_batch_info* out) {
     if (!out) return fail(FFA_ERR_ARG, "out is null");
+    Tiles T;
+    ffa_status st = read_tiles(tiles, &T);
+    if (st != FFA_OK) return st;
     Batch* B = nullptr;
-    ffa_status st = get_batch(h_series, nseries, h_widths, nw, ws_budget, &B);
+    st = get_batch(h_series, nseries, h_widths, nw, ws_budget, T, &B);
     if (st != FFA_OK) return st;
     std::memset(out, 0, sizeof(*out));
     out->ntrials = B->trial0.back();
@@ -1034,16 +1092,27 @@ ffa_status ffa_batch_plan(const ffa_series* h_series, int32_t nseries, const int
     return FFA_OK;
 }
 
-ffa_status ffa_periodogram_batch(const void* d_x, ffa_dtype dtype, const ffa_series* h_series,
-                                 int32_t nseries, const int32_t* h_widths, int32_t nw,
-                                 size_t ws_budget, double* d_periods, int32_t* d_foldbins,
-                                 float* d_snr, int64_t ntrials_cap, void* d_ws, size_t ws_bytes,
-                                 void* stream) {
+ffa_status ffa_batch_plan(const ffa_series* h_series, int32_t nseries, const int32_t* h_widths,
+                          int32_t nw, size_t ws_budget, int64_t* h_trial_offsets,
+                          ffa_batch_info* out) {
+    return ffa_batch_plan_tiles(h_series, nseries, h_widths, nw, ws_budget, nullptr,
+                                h_trial_offsets, out);
+}
+
+ffa_status ffa_periodogram_batch_tiles(const void* d_x, ffa_dtype dtype,
+                                       const ffa_series* h_series, int32_t nseries,
+                                       const int32_t* h_widths, int32_t nw, size_t ws_budget,
+                                       const ffa_tiles* tiles, double* d_periods,
+                                       int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
+                                       void* d_ws, size_t ws_bytes, void* stream) {
     if (!d_x || !d_periods || !d_foldbins || !d_snr || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
     if (dtype != FFA_F32 && dtype != FFA_F16 && dtype != FFA_I8) return fail(FFA_ERR_ARG, "bad dtype");
     if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
+    Tiles T;
+    ffa_status st = read_tiles(tiles, &T);
+    if (st != FFA_OK) return st;
     Batch* B = nullptr;
-    ffa_status st = get_batch(h_series, nseries, h_widths, nw, ws_budget, &B);
+    st = get_batch(h_series, nseries, h_widths, nw, ws_budget, T, &B);
     if (st != FFA_OK) return st;
     if (ntrials_cap < B->trial0.back()) return fail(FFA_ERR_CAPACITY, "ntrials_cap too small");
     if (ws_bytes < B->ws_bytes) return fail(FFA_ERR_CAPACITY, "workspace needs %zu bytes", B->ws_bytes);
@@ -1062,6 +1131,16 @@ ffa_status ffa_periodogram_batch(const void* d_x, ffa_dtype dtype, const ffa_ser
     return FFA_OK;
 }
 
+ffa_status ffa_periodogram_batch(const void* d_x, ffa_dtype dtype, const ffa_series* h_series,
+                                 int32_t nseries, const int32_t* h_widths, int32_t nw,
+                                 size_t ws_budget, double* d_periods, int32_t* d_foldbins,
+                                 float* d_snr, int64_t ntrials_cap, void* d_ws, size_t ws_bytes,
+                                 void* stream) {
+    return ffa_periodogram_batch_tiles(d_x, dtype, h_series, nseries, h_widths, nw, ws_budget,
+                                       nullptr, d_periods, d_foldbins, d_snr, ntrials_cap, d_ws,
+                                       ws_bytes, stream);
+}
+
 ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, double pmin,
                                 double pmax, int32_t bmin, int32_t bmax, const int32_t* h_widths,
                                 int32_t nw, double* h_periods, int32_t* h_foldbins, float* h_snr,
@@ -1069,7 +1148,7 @@ ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, doubl
     if (!h_x || !h_periods || !h_foldbins || !h_snr || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
     if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
     Plan* pl = nullptr;
-    ffa_status st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, &pl);
+    ffa_status st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, Tiles{}, &pl);
     if (st != FFA_OK) return st;
     if (ntrials_cap < pl->ntrials) return fail(FFA_ERR_CAPACITY, "ntrials_cap too small");
     if (ws_bytes < pl->ws_host_bytes)

@@ -347,7 +347,7 @@ struct TopParams {
     int single_rows;
 };
 
-constexpr int kMaxStages = 8;  // sub-trees + up to 7 top passes per transform
+constexpr int kMaxStages = 16;  // sub-trees + up to 15 top passes per transform
 
 struct PersistentParams {
     BottomParams bottom;            // sub-tree items (pass -1)

@@ -154,3 +154,25 @@ def test_batch_rejects_bad_series(lib):
         ffa.batch_plan(bad, b.widths)
     with pytest.raises(ffa.FFAError):
         ffa.batch_plan([], b.widths)
+
+
+def test_tiles_cap_the_plan(lib):
+    args = (2 ** 23, 64e-6, 0.2, 20.0, 240, 260, synth.WIDTHS_11)
+    auto = ffa.periodogram_plan(*args)
+    assert auto.tiles.subtree_rows >= 2 and 1 <= auto.tiles.top_levels <= 3
+    for t in ffa.tile_candidates(auto.tiles) + [ffa.Tiles(16, 1, 8), ffa.Tiles(0, 2, 0)]:
+        info = ffa.periodogram_plan(*args, tiles=t)
+        # the same search, only the work items differ
+        assert (info.ntrials, info.ntransforms, info.folded_samples) == \
+            (auto.ntrials, auto.ntransforms, auto.folded_samples)
+        for got, cap in zip((info.tiles.subtree_rows, info.tiles.top_levels, info.tiles.top_rows),
+                            (t.subtree_rows, t.top_levels, t.top_rows)):
+            assert cap == 0 or got <= cap
+
+
+@pytest.mark.parametrize("bad", [ffa.Tiles(1, 0, 0), ffa.Tiles(2000, 0, 0), ffa.Tiles(0, 4, 0),
+                                 ffa.Tiles(0, -1, 0), ffa.Tiles(0, 0, 129)])
+def test_tiles_rejected(lib, bad):
+    with pytest.raises(ffa.FFAError) as e:
+        ffa.periodogram_plan(262144, 1e-3, 1.0, 10.0, 240, 260, (1, 2, 4), tiles=bad)
+    assert e.value.status == 1
