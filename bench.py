@@ -74,14 +74,22 @@ def parse():
     return ap.parse_args()
 
 
+def kernel_source_sha():
+    """First 16 hex digits of the SHA-256 of the kernel sources (the .cu file and the
+    header that fixes its constants and layouts)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ffa_kernels.cu", "ffa_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2004_03701_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic(kernel, workload):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu record, or
     None if there is none or the kernel source changed since it was taken."""
-    import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_2004_03701_gb300", "csrc", "ffa_kernels.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_prefix"]:
+        if kernel_source_sha() != rec["kernel_source_sha256_prefix"]:
             return None
         if rec["kernel"] != kernel or rec.get("workload", workload) != workload:
             return None
@@ -196,7 +204,7 @@ def oracle_sample_time(w, stride, offset=0, full_ds=True):
              stride, pl.n_transforms, 100.0 / ratio, t_ds_meas + t_sel))
     rows = (np.concatenate([np.arange(pl.tr_first_trial[t], pl.tr_first_trial[t] + pl.tr_kept[t])
                             for t in np.flatnonzero(sel)]) if sel.any() else np.zeros(0, np.int64))
-    return est, desc, (rows, ref)
+    return est, desc, (rows, ref, pl, sel, w.x)
 
 
 def oracle_rate(job, stride, offset=0, full_ds=True):
@@ -232,7 +240,7 @@ def accuracy(job, checks):
     trials (the oracle searched the same stored values), periods and fold bins
     compared exactly, and whether the strongest sampled trial is the same."""
     err, n, same_best, exact = 0.0, 0, True, True
-    for i, rows, ref in checks:
+    for i, rows, ref, _, _, _ in checks:
         if len(rows) == 0:
             continue
         got = job.searcher.series_result(i) if i is not None else \
@@ -244,10 +252,29 @@ def accuracy(job, checks):
         n += len(rows)
         same_best &= bool(np.unravel_index(snr.argmax(), snr.shape) ==
                           np.unravel_index(ref.snr.argmax(), ref.snr.shape))
+    prof = profile_error(job, checks[0])
     return {"max_snr_error": err, "trials_compared": n, "periods_foldbins_identical": exact,
-            "top_candidate_identical": same_best,
+            "top_candidate_identical": same_best, "profile": prof,
             "reference": "FP64 oracle on the values the GPU searched (dequantised for f16/i8 "
                          "storage), on the cpu_baseline sample of trials"}
+
+
+def profile_error(job, check):
+    """Max error of the FP32 FFA profiles against the FP64 oracle's, on the same
+    downsampled block: the sampled transform with the most rows."""
+    import oracle
+    _, _, _, pl, sel, x = check
+    idx = np.flatnonzero(sel)
+    if len(idx) == 0:
+        return None
+    t = idx[np.argmax(pl.tr_m[idx])]
+    m, p = int(pl.tr_m[t]), int(pl.tr_p[t])
+    block = oracle.downsample(x, float(pl.oct_factor[pl.tr_octave[t]]))[:m * p].reshape(m, p)
+    ref = oracle.ffa(block)
+    got = job.ffa.ffa_transform(job.torch.from_numpy(block.astype(np.float32)).to(job.dev))
+    got = got.cpu().numpy().astype(np.float64)
+    return {"max_abs_error": float(np.abs(got - ref).max()), "m": m, "p": p,
+            "profile_rms": float(np.sqrt(np.mean(ref * ref)))}
 
 
 # --------------------------------------------------------------------------- workloads
