@@ -75,12 +75,17 @@ def parse():
 
 
 def kernel_source_sha():
-    """First 16 hex digits of the SHA-256 of the kernel sources (the .cu file and the
-    header that fixes its constants and layouts)."""
+    """First 16 hex digits of the SHA-256 of the kernel code: the .cu file and the header
+    that fixes its constants and layouts, with comments and blank space removed (a
+    comment edit does not change the kernel whose counters were recorded)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("ffa_kernels.cu", "ffa_internal.h"):
-        h.update(open(os.path.join(ROOT, "paper_2004_03701_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2004_03701_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

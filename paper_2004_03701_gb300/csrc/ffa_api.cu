@@ -421,7 +421,8 @@ ffa_status build_plan(Plan& pl) {
     if ((pl.smem_floats + 4) * 4 > kSmemBytes) return kRetrySmaller;
     pl.nitems = (int)pl.items.size();
 
-    // Tables: octaves | transforms | items, each 256-byte aligned.
+    // Tables: octaves | transforms | items | downsampling CTAs | stage counts | prefix
+    // series | prefix chunks, each 256-byte aligned.
     size_t o = 0;
     pl.o_oct = o;
     o = align_up(o + pl.oct.size() * sizeof(OctaveDesc), 256);
@@ -439,7 +440,8 @@ ffa_status build_plan(Plan& pl) {
     o = align_up(o + pl.blk_seg.size() * sizeof(int), 256);
     pl.tables_bytes = std::max<size_t>(o, 256);
 
-    // Workspace: status | tables | prefix | chunk sums | series | scratch 0 | scratch 1
+    // Workspace: status | tables | prefix | chunk sums | octave series | scratch 0 |
+    // scratch 1 | stage counters | top-pass records
     pl.nchunks = (int64_t)pl.blk_seg.size();
     size_t w = kStatusBytes;
     pl.o_tables = w;

@@ -1,21 +1,25 @@
 // ffa_kernels.cu -- sm_103a kernels of the FFA periodogram (Morello et al. 2020).
 //
-//   prefix_*      double-float exclusive prefix sums of the raw series, so that every
-//                 real-factor downsampling window (Sec. 5.3, App. A.4) costs two
-//                 lookups instead of re-reading ~f raw samples per output sample.
-//   downsample    all pseudo-octaves in one launch; window edges i*f in exact 64.64
-//                 fixed point, partial samples weighted by their overlap.
-//   ffa_bottom    one CTA per depth-D sub-tree of an FFA transform: the rows arrive by
-//                 one bulk asynchronous copy (cp.async.bulk + mbarrier), then every
-//                 merge level of the sub-tree (Eq. ffa_merge_rule) runs in shared
-//                 memory; either writes the sub-tree's transform or, when the sub-tree
-//                 is the whole transform, scores its rows directly (fused S/N).
-//   ffa_top       the levels above the sub-trees, up to three per pass: a CTA gathers
-//                 only the rows its block of outputs depends on (one interval per
-//                 descendant, one bulk copy each) and merges them in shared memory;
-//                 the last pass of a periodogram scores its rows with the boxcar
-//                 filters (Sec. 5.4), so final profiles are never stored.
+//   prefix_*      double-float exclusive prefix sums of every raw series (restarting at
+//                 each series), so that every real-factor downsampling window (Sec.
+//                 5.3, App. A.4) costs two lookups instead of re-reading ~f raw samples.
+//   downsample    all pseudo-octaves of all series in one launch; window edges i*f in
+//                 exact 64.64 fixed point, partial samples weighted by their overlap.
+//   top_prep      the records of all top-pass work items (row intervals, shared-memory
+//                 offsets, bulk-copy bytes), one thread per item.
+//   ffa_persistent  one CTA per SM takes work items from a queue until the periodogram
+//                 is done.  Sub-tree items (bottom_item): the rows of a node arrive by
+//                 one bulk asynchronous copy (cp.async.bulk + mbarrier), nodes of up to
+//                 16 rows are transformed in registers, the remaining levels (Eq.
+//                 ffa_merge_rule) in shared memory; the sub-tree is written out or, when
+//                 it is the whole transform, scored (fused S/N).  Top-pass items
+//                 (top_item): up to three levels above the sub-trees for a block of
+//                 output rows, gathering only the row intervals the block depends on;
+//                 the last pass scores its rows with the boxcar filters (Sec. 5.4), so
+//                 final profiles are never stored.
+//   ffa_bottom, ffa_top  the same items as plain grids, for a single ffa_transform.
 //   boxcar_snr    standalone S/N of stored profiles.
+//   normalise_*   whole-series FP64 mean and standard deviation, FP32/FP16/int8 output.
 //
 // Every floating-point add of the FFA is the same single float add of H_i[x] and
 // T_j[(x + i + b) mod p] that the recursion performs, so transforms are bit-exact.
