@@ -176,3 +176,12 @@ def test_tiles_rejected(lib, bad):
     with pytest.raises(ffa.FFAError) as e:
         ffa.periodogram_plan(262144, 1e-3, 1.0, 10.0, 240, 260, (1, 2, 4), tiles=bad)
     assert e.value.status == 1
+
+
+def test_batch_tiles_rejected_and_accepted(lib):
+    b, ser = _batch_series(2)
+    with pytest.raises(ffa.FFAError):
+        ffa.batch_plan(ser, b.widths, tiles=ffa.Tiles(0, 9, 0))
+    info, offs = ffa.batch_plan(ser, b.widths, tiles=ffa.Tiles(12, 2, 8))
+    ref, offs0 = ffa.batch_plan(ser, b.widths)
+    assert np.array_equal(offs, offs0) and info.ntrials == ref.ntrials
