@@ -84,6 +84,9 @@ def test_downsample(F, n, f):
 @pytest.mark.parametrize("rows,cols,widths", [
     (1, 1, (1,)), (3, 7, (1, 2, 7)), (1000, 240, synth.WIDTHS_11), (777, 260, synth.WIDTHS_11),
     (300, 520, synth.WIDTHS_16), (50, 64, tuple(range(1, 33))),
+    # the last half-warp size (Q = 35), the first warp-per-row size, and long profiles
+    (41, 560, synth.WIDTHS_16), (41, 561, synth.WIDTHS_16), (20, 1024, synth.WIDTHS_16),
+    (5, 4096, (1, 64, 1000)),
 ])
 def test_boxcar_snr(F, rows, cols, widths):
     m = 500
@@ -184,6 +187,25 @@ def test_periodogram_ragged_small(F):
         got = F.periodogram(dev(x), tsamp, pmin, pmax, bmin, bmax, widths)
         ref = oracle.periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths)
         compare_periodogram(got, ref)
+
+
+@pytest.mark.parametrize("bins,widths", [
+    ((545, 560), (1, 2, 3, 5, 8, 13, 21, 34, 55, 89, 144)),   # half-warp S/N, Q = 35
+    ((983, 1065), (1, 2, 4, 8, 16, 32, 64, 128, 200)),       # the paper's context bins
+])
+def test_periodogram_long_profiles(F, bins, widths):
+    """Base periods above the half-warp S/N limit score stored rows one warp each;
+    sampled transforms of a 2^20-sample series at 64 us, P 1-10 s."""
+    n, tsamp, pmin, pmax = 2 ** 20, 64e-6, 1.0, 10.0
+    x = synth.make_series(n, tsamp, seed=bins[0], pulses=[synth.Pulse(2.2, 0.03, 12.0, 0.3)])
+    args = (tsamp, pmin, pmax, bins[0], bins[1], widths)
+    got = F.periodogram(dev(x), *args)
+    pl = oracle.plan(n, *args[:-1])
+    sel = np.zeros(pl.n_transforms, bool)
+    sel[[0, pl.n_transforms - 1, int(np.argmax(pl.tr_m))]] = True
+    sel[synth.rng(bins[0]).choice(pl.n_transforms, 5, replace=False)] = True
+    ref = oracle.periodogram(x, *args, select=sel)
+    compare_periodogram(got, ref, _sampled_rows(pl, sel))
 
 
 def test_status_and_launch_accounting(F):
