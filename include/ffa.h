@@ -200,7 +200,12 @@ ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double t
                            int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
                            void* d_ws, size_t ws_bytes, void* stream);
 /* Same with a tile shape (NULL = automatic); the workspace is the one that
- * ffa_periodogram_plan_tiles reports for the same tiles. */
+ * ffa_periodogram_plan_tiles reports for the same tiles.
+ * All periodogram calls: the first call of a host thread on a device also creates a
+ * helper stream and two events of that thread (the top-pass records are made on it,
+ * concurrently with the prefix sums and downsampling, and joined back into `stream`).
+ * Make that first call outside any stream capture; later calls capture as one graph
+ * with a fork and a join. */
 ffa_status ffa_periodogram_tiles(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp,
                                  double pmin, double pmax, int32_t bmin, int32_t bmax,
                                  const int32_t* h_widths, int32_t nw, const ffa_tiles* tiles,

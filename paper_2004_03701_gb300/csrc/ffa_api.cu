@@ -656,6 +656,33 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
 
 // Issues the whole periodogram on `st`: tables upload, prefix, downsampling, then
 // the FFA + S/N launches group by group.
+// A second stream per host thread and device, with a fork and a join event: the
+// top-pass records are made on it while the prefix sums and downsampling run.  Made on
+// a thread's first periodogram call on a device (so that call should precede any stream
+// capture); if it cannot be made, everything runs on the caller's stream.
+struct SideStream {
+    int dev = -1;
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+SideStream* side_stream() {
+    thread_local SideStream t;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (t.dev == dev) return &t;
+    SideStream n;
+    n.dev = dev;
+    if (cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n.fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n.join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();  // clear; fall back to the caller's stream
+        return nullptr;
+    }
+    t = n;  // the previous device's stream and events stay (a thread rarely switches)
+    return &t;
+}
+
 ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d_periods,
                            int32_t* d_foldbins, float* d_snr, char* ws, cudaStream_t st,
                            bool reset_status = true) {
@@ -674,32 +701,8 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     float* s0 = reinterpret_cast<float*>(ws + pl.o_s0);
     float* s1 = reinterpret_cast<float*>(ws + pl.o_s1);
 
-    PrefixParams xp{};
-    xp.x = d_x;
-    xp.dtype = dtype;
-    xp.segs = reinterpret_cast<const PrefixSeg*>(ws + pl.o_tables + pl.o_segs);
-    xp.blk_seg = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_blkseg);
-    xp.nsegs = (int)pl.segs.size();
-    xp.partial = reinterpret_cast<float2*>(ws + pl.o_partial);
-    xp.prefix = prefix;
-    xp.nchunks = pl.nchunks;
-    xp.total = pl.input_total;
-    FFA_CUDA(launch_prefix(xp, st), "prefix launch");
-    DownsampleParams dp{};
-    dp.x = d_x;
-    dp.dtype = dtype;
-    dp.n = pl.n;
-    dp.prefix = prefix;
-    dp.oct = d_oct;
-    dp.blocks = reinterpret_cast<const int2*>(ws + pl.o_tables + pl.o_dsblk);
-    dp.nblocks = (int)pl.ds_blocks.size();
-    dp.total = pl.ds_total;
-    dp.out = ds;
-    FFA_CUDA(launch_downsample(dp, st), "downsample launch");
-
-    // ---- all FFA work: one persistent launch over the plan's queue
+    // ---- parameters of the persistent launch (the top-pass records are made first)
     int* counters = reinterpret_cast<int*>(ws + pl.o_counters);
-    FFA_CUDA(cudaMemsetAsync(counters, 0, pl.counter_bytes, st), "cudaMemsetAsync(counters)");
     PersistentParams pp{};
     BottomParams& bp = pp.bottom;
     bp.src = ds;
@@ -736,7 +739,47 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     pp.done = counters + 1;
     pp.stage_count = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt);
     pp.smem_floats = pl.smem_floats;
-    FFA_CUDA(launch_top_prep(tp, pl.nitems, pl.ntop, recs, st), "top_prep launch");
+
+    // ---- top-pass records on a side stream, concurrent with prefix sums and
+    //      downsampling (they need only the tables); joined before the FFA launch
+    SideStream* side = side_stream();
+    cudaStream_t sp = st;
+    if (side && pl.ntop > 0) {
+        FFA_CUDA(cudaEventRecord(side->fork, st), "cudaEventRecord(fork)");
+        FFA_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0), "cudaStreamWaitEvent(fork)");
+        sp = side->s;
+    }
+    FFA_CUDA(launch_top_prep(tp, pl.nitems, pl.ntop, recs, sp), "top_prep launch");
+    if (sp != st) {
+        FFA_CUDA(cudaEventRecord(side->join, sp), "cudaEventRecord(join)");
+    }
+
+    PrefixParams xp{};
+    xp.x = d_x;
+    xp.dtype = dtype;
+    xp.segs = reinterpret_cast<const PrefixSeg*>(ws + pl.o_tables + pl.o_segs);
+    xp.blk_seg = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_blkseg);
+    xp.nsegs = (int)pl.segs.size();
+    xp.partial = reinterpret_cast<float2*>(ws + pl.o_partial);
+    xp.prefix = prefix;
+    xp.nchunks = pl.nchunks;
+    xp.total = pl.input_total;
+    FFA_CUDA(launch_prefix(xp, st), "prefix launch");
+    DownsampleParams dp{};
+    dp.x = d_x;
+    dp.dtype = dtype;
+    dp.n = pl.n;
+    dp.prefix = prefix;
+    dp.oct = d_oct;
+    dp.blocks = reinterpret_cast<const int2*>(ws + pl.o_tables + pl.o_dsblk);
+    dp.nblocks = (int)pl.ds_blocks.size();
+    dp.total = pl.ds_total;
+    dp.out = ds;
+    FFA_CUDA(launch_downsample(dp, st), "downsample launch");
+
+    // ---- all FFA work: one persistent launch over the plan's queue
+    FFA_CUDA(cudaMemsetAsync(counters, 0, pl.counter_bytes, st), "cudaMemsetAsync(counters)");
+    if (sp != st) FFA_CUDA(cudaStreamWaitEvent(st, side->join, 0), "cudaStreamWaitEvent(join)");
     {
         LaunchScope ls(kFfaPersistent, pl.ffa_bytes, st);
         FFA_CUDA(launch_persistent(pp, (pl.smem_floats + 4) * 4, st), "ffa_persistent launch");
