@@ -258,10 +258,40 @@ def accuracy(job, checks):
         same_best &= bool(np.unravel_index(snr.argmax(), snr.shape) ==
                           np.unravel_index(ref.snr.argmax(), ref.snr.shape))
     prof = profile_error(job, checks[0])
-    return {"max_snr_error": err, "trials_compared": n, "periods_foldbins_identical": exact,
-            "top_candidate_identical": same_best, "profile": prof,
-            "reference": "FP64 oracle on the values the GPU searched (dequantised for f16/i8 "
-                         "storage), on the cpu_baseline sample of trials"}
+    out = {"max_snr_error": err, "trials_compared": n, "periods_foldbins_identical": exact,
+           "top_candidate_identical": same_best, "profile": prof,
+           "reference": "FP64 oracle on the values the GPU searched (dequantised for f16/i8 "
+                        "storage), on the cpu_baseline sample of trials"}
+    if job.store != "f32":
+        out["vs_fp32_input"] = quantisation_error(job, checks)
+    return out
+
+
+def quantisation_error(job, checks):
+    """For FP16/int8 storage: the same sampled trials against the FP64 oracle run on the
+    FP32 series normalised in FP64 by the oracle (the search assumes normalised input,
+    Sec. 3.1), so the difference is the storage rounding alone."""
+    import oracle
+    err, same_best = 0.0, True
+    for i, rows, _, pl, sel, _ in checks:
+        if len(rows) == 0:
+            continue
+        if i is None:
+            w = job.single
+            x, args = w.x, (w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths)
+        else:
+            s = job.batch.series[i]
+            x, args = job.batch.series_x(i), (s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax,
+                                              job.batch.widths)
+        ref = oracle.periodogram(oracle.normalise(x)[2], *args, select=sel)
+        got = job.searcher.series_result(i) if i is not None else \
+            (job.searcher.periods, job.searcher.foldbins, job.searcher.snr)
+        snr = got[2].cpu().numpy()[rows].astype(np.float64)
+        err = max(err, float(np.abs(snr - ref.snr).max()))
+        same_best &= bool(np.unravel_index(snr.argmax(), snr.shape) ==
+                          np.unravel_index(ref.snr.argmax(), ref.snr.shape))
+    return {"max_snr_error": err, "top_candidate_identical": same_best,
+            "reference": "FP64 oracle on the oracle-normalised FP32 series"}
 
 
 def profile_error(job, check):
