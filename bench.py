@@ -616,6 +616,17 @@ def run_ffa(a):
                 "share_of_step": kq["ms"] / tot_ms if tot_ms else None,
                 "launches_per_step": kq["launches"] / a.steps}
     if job.batch is None and top == "ffa_persistent":
+        # the same kernel against the FP32 ALU: the method's adds, subtracts and maxima
+        # over 128 FP32 lanes per SM at the maximum SM clock
+        i = s.info
+        ops = i.ffa_adds + i.snr_ops
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clk or {}).get("sm_max_mhz") or 2070.0
+        alu_peak = sms * 128 * mhz * 1e6 / 1e12
+        alu = ops / avg_s / 1e12
+        roofline["alu"] = {"ops_per_launch": ops, "achieved": alu, "peak": alu_peak,
+                           "unit": "TFLOP/s", "frac": alu / alu_peak,
+                           "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz" % (sms, mhz)}
         # whole-step effective fraction: B_ref = sum_k (read the raw series + write
         # octave k) + the FFA + S/N term, over the device time of one step
         i = s.info

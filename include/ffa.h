@@ -169,6 +169,10 @@ typedef struct ffa_plan_info {
     size_t host_workspace_bytes;      /* for ffa_periodogram_host (includes I/O)     */
     ffa_tiles tiles;                  /* tiles in effect: largest sub-tree, levels per
                                          top pass and rows per top item of the plan  */
+    double ffa_adds;                  /* FP32 adds of all merges (one per element of
+                                         every merged row)                           */
+    double snr_ops;                   /* FP32 operations of the S/N: per kept profile
+                                         p prefix adds + 2 p per width               */
 } ffa_plan_info;
 
 ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pmax,

@@ -56,7 +56,8 @@ class _PlanInfo(ctypes.Structure):
                 ("ntransforms", ctypes.c_int32), ("nwidths", ctypes.c_int32),
                 ("max_rows", ctypes.c_int32), ("downsampled_samples", ctypes.c_int64),
                 ("folded_samples", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
-                ("host_workspace_bytes", ctypes.c_size_t), ("tiles", _Tiles)]
+                ("host_workspace_bytes", ctypes.c_size_t), ("tiles", _Tiles),
+                ("ffa_adds", ctypes.c_double), ("snr_ops", ctypes.c_double)]
 
 
 class _Series(ctypes.Structure):
@@ -261,6 +262,8 @@ class PlanInfo:
     workspace_bytes: int
     host_workspace_bytes: int
     tiles: "Tiles"
+    ffa_adds: float
+    snr_ops: float
 
 
 @dataclass(frozen=True)
@@ -285,9 +288,10 @@ def periodogram_plan(n: int, tsamp: float, pmin: float, pmax: float, bmin: int, 
     keep, tp = _tiles_arg(tiles)
     _check(library().ffa_periodogram_plan_tiles(n, tsamp, pmin, pmax, bmin, bmax, _vp(w), len(w),
                                                 tp, ctypes.byref(info)))
-    vals = [getattr(info, f) for f, _ in _PlanInfo._fields_[:-1]]
+    vals = [getattr(info, f) for f, _ in _PlanInfo._fields_[:-3]]
     t = info.tiles
-    return PlanInfo(*vals, Tiles(t.subtree_rows, t.top_levels, t.top_rows))
+    return PlanInfo(*vals, Tiles(t.subtree_rows, t.top_levels, t.top_rows), info.ffa_adds,
+                    info.snr_ops)
 
 
 def _dtype_code(t) -> int:

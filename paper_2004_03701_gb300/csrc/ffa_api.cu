@@ -157,6 +157,7 @@ struct Plan {
     int smem_floats = 0;
     int nitems = 0;
     double ffa_bytes = 0;  // algorithmic bytes of the FFA + S/N: per transform 4 m p + 4 nw kept
+    double ffa_adds = 0, snr_ops = 0;  // arithmetic of the method (FP32 operations)
     size_t o_counters = 0, counter_bytes = 0;
     int64_t ntrials = 0, ds_total = 0, ds_floats = 0, scratch_floats = 0, folded = 0;
     int max_rows = 0, max_p = 0;
@@ -245,6 +246,18 @@ void fixed_point(double f, uint64_t* fi, uint64_t* ff) {
     *ff = (uint64_t)std::ldexp(f - fl, 64);
 }
 
+// Rows produced by all merges of an n-row transform: every node of two or more rows
+// produces all of its rows (head ⌊n/2⌋, tail n - ⌊n/2⌋, Sec. 2.2).
+double merged_rows(int n) {
+    static thread_local std::map<int, double> memo;
+    if (n < 2) return 0.0;
+    auto it = memo.find(n);
+    if (it != memo.end()) return it->second;
+    const double r = n + merged_rows(n >> 1) + merged_rows(n - (n >> 1));
+    memo[n] = r;
+    return r;
+}
+
 ffa_status build_plan(Plan& pl) {
     int64_t ds_off = 0, first = 0, trial = 0;
     pl.series_trial0.clear();
@@ -312,6 +325,11 @@ ffa_status build_plan(Plan& pl) {
                 pl.trs.push_back(t);
                 trial += kept;
                 pl.folded += (int64_t)m * p;
+                // arithmetic of the method: one add per element of every merged row
+                // (Eq. ffa_merge_rule), then per kept profile p prefix adds and, per
+                // width and phase, one subtract and one max (Sec. 5.4)
+                pl.ffa_adds += (double)merged_rows(m) * p;
+                pl.snr_ops += (double)kept * p * (1.0 + 2.0 * pl.W.nw);
                 pl.max_rows = std::max(pl.max_rows, m);
                 pl.max_p = std::max(pl.max_p, p);
             }
@@ -1058,6 +1076,8 @@ ffa_status ffa_periodogram_plan_tiles(int64_t n, double tsamp, double pmin, doub
     out->max_rows = pl->max_rows;
     out->downsampled_samples = pl->ds_total;
     out->folded_samples = pl->folded;
+    out->ffa_adds = pl->ffa_adds;
+    out->snr_ops = pl->snr_ops;
     out->workspace_bytes = pl->ws_bytes;
     out->host_workspace_bytes = pl->ws_host_bytes;
     out->tiles = ffa_tiles{std::max(pl->bottom_nmax, pl->bottom0_nmax), 0, 0};

@@ -185,3 +185,21 @@ def test_batch_tiles_rejected_and_accepted(lib):
     info, offs = ffa.batch_plan(ser, b.widths, tiles=ffa.Tiles(12, 2, 8))
     ref, offs0 = ffa.batch_plan(ser, b.widths)
     assert np.array_equal(offs, offs0) and info.ntrials == ref.ntrials
+
+
+def test_plan_arithmetic_counts(lib):
+    """The plan's operation counts against an independent count over the oracle's plan:
+    an n-row FFA produces n rows at its top node plus those of its two halves."""
+    from functools import lru_cache
+
+    @lru_cache(None)
+    def rows(n):
+        return 0 if n < 2 else n + rows(n // 2) + rows(n - n // 2)
+
+    for args, widths in [((2 ** 23, 64e-6, 0.2, 20.0, 240, 260), synth.WIDTHS_11),
+                         ((100_000, 1e-3, 0.5, 3.0, 40, 44), (1, 2, 3))]:
+        info = ffa.periodogram_plan(*args, widths)
+        pl = oracle.plan(*args)
+        adds = sum(rows(int(m)) * int(p) for m, p in zip(pl.tr_m, pl.tr_p))
+        ops = sum(int(k) * int(p) * (1 + 2 * len(widths)) for k, p in zip(pl.tr_kept, pl.tr_p))
+        assert info.ffa_adds == adds and info.snr_ops == ops
