@@ -256,6 +256,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+// Shared -> global bulk copy (16-byte aligned ends, bytes a multiple of 16), tracked by
+// the issuing thread's bulk async-group.  The shared data must be visible to the async
+// proxy first (fence_proxy_async_smem after the barrier that completed it).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_addr(src)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until the issuing thread's bulk stores have completed (their global writes done),
+// then orders them before the thread's later generic-proxy accesses.
+__device__ __forceinline__ void bulk_store_wait() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
                                          uint64_t* bar) {
     asm volatile(
@@ -648,7 +667,14 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     }
 
     // ---- register stage: complete transforms of the nodes of <= 16 rows, A -> B
-    int in = lay.buf_b, out = lay.buf_a;
+    // Rows after the register stage sit at the 16-byte phase of their destination in
+    // global memory (hd floats past a 16-byte boundary), so that the finished sub-tree
+    // leaves by one bulk copy.  The buffers have 4 floats of slack for it.
+    float* const dst_g = kSnr ? nullptr
+                              : ((top_passes(tr.depth, tr.chunk) & 1) ? P.dst_odd : P.dst) +
+                                    tr.scratch_off + (int64_t)start * p;
+    const int hd = kSnr ? 0 : (int)((reinterpret_cast<uintptr_t>(dst_g) >> 2) & 3);
+    int in = lay.buf_b + hd, out = lay.buf_a + hd;
     {
         const int vstep = 33 - regmax;
         const int nstrip = (p + vstep - 1) / vstep;
@@ -656,7 +682,7 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
         for (int w = warp; w < nwork; w += nwarps) {
             const int q = w / nstrip, c = w - q * nstrip;
             const int nd = rnodes[q];
-            reg_strip_any(smem, a0, lay.buf_b, nd & 0xffff, nd >> 16, p, c * vstep, vstep, lane);
+            reg_strip_any(smem, a0, in, nd & 0xffff, nd >> 16, p, c * vstep, vstep, lane);
         }
         __syncthreads();
     }
@@ -677,9 +703,20 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     }
 
     if constexpr (!kSnr) {
-        float* dst = ((top_passes(tr.depth, tr.chunk) & 1) ? P.dst_odd : P.dst) + tr.scratch_off +
-                     (int64_t)start * p;
-        for (int e = tid; e < total; e += kBottomThreads) dst[e] = smem[in + e];
+        // the 16-byte-aligned interior by one bulk copy, up to 3 floats at either end by
+        // plain stores; the copy completes before the item ends (the buffers are reused)
+        const int lead = bulk_lead(dst_g);
+        const unsigned bytes = bulk_bytes(dst_g, total);
+        if (tid == 0 && bytes) {
+            fence_proxy_async_smem();
+            bulk_s2g(dst_g + lead, smem + in + lead, bytes);
+        }
+        const int tail0 = lead + (int)(bytes / 4);
+        for (int e = tid; e < lead + (total - tail0); e += kBottomThreads) {
+            const int q = e < lead ? e : tail0 + (e - lead);
+            dst_g[q] = smem[in + q];
+        }
+        if (tid == 0 && bytes) bulk_store_wait();
     } else {
         // The sub-tree is the whole transform: score rows s < kept (Sec. 2.3).
         float* S = smem + out + warp * snr_warp_floats(p, P.widths.wmax);
