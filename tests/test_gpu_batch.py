@@ -151,3 +151,25 @@ def test_batch_cuda_graph_replay(F, batch):
     torch.cuda.synchronize()
     assert torch.equal(got, S.snr)
     assert not torch.equal(got, eager[2])
+
+
+def test_batch_with_series_too_short_for_any_transform(F):
+    """A series with no 2-row transform contributes no trials; its neighbours are
+    unaffected."""
+    b = synth.batch_uneven(3, 2 ** 15, 2 ** 16, seed=31, threads=2)
+    short = np.random.default_rng(3).standard_normal(500).astype(np.float32)
+    x = np.concatenate([b.series_x(0), short, b.series_x(1)])
+    s0, s1 = b.series[0], b.series[1]
+    ser = [F.Series(0, s0.n, s0.tsamp, s0.pmin, s0.pmax, s0.bmin, s0.bmax),
+           F.Series(s0.n, 500, 64e-6, 0.5, 3.0, 240, 260),
+           F.Series(s0.n + 500, s1.n, s1.tsamp, s1.pmin, s1.pmax, s1.bmin, s1.bmax)]
+    for budget in (1 << 40, 1):
+        S = F.BatchSearcher(ser, b.widths, ws_budget=budget)
+        assert S.trial_offsets[1] == S.trial_offsets[2]   # no trials for the short series
+        S(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        S.check()
+        _compare(S.series_result(0), _oracle(b, 0))
+        ref = oracle.periodogram(b.series_x(1), s1.tsamp, s1.pmin, s1.pmax, s1.bmin, s1.bmax,
+                                 b.widths)
+        _compare(S.series_result(2), ref)
