@@ -13,6 +13,7 @@ Calls (names follow include/ffa.h and the paper, Morello et al. 2020):
   periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths)        Sec. 5.3, Fig. 4
   periodogram_host(x_host, ...)                 same, host buffers in and out
   BatchSearcher(series, widths)                 many series in one buffer, Sec. 5.7
+  SegmentSearcher(n, tsamp, segments, widths)   dynamic duty-cycle resolution, Sec. 5.6
 """
 from __future__ import annotations
 
@@ -27,7 +28,7 @@ __all__ = [
     "FFAError", "library", "build", "normalise", "downsample", "ffa_transform", "boxcar_snr",
     "PlanInfo", "periodogram_plan", "periodogram", "periodogram_host", "Searcher",
     "Series", "BatchInfo", "batch_plan", "BatchSearcher", "periodogram_batch", "shard_series",
-    "Tiles", "tile_candidates", "tune", "tune_periodogram",
+    "Tiles", "tile_candidates", "tune", "tune_periodogram", "SegmentSearcher",
     "check", "plan_cache_clear", "launch_count", "kernel_names", "profile_enable", "profile_reset",
     "profile_query",
 ]
@@ -478,6 +479,34 @@ def periodogram_batch(x, series: Sequence[Series], widths: Sequence[int],
     s = BatchSearcher(series, widths, ws_budget, device=x.device)
     per, fb, snr = s(x, stream)
     return per, fb, snr, s.trial_offsets
+
+
+class SegmentSearcher:
+    """Dynamic duty-cycle resolution (Sec. 5.6): one series searched over consecutive
+    period segments, each with its own bins range (more bins at longer periods), as one
+    batch whose series all point at the same samples.  Widths are shared: each must lie below
+    every segment's bmin.  Results of segment k: `segment_result(k)`."""
+
+    def __init__(self, n: int, tsamp: float, segments, widths: Sequence[int],
+                 ws_budget: int = DEFAULT_BATCH_BUDGET, device="cuda",
+                 tiles: Optional[Tiles] = None):
+        self.segments = [tuple(s) for s in segments]
+        series = [Series(0, int(n), float(tsamp), float(pmin), float(pmax), int(bmin), int(bmax))
+                  for pmin, pmax, bmin, bmax in self.segments]
+        self.batch = BatchSearcher(series, widths, ws_budget, device, tiles)
+        self.n = int(n)
+
+    def __call__(self, x, stream=None):
+        if x.numel() != self.n:
+            raise ValueError("series length differs from the plan")
+        return self.batch(x, stream)
+
+    def segment_result(self, k: int):
+        return self.batch.series_result(k)
+
+    @property
+    def info(self):
+        return self.batch.info
 
 
 def tile_candidates(auto: Tiles):

@@ -173,3 +173,20 @@ def test_batch_with_series_too_short_for_any_transform(F):
         ref = oracle.periodogram(b.series_x(1), s1.tsamp, s1.pmin, s1.pmax, s1.bmin, s1.bmax,
                                  b.widths)
         _compare(S.series_result(2), ref)
+
+
+def test_dynamic_duty_cycle_segments(F):
+    """One series, three period segments with more bins at longer periods (the paper's
+    dynamic duty-cycle resolution): each segment equals its own oracle periodogram."""
+    w = synth.plain_small()
+    segs = [(1.0, 2.5, 240, 260), (2.5, 6.0, 360, 390), (6.0, 10.0, 480, 520)]
+    S = F.SegmentSearcher(w.n, w.tsamp, segs, w.widths)
+    S(torch.from_numpy(w.x).cuda())
+    torch.cuda.synchronize()
+    S.batch.check()
+    for k, (pmin, pmax, bmin, bmax) in enumerate(segs):
+        ref = oracle.periodogram(w.x, w.tsamp, pmin, pmax, bmin, bmax, w.widths)
+        _compare(S.segment_result(k), ref)
+    # the injected 2.345 s pulse is the strongest trial of the segment that holds it
+    per, _, snr = (t.cpu().numpy() for t in S.segment_result(0))
+    assert abs(per[snr.max(axis=1).argmax()] - 2.345) / 2.345 < 2e-3
