@@ -14,7 +14,8 @@ Paper passages followed (sections and equations of the paper):
   * downsample ...... Sec. 5.3, App. A.4 (overlap-weighted real-factor windows)
   * ffa ............. Sec. 2.2, Eq. ffa_merge_rule (depth-first, m_h = floor(m/2))
   * trial periods ... Sec. 2.3 (P_s = p^2 tau / (p - s/(m-1)); redundant rows)
-  * boxcar S/N ...... Sec. 5.4, Sec. 3.3 (Z = x.s, unit square sum), App. A.3
+  * boxcar S/N ...... Sec. 5.4, Sec. 3.3 (Z = x.s, unit square sum), App. A.3; the
+                      zero-mean boxcar: Sec. 3.3 and 3.5 (another unit-square-sum template)
   * normalise ....... Sec. 3.1, Sec. 5.2 (zero mean, unit std from the whole series)
 """
 from __future__ import annotations
@@ -77,6 +78,11 @@ def _load():
     lib.oracle_trial_period.argtypes = [_dbl, _i64, _i64, _i64]
     lib.oracle_boxcar_snr.restype = _int
     lib.oracle_boxcar_snr.argtypes = [_p, _i64, _i64, _p, _int, _dbl, _p]
+    lib.oracle_boxcar_snr_kind.restype = _int
+    lib.oracle_boxcar_snr_kind.argtypes = [_p, _i64, _i64, _p, _int, _dbl, _int, _p]
+    lib.oracle_periodogram_kind.restype = _i64
+    lib.oracle_periodogram_kind.argtypes = [_p, _i64, _dbl, _dbl, _dbl, _int, _int, _p, _int,
+                                            _int, _p, _p, _p, _p, _i64]
     lib.oracle_normalise.restype = _int
     lib.oracle_normalise.argtypes = [_p, _i64, _p, _p, _p]
     lib.oracle_periodogram.restype = _i64
@@ -192,8 +198,9 @@ def trial_period(tau: float, p: int, m: int, s: int) -> float:
     return float(_load().oracle_trial_period(tau, p, m, s))
 
 
-def boxcar_snr(prof: np.ndarray, widths, stdnoise: float) -> np.ndarray:
-    """Boxcar S/N of every row of a profile array (Sec. 5.4), FP64, direct sums."""
+def boxcar_snr(prof: np.ndarray, widths, stdnoise: float, zero_mean: bool = False) -> np.ndarray:
+    """Boxcar S/N of every row of a profile array (Sec. 5.4), FP64, direct sums.
+    zero_mean: the zero-sum, unit-square-sum boxcar instead of the plain one."""
     lib = _load()
     P = np.ascontiguousarray(prof, dtype=np.float64)
     if P.ndim == 1:
@@ -201,7 +208,8 @@ def boxcar_snr(prof: np.ndarray, widths, stdnoise: float) -> np.ndarray:
     rows, p = P.shape
     w = np.ascontiguousarray(widths, dtype=np.int32)
     out = np.zeros((rows, len(w)), np.float64)
-    if lib.oracle_boxcar_snr(_ptr(P), rows, p, _ptr(w), len(w), stdnoise, _ptr(out)) != 0:
+    if lib.oracle_boxcar_snr_kind(_ptr(P), rows, p, _ptr(w), len(w), stdnoise,
+                                  1 if zero_mean else 0, _ptr(out)) != 0:
         raise ValueError("invalid boxcar arguments")
     return out
 
@@ -224,11 +232,13 @@ class Periodogram:
     snr: np.ndarray       # float64 [ntrials, nw]
 
 
-def periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths, select=None) -> Periodogram:
+def periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths, select=None,
+                zero_mean: bool = False) -> Periodogram:
     """Sec. 5.3 periodogram of a float32 series, FP64 throughout.
 
     ``select``: optional boolean mask over the plan's transforms; only those are
     computed and their trials are returned compactly in plan order.
+    ``zero_mean``: score with the zero-mean boxcar (see boxcar_snr).
     """
     lib = _load()
     x = np.ascontiguousarray(x, dtype=np.float32)
@@ -246,8 +256,9 @@ def periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths, select=None) -> Period
     periods = np.zeros(cap, np.float64)
     fb = np.zeros(cap, np.int32)
     snr = np.zeros((cap, len(w)), np.float64)
-    got = lib.oracle_periodogram(_ptr(x), len(x), tsamp, pmin, pmax, bmin, bmax, _ptr(w),
-                                 len(w), sel_ptr, _ptr(periods), _ptr(fb), _ptr(snr), cap)
+    got = lib.oracle_periodogram_kind(_ptr(x), len(x), tsamp, pmin, pmax, bmin, bmax, _ptr(w),
+                                      len(w), 1 if zero_mean else 0, sel_ptr, _ptr(periods),
+                                      _ptr(fb), _ptr(snr), cap)
     if got != cap:
         raise ValueError("oracle periodogram failed (%d)" % got)
     return Periodogram(periods, fb, snr)

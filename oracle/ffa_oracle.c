@@ -247,23 +247,46 @@ double oracle_trial_period(double tau, int64_t p, int64_t m, int64_t s)
 int oracle_boxcar_snr(const double* prof, int64_t rows, int64_t p, const int* widths,
                       int nw, double stdnoise, double* snr)
 {
-    int64_t r, k;
+    return oracle_boxcar_snr_kind(prof, rows, p, widths, nw, stdnoise, 0, snr);
+}
+
+/* kind 0: the plain boxcar (height 1/sqrt(w) on w bins, 0 elsewhere; Sec. 5.4).
+ * kind 1: the zero-mean boxcar, another template with unit square sum, so that its
+ *   Z-statistic (Sec. 3.3) is again N(0, 1) under pure noise (Sec. 3.5 leaves the
+ *   choice of matched filters open): value a on the w on-pulse bins and b on the p - w
+ *   others, with zero sum and unit square sum, i.e. a = sqrt((p - w) / (w p)),
+ *   b = -sqrt(w / (p (p - w))).  The statistic at phase k is the template's dot product
+ *   with the profile, a * (on-pulse sum) + b * (off-pulse sum), over the per-bin noise
+ *   std; a constant added to the profile does not change it.  Needs w < p.
+ * Both take the maximum over the p phases; sums are direct (no prefix sums). */
+int oracle_boxcar_snr_kind(const double* prof, int64_t rows, int64_t p, const int* widths,
+                           int nw, double stdnoise, int kind, double* snr)
+{
+    int64_t r, k, x;
     int iw;
-    if (rows < 0 || p < 1 || nw < 1 || !(stdnoise > 0.0)) return -1;
+    if (rows < 0 || p < 1 || nw < 1 || !(stdnoise > 0.0) || kind < 0 || kind > 1) return -1;
     for (iw = 0; iw < nw; ++iw)
-        if (widths[iw] < 1 || widths[iw] > p) return -1;
+        if (widths[iw] < 1 || widths[iw] > p || (kind == 1 && widths[iw] >= p)) return -1;
     for (r = 0; r < rows; ++r) {
         const double* P = prof + r * p;
+        double total = 0.0;
+        for (x = 0; x < p; ++x) total += P[x];
         for (iw = 0; iw < nw; ++iw) {
             int w = widths[iw];
             double best = -INFINITY;
-            for (k = 0; k < p; ++k) {
-                double c = 0.0;
-                int q;
-                for (q = 0; q < w; ++q) c += P[(k + q) % p];
-                if (c > best) best = c;
+            double a = 1.0 / sqrt((double)w), b = 0.0;
+            if (kind == 1) {
+                a = sqrt((double)(p - w) / ((double)w * (double)p));
+                b = -sqrt((double)w / ((double)p * (double)(p - w)));
             }
-            snr[r * nw + iw] = best / (stdnoise * sqrt((double)w));
+            for (k = 0; k < p; ++k) {
+                double on = 0.0, z;
+                int q;
+                for (q = 0; q < w; ++q) on += P[(k + q) % p];
+                z = a * on + b * (total - on);
+                if (z > best) best = z;
+            }
+            snr[r * nw + iw] = best / stdnoise;
         }
     }
     return 0;
@@ -309,6 +332,15 @@ int64_t oracle_periodogram(const float* x, int64_t n, double tsamp, double pmin,
                            const unsigned char* select, double* periods, int* foldbins,
                            double* snr, int64_t cap)
 {
+    return oracle_periodogram_kind(x, n, tsamp, pmin, pmax, bmin, bmax, widths, nw, 0,
+                                   select, periods, foldbins, snr, cap);
+}
+
+int64_t oracle_periodogram_kind(const float* x, int64_t n, double tsamp, double pmin,
+                                double pmax, int bmin, int bmax, const int* widths, int nw,
+                                int kind, const unsigned char* select, double* periods,
+                                int* foldbins, double* snr, int64_t cap)
+{
     int k, p, t = 0, iw;
     int64_t written = 0;
     if (!plan_args_ok(n, tsamp, pmin, pmax, bmin, bmax) || nw < 1) return -1;
@@ -337,7 +369,8 @@ int64_t oracle_periodogram(const float* x, int64_t n, double tsamp, double pmin,
             fold = (double*)malloc((size_t)(m * p) * sizeof(double));
             s_n = (double*)malloc((size_t)(kept * nw) * sizeof(double));
             oracle_ffa_f64(ds, m, p, fold);
-            oracle_boxcar_snr(fold, kept, p, widths, nw, sqrt((double)m * var_f), s_n);
+            oracle_boxcar_snr_kind(fold, kept, p, widths, nw, sqrt((double)m * var_f), kind,
+                                   s_n);
             for (s = 0; s < kept; ++s) {
                 periods[written + s] = oracle_trial_period(tau_k, p, m, s);
                 foldbins[written + s] = p;

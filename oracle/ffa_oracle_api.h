@@ -24,6 +24,8 @@ double oracle_trial_period(double tau, int64_t p, int64_t m, int64_t s);
 
 int oracle_boxcar_snr(const double* prof, int64_t rows, int64_t p, const int* widths,
                       int nw, double stdnoise, double* snr);
+int oracle_boxcar_snr_kind(const double* prof, int64_t rows, int64_t p, const int* widths,
+                           int nw, double stdnoise, int kind, double* snr);
 
 int oracle_normalise(const float* x, int64_t n, double* mean, double* stdev, double* out);
 
@@ -31,4 +33,8 @@ int64_t oracle_periodogram(const float* x, int64_t n, double tsamp, double pmin,
                            double pmax, int bmin, int bmax, const int* widths, int nw,
                            const unsigned char* select, double* periods, int* foldbins,
                            double* snr, int64_t cap);
+int64_t oracle_periodogram_kind(const float* x, int64_t n, double tsamp, double pmin,
+                                double pmax, int bmin, int bmax, const int* widths, int nw,
+                                int kind, const unsigned char* select, double* periods,
+                                int* foldbins, double* snr, int64_t cap);
 #endif

@@ -1,7 +1,10 @@
 """Pins of the oracle's boxcar S/N (Sec. 3.3, Sec. 5.4, App. A.3): it equals the
 Z-statistic x.s of an explicit unit-square-sum template, the prefix-sum identity of
 Sec. 5.4, the closed-form boxcar efficiency on a Gaussian pulse (0.943 / 0.930 /
-0.901), N(0, 1) under pure noise, and the Cauchy-Schwarz bound."""
+0.901), N(0, 1) under pure noise, and the Cauchy-Schwarz bound.  The zero-mean boxcar
+(Sec. 3.3 and 3.5: another unit-square-sum template) equals an FFT circular correlation
+with the explicit template vector, ignores a constant offset, and is N(0, 1) at a fixed
+phase under pure noise."""
 import math
 
 import numpy as np
@@ -142,3 +145,52 @@ def test_invalid_arguments():
         oracle.boxcar_snr(np.zeros((2, 5)), [6], 1.0)
     with pytest.raises(ValueError):
         oracle.boxcar_snr(np.zeros((2, 5)), [1], 0.0)
+
+
+# ------------------------------------------------------------ zero-mean boxcar template
+def _zm_template(p, w):
+    """The zero-mean boxcar as an explicit vector: equal values on w bins, equal values
+    on the rest, zero sum and unit square sum (built by projection, not by formula)."""
+    t = np.zeros(p)
+    t[:w] = 1.0
+    t -= t.mean()
+    return t / np.sqrt(np.sum(t * t))
+
+
+@pytest.mark.parametrize("p,widths", [(7, (1, 2, 3, 6)), (40, (1, 3, 9, 20)), (251, (1, 13, 63))])
+def test_zero_mean_boxcar_is_a_circular_correlation(p, widths):
+    """Z at every phase is the circular correlation of the profile with the explicit
+    template (computed here by FFT), maximised over phase."""
+    rng = synth.rng(p)
+    prof = rng.standard_normal((5, p)) + 3.0
+    got = oracle.boxcar_snr(prof, widths, 1.7, zero_mean=True)
+    for iw, w in enumerate(widths):
+        t = _zm_template(p, w)
+        corr = np.real(np.fft.ifft(np.conj(np.fft.fft(t))[None, :] * np.fft.fft(prof, axis=1),
+                                   axis=1))
+        np.testing.assert_allclose(got[:, iw], corr.max(axis=1) / 1.7, rtol=1e-12, atol=1e-12)
+
+
+def test_zero_mean_boxcar_ignores_a_constant_and_is_unit_normal():
+    rng = synth.rng(5)
+    prof = rng.standard_normal((2000, 64))
+    a = oracle.boxcar_snr(prof, (1, 4, 16), 1.0, zero_mean=True)
+    b = oracle.boxcar_snr(prof + 123.0, (1, 4, 16), 1.0, zero_mean=True)
+    np.testing.assert_allclose(a, b, atol=1e-9)
+    # the statistic at one fixed phase is N(0, 1) under pure noise (unit square sum)
+    t = _zm_template(64, 4)
+    z = prof @ t
+    assert abs(z.mean()) < 3 / np.sqrt(len(z)) and abs(z.std() - 1.0) < 0.05
+
+
+def test_zero_mean_boxcar_rejects_full_width():
+    with pytest.raises(ValueError):
+        oracle.boxcar_snr(np.zeros((1, 8)), (8,), 1.0, zero_mean=True)
+
+
+def test_zero_mean_periodogram_recovers_the_pulse():
+    w = synth.plain_small()
+    ref = oracle.periodogram(w.x, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths,
+                             zero_mean=True)
+    best = ref.snr.max(axis=1)
+    assert abs(ref.periods[best.argmax()] - 2.345) / 2.345 < 2e-3
