@@ -115,6 +115,13 @@ ffa_status ffa_transform_noalloc(const float* d_in, int32_t rows, int32_t cols, 
 ffa_status ffa_boxcar_snr(const float* d_prof, int32_t rows, int32_t cols,
                           const int32_t* h_widths, int32_t nw, double stdnoise,
                           float* d_snr, void* stream);
+/* Same with a choice of template: boxcar = FFA_BOXCAR_PLAIN (as above) or
+ * FFA_BOXCAR_ZERO_MEAN (see ffa_plan_opts below: value a on the w bins and b on the
+ * others, zero sum, unit square sum; the score is max_k (a C_k + b (T - C_k)) / stdnoise
+ * with T the profile's sum; widths must be below cols). */
+ffa_status ffa_boxcar_snr_template(const float* d_prof, int32_t rows, int32_t cols,
+                                   const int32_t* h_widths, int32_t nw, double stdnoise,
+                                   int32_t boxcar, float* d_snr, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Normalisation of a whole series (paper Sec. 3.1 and Sec. 5.2): the noise mean and
@@ -141,21 +148,31 @@ ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out
  *   (Sec. 2.3); P_s = tau_k p^2 / (p - s / (m - 1)).
  * Host only.  Widths: 1 <= w < bmin, strictly increasing, at most 64.
  * ---------------------------------------------------------------------------- */
-/* Tile shape of a plan: the work-item sizes of the persistent FFA launch.  Any field 0
- * means "the largest that fits shared memory" (the default of every call without
- * tiles).  Every tile shape gives the same results, bit for bit: the merges and the S/N
- * of each row do not depend on how rows are grouped.  The Python binding's `tune`
- * times a few shapes on the caller's data and keeps the fastest.
+/* Options of a plan.  Zero-initialised options are the default of every call without
+ * options.
+ * Tile shape: the work-item sizes of the persistent FFA launch; 0 means "the largest
+ * that fits shared memory".  Every tile shape gives the same results, bit for bit: the
+ * merges and the S/N of each row do not depend on how rows are grouped.  The Python
+ * binding's `tune` times a few shapes on the caller's data and keeps the fastest.
  *   subtree_rows  rows of a shared-memory sub-tree item, 2..1024
  *   top_levels    merge levels per gathered top pass, 1..3
  *   top_rows      output rows per top-pass item, 1..128
- * Out-of-range values give FFA_ERR_ARG.  No counterpart in the paper: its CPU code
- * recurses depth first and has no tiles. */
-typedef struct ffa_tiles {
+ * Boxcar template of the S/N (both with unit square sum, so the S/N is the
+ * Z-statistic of Sec. 3.3; Sec. 3.5 leaves the choice of matched filters open):
+ *   FFA_BOXCAR_PLAIN      height 1/sqrt(w) on w bins, 0 elsewhere (Sec. 5.4)
+ *   FFA_BOXCAR_ZERO_MEAN  value a on w bins and b on the other p - w, zero sum:
+ *                         a = sqrt((p-w)/(w p)), b = -sqrt(w/(p (p-w))); a constant
+ *                         added to a profile does not change its S/N
+ * Out-of-range values give FFA_ERR_ARG.  The tiles have no counterpart in the paper (its
+ * CPU code recurses depth first). */
+enum { FFA_BOXCAR_PLAIN = 0, FFA_BOXCAR_ZERO_MEAN = 1 };
+
+typedef struct ffa_plan_opts {
     int32_t subtree_rows;
     int32_t top_levels;
     int32_t top_rows;
-} ffa_tiles;
+    int32_t boxcar;
+} ffa_plan_opts;
 
 typedef struct ffa_plan_info {
     int64_t ntrials;                  /* rows of the periodogram                     */
@@ -167,8 +184,9 @@ typedef struct ffa_plan_info {
     int64_t folded_samples;           /* sum over transforms of m * p                */
     size_t workspace_bytes;           /* for ffa_periodogram                         */
     size_t host_workspace_bytes;      /* for ffa_periodogram_host (includes I/O)     */
-    ffa_tiles tiles;                  /* tiles in effect: largest sub-tree, levels per
-                                         top pass and rows per top item of the plan  */
+    ffa_plan_opts opts;               /* options in effect: largest sub-tree, levels per
+                                         top pass and rows per top item of the plan,
+                                         boxcar template                             */
     double ffa_adds;                  /* FP32 adds of all merges (one per element of
                                          every merged row)                           */
     double snr_ops;                   /* FP32 operations of the S/N: per kept profile
@@ -178,10 +196,10 @@ typedef struct ffa_plan_info {
 ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pmax,
                                 int32_t bmin, int32_t bmax, const int32_t* h_widths,
                                 int32_t nw, ffa_plan_info* out);
-/* Same with a tile shape (NULL = automatic). */
-ffa_status ffa_periodogram_plan_tiles(int64_t n, double tsamp, double pmin, double pmax,
-                                      int32_t bmin, int32_t bmax, const int32_t* h_widths,
-                                      int32_t nw, const ffa_tiles* tiles, ffa_plan_info* out);
+/* Same with plan options (NULL = defaults). */
+ffa_status ffa_periodogram_plan_opts(int64_t n, double tsamp, double pmin, double pmax,
+                                     int32_t bmin, int32_t bmax, const int32_t* h_widths,
+                                     int32_t nw, const ffa_plan_opts* opts, ffa_plan_info* out);
 
 /* ------------------------------------------------------------------------------
  * FFA periodogram (paper Sec. 5.3, Fig. 4; Sec. 5.5 for the two-dimensional output).
@@ -203,18 +221,18 @@ ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double t
                            const int32_t* h_widths, int32_t nw, double* d_periods,
                            int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
                            void* d_ws, size_t ws_bytes, void* stream);
-/* Same with a tile shape (NULL = automatic); the workspace is the one that
- * ffa_periodogram_plan_tiles reports for the same tiles.
+/* Same with plan options (NULL = defaults); the workspace is the one that
+ * ffa_periodogram_plan_opts reports for the same options.
  * All periodogram calls: the first call of a host thread on a device also creates a
  * helper stream and two events of that thread (the top-pass records are made on it,
  * concurrently with the prefix sums and downsampling, and joined back into `stream`).
  * Make that first call outside any stream capture; later calls capture as one graph
  * with a fork and a join. */
-ffa_status ffa_periodogram_tiles(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp,
-                                 double pmin, double pmax, int32_t bmin, int32_t bmax,
-                                 const int32_t* h_widths, int32_t nw, const ffa_tiles* tiles,
-                                 double* d_periods, int32_t* d_foldbins, float* d_snr,
-                                 int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream);
+ffa_status ffa_periodogram_opts(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp,
+                                double pmin, double pmax, int32_t bmin, int32_t bmax,
+                                const int32_t* h_widths, int32_t nw, const ffa_plan_opts* opts,
+                                double* d_periods, int32_t* d_foldbins, float* d_snr,
+                                int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Batched periodograms (many series, e.g. the dedispersed DM trials of an observation,
@@ -253,17 +271,17 @@ ffa_status ffa_periodogram_batch(const void* d_x, ffa_dtype dtype, const ffa_ser
                                  size_t ws_budget, double* d_periods, int32_t* d_foldbins,
                                  float* d_snr, int64_t ntrials_cap, void* d_ws, size_t ws_bytes,
                                  void* stream);
-/* Same two calls with a tile shape for every chunk (NULL = automatic). */
-ffa_status ffa_batch_plan_tiles(const ffa_series* h_series, int32_t nseries,
-                                const int32_t* h_widths, int32_t nw, size_t ws_budget,
-                                const ffa_tiles* tiles, int64_t* h_trial_offsets,
-                                ffa_batch_info* out);
-ffa_status ffa_periodogram_batch_tiles(const void* d_x, ffa_dtype dtype,
-                                       const ffa_series* h_series, int32_t nseries,
-                                       const int32_t* h_widths, int32_t nw, size_t ws_budget,
-                                       const ffa_tiles* tiles, double* d_periods,
-                                       int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
-                                       void* d_ws, size_t ws_bytes, void* stream);
+/* Same two calls with plan options for every chunk (NULL = defaults). */
+ffa_status ffa_batch_plan_opts(const ffa_series* h_series, int32_t nseries,
+                               const int32_t* h_widths, int32_t nw, size_t ws_budget,
+                               const ffa_plan_opts* opts, int64_t* h_trial_offsets,
+                               ffa_batch_info* out);
+ffa_status ffa_periodogram_batch_opts(const void* d_x, ffa_dtype dtype,
+                                      const ffa_series* h_series, int32_t nseries,
+                                      const int32_t* h_widths, int32_t nw, size_t ws_budget,
+                                      const ffa_plan_opts* opts, double* d_periods,
+                                      int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
+                                      void* d_ws, size_t ws_bytes, void* stream);
 
 /* Plans (single-series and batch) are built on first use and cached by their parameters
  * for the life of the process: their page-locked tables are what the table copy of

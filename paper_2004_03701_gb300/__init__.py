@@ -47,9 +47,9 @@ class FFAError(RuntimeError):
         self.status = status
 
 
-class _Tiles(ctypes.Structure):
+class _PlanOpts(ctypes.Structure):
     _fields_ = [("subtree_rows", ctypes.c_int32), ("top_levels", ctypes.c_int32),
-                ("top_rows", ctypes.c_int32)]
+                ("top_rows", ctypes.c_int32), ("boxcar", ctypes.c_int32)]
 
 
 class _PlanInfo(ctypes.Structure):
@@ -57,7 +57,7 @@ class _PlanInfo(ctypes.Structure):
                 ("ntransforms", ctypes.c_int32), ("nwidths", ctypes.c_int32),
                 ("max_rows", ctypes.c_int32), ("downsampled_samples", ctypes.c_int64),
                 ("folded_samples", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
-                ("host_workspace_bytes", ctypes.c_size_t), ("tiles", _Tiles),
+                ("host_workspace_bytes", ctypes.c_size_t), ("opts", _PlanOpts),
                 ("ffa_adds", ctypes.c_double), ("snr_ops", ctypes.c_double)]
 
 
@@ -101,13 +101,14 @@ def library() -> ctypes.CDLL:
     L.ffa_boxcar_snr.argtypes = [vp, i32, i32, vp, i32, dbl, vp, vp]
     L.ffa_periodogram_plan.argtypes = [i64, dbl, dbl, dbl, i32, i32, vp, i32,
                                        ctypes.POINTER(_PlanInfo)]
-    L.ffa_periodogram_plan_tiles.argtypes = [i64, dbl, dbl, dbl, i32, i32, vp, i32, vp,
-                                             ctypes.POINTER(_PlanInfo)]
-    L.ffa_periodogram_tiles.argtypes = [vp, i32, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp,
-                                        vp, vp, i64, vp, sz, vp]
-    L.ffa_batch_plan_tiles.argtypes = [vp, i32, vp, i32, sz, vp, vp, ctypes.POINTER(_BatchInfo)]
-    L.ffa_periodogram_batch_tiles.argtypes = [vp, i32, vp, i32, vp, i32, sz, vp, vp, vp, vp,
-                                              i64, vp, sz, vp]
+    L.ffa_periodogram_plan_opts.argtypes = [i64, dbl, dbl, dbl, i32, i32, vp, i32, vp,
+                                            ctypes.POINTER(_PlanInfo)]
+    L.ffa_periodogram_opts.argtypes = [vp, i32, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp,
+                                       vp, vp, i64, vp, sz, vp]
+    L.ffa_batch_plan_opts.argtypes = [vp, i32, vp, i32, sz, vp, vp, ctypes.POINTER(_BatchInfo)]
+    L.ffa_periodogram_batch_opts.argtypes = [vp, i32, vp, i32, vp, i32, sz, vp, vp, vp, vp,
+                                             i64, vp, sz, vp]
+    L.ffa_boxcar_snr_template.argtypes = [vp, i32, i32, vp, i32, dbl, i32, vp, vp]
     L.ffa_periodogram.argtypes = [vp, i32, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
                                   i64, vp, sz, vp]
     L.ffa_periodogram_host.argtypes = [vp, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
@@ -129,8 +130,9 @@ def library() -> ctypes.CDLL:
               "ffa_transform", "ffa_boxcar_snr", "ffa_periodogram_plan", "ffa_periodogram",
               "ffa_periodogram_host", "ffa_check", "ffa_profile_enable", "ffa_profile_reset",
               "ffa_normalise_workspace", "ffa_normalise", "ffa_batch_plan",
-              "ffa_periodogram_batch", "ffa_plan_cache_clear", "ffa_periodogram_plan_tiles",
-              "ffa_periodogram_tiles", "ffa_batch_plan_tiles", "ffa_periodogram_batch_tiles",
+              "ffa_periodogram_batch", "ffa_plan_cache_clear", "ffa_periodogram_plan_opts",
+              "ffa_periodogram_opts", "ffa_batch_plan_opts", "ffa_periodogram_batch_opts",
+              "ffa_boxcar_snr_template",
               "ffa_profile_query"):
         getattr(L, f).restype = i32
     _lib = L
@@ -237,8 +239,10 @@ def ffa_transform(block, stream=None):
     return out
 
 
-def boxcar_snr(prof, widths: Sequence[int], stdnoise: float, stream=None):
-    """Boxcar S/N (rows, nw) of a (rows, cols) float32 CUDA profile array (Sec. 5.4)."""
+def boxcar_snr(prof, widths: Sequence[int], stdnoise: float, stream=None,
+               zero_mean: bool = False):
+    """Boxcar S/N (rows, nw) of a (rows, cols) float32 CUDA profile array (Sec. 5.4);
+    zero_mean: the zero-sum, unit-square-sum boxcar (widths below cols)."""
     torch = _torch()
     _dev_tensor(prof, "prof")
     if prof.dtype != torch.float32 or prof.dim() != 2:
@@ -246,8 +250,10 @@ def boxcar_snr(prof, widths: Sequence[int], stdnoise: float, stream=None):
     w = _widths_array(widths)
     rows, cols = prof.shape
     out = torch.empty((rows, len(w)), dtype=torch.float32, device=prof.device)
-    _check(library().ffa_boxcar_snr(_vp(prof), rows, cols, _vp(w), len(w), float(stdnoise),
-                                    _vp(out), _stream_handle(stream)))
+    _check(library().ffa_boxcar_snr_template(_vp(prof), rows, cols, _vp(w), len(w),
+                                             float(stdnoise),
+                                             BOXCAR_ZERO_MEAN if zero_mean else BOXCAR_PLAIN,
+                                             _vp(out), _stream_handle(stream)))
     return out
 
 
@@ -275,22 +281,29 @@ class Tiles:
     top_rows: int = 0
 
 
-def _tiles_arg(tiles: Optional[Tiles]):
-    if tiles is None:
+BOXCAR_PLAIN, BOXCAR_ZERO_MEAN = 0, 1
+
+
+def _tiles_arg(tiles: Optional[Tiles], zero_mean: bool = False):
+    """(struct kept alive, pointer) of plan options; NULL for all defaults."""
+    if tiles is None and not zero_mean:
         return None, ctypes.c_void_p(None)
-    t = _Tiles(int(tiles.subtree_rows), int(tiles.top_levels), int(tiles.top_rows))
-    return t, ctypes.cast(ctypes.byref(t), ctypes.c_void_p)
+    t = tiles or Tiles()
+    o = _PlanOpts(int(t.subtree_rows), int(t.top_levels), int(t.top_rows),
+                  BOXCAR_ZERO_MEAN if zero_mean else BOXCAR_PLAIN)
+    return o, ctypes.cast(ctypes.byref(o), ctypes.c_void_p)
 
 
 def periodogram_plan(n: int, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,
-                     widths: Sequence[int], tiles: Optional[Tiles] = None) -> PlanInfo:
+                     widths: Sequence[int], tiles: Optional[Tiles] = None,
+                     zero_mean: bool = False) -> PlanInfo:
     w = _widths_array(widths)
     info = _PlanInfo()
-    keep, tp = _tiles_arg(tiles)
-    _check(library().ffa_periodogram_plan_tiles(n, tsamp, pmin, pmax, bmin, bmax, _vp(w), len(w),
-                                                tp, ctypes.byref(info)))
+    keep, tp = _tiles_arg(tiles, zero_mean)
+    _check(library().ffa_periodogram_plan_opts(n, tsamp, pmin, pmax, bmin, bmax, _vp(w), len(w),
+                                               tp, ctypes.byref(info)))
     vals = [getattr(info, f) for f, _ in _PlanInfo._fields_[:-3]]
-    t = info.tiles
+    t = info.opts
     return PlanInfo(*vals, Tiles(t.subtree_rows, t.top_levels, t.top_rows), info.ffa_adds,
                     info.snr_ops)
 
@@ -310,13 +323,14 @@ class Searcher:
     """Holds the workspace and outputs of one search configuration for repeated calls."""
 
     def __init__(self, n, tsamp, pmin, pmax, bmin, bmax, widths, device="cuda",
-                 tiles: Optional[Tiles] = None):
+                 tiles: Optional[Tiles] = None, zero_mean: bool = False):
         torch = _torch()
         self.args = (int(n), float(tsamp), float(pmin), float(pmax), int(bmin), int(bmax))
         self.widths = _widths_array(widths)
         self.tiles = tiles
-        self._tiles_keep, self._tiles_ptr = _tiles_arg(tiles)
-        self.info = periodogram_plan(*self.args, self.widths, tiles)
+        self.zero_mean = bool(zero_mean)
+        self._tiles_keep, self._tiles_ptr = _tiles_arg(tiles, zero_mean)
+        self.info = periodogram_plan(*self.args, self.widths, tiles, zero_mean)
         T, nw = self.info.ntrials, len(self.widths)
         self.device = torch.device(device)
         self.ws = _workspace(self.info.workspace_bytes, self.device)
@@ -332,7 +346,7 @@ class Searcher:
         if x.numel() != self.args[0]:
             raise ValueError("series length differs from the plan")
         n, tsamp, pmin, pmax, bmin, bmax = self.args
-        _check(library().ffa_periodogram_tiles(
+        _check(library().ffa_periodogram_opts(
             _vp(x), _dtype_code(x), n, tsamp, pmin, pmax, bmin, bmax, _vp(self.widths),
             len(self.widths), self._tiles_ptr, _vp(self._per), _vp(self._fb), _vp(self._snr),
             self.periods.numel(), _vp(self.ws), self.ws.numel(), _stream_handle(stream)))
@@ -340,7 +354,9 @@ class Searcher:
 
     def run_host(self, x_host, periods_h, foldbins_h, snr_h, stream=None):
         """End to end from host memory: copies in, searches, copies out, synchronises
-        (with the automatic tile shape)."""
+        (with the default plan options)."""
+        if self.zero_mean:
+            raise ValueError("the host-buffer call uses the plain boxcar")
         if self._host_ws is None:
             info0 = self.info if self.tiles is None else periodogram_plan(*self.args, self.widths)
             self._host_ws = _workspace(info0.host_workspace_bytes, self.device)
@@ -356,12 +372,13 @@ class Searcher:
 
 
 def periodogram(x, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,
-                widths: Sequence[int], stream=None):
+                widths: Sequence[int], stream=None, zero_mean: bool = False):
     """FFA periodogram of a normalised CUDA series (float32, float16 or int8 as q/16).
 
     Returns (periods float64 [T], foldbins int32 [T], snr float32 [T, nw]) on the device.
     """
-    s = Searcher(x.numel(), tsamp, pmin, pmax, bmin, bmax, widths, device=x.device)
+    s = Searcher(x.numel(), tsamp, pmin, pmax, bmin, bmax, widths, device=x.device,
+                 zero_mean=zero_mean)
     return s(x, stream)
 
 
@@ -412,14 +429,15 @@ DEFAULT_BATCH_BUDGET = 1 << 30
 
 
 def batch_plan(series: Sequence[Series], widths: Sequence[int],
-               ws_budget: int = DEFAULT_BATCH_BUDGET, tiles: Optional[Tiles] = None):
+               ws_budget: int = DEFAULT_BATCH_BUDGET, tiles: Optional[Tiles] = None,
+               zero_mean: bool = False):
     """(BatchInfo, trial offsets int64 [len(series) + 1]) of a batch search."""
     w = _widths_array(widths)
     arr = _series_array(series)
     offs = np.zeros(len(series) + 1, np.int64)
     info = _BatchInfo()
-    keep, tp = _tiles_arg(tiles)
-    _check(library().ffa_batch_plan_tiles(ctypes.cast(arr, ctypes.c_void_p), len(series), _vp(w),
+    keep, tp = _tiles_arg(tiles, zero_mean)
+    _check(library().ffa_batch_plan_opts(ctypes.cast(arr, ctypes.c_void_p), len(series), _vp(w),
                                           len(w), int(ws_budget), tp, _vp(offs),
                                           ctypes.byref(info)))
     return BatchInfo(*(getattr(info, f) for f, _ in _BatchInfo._fields_)), offs
@@ -435,16 +453,16 @@ class BatchSearcher:
 
     def __init__(self, series: Sequence[Series], widths: Sequence[int],
                  ws_budget: int = DEFAULT_BATCH_BUDGET, device="cuda",
-                 tiles: Optional[Tiles] = None):
+                 tiles: Optional[Tiles] = None, zero_mean: bool = False):
         torch = _torch()
         self.series = list(series)
         self.widths = _widths_array(widths)
         self.ws_budget = int(ws_budget)
         self.tiles = tiles
-        self._tiles_keep, self._tiles_ptr = _tiles_arg(tiles)
+        self._tiles_keep, self._tiles_ptr = _tiles_arg(tiles, zero_mean)
         self._arr = _series_array(self.series)
         self.info, self.trial_offsets = batch_plan(self.series, self.widths, self.ws_budget,
-                                                   tiles)
+                                                   tiles, zero_mean)
         self.span = max(s.offset + s.n for s in self.series)
         T, nw = self.info.ntrials, len(self.widths)
         self.device = torch.device(device)
@@ -458,7 +476,7 @@ class BatchSearcher:
         _dev_tensor(x, "x")
         if x.numel() < self.span:
             raise ValueError("batch buffer is shorter than the series span")
-        _check(library().ffa_periodogram_batch_tiles(
+        _check(library().ffa_periodogram_batch_opts(
             _vp(x), _dtype_code(x), ctypes.cast(self._arr, ctypes.c_void_p), len(self.series),
             _vp(self.widths), len(self.widths), self.ws_budget, self._tiles_ptr, _vp(self._per),
             _vp(self._fb), _vp(self._snr), self.periods.numel(), _vp(self.ws), self.ws.numel(),
@@ -489,11 +507,11 @@ class SegmentSearcher:
 
     def __init__(self, n: int, tsamp: float, segments, widths: Sequence[int],
                  ws_budget: int = DEFAULT_BATCH_BUDGET, device="cuda",
-                 tiles: Optional[Tiles] = None):
+                 tiles: Optional[Tiles] = None, zero_mean: bool = False):
         self.segments = [tuple(s) for s in segments]
         series = [Series(0, int(n), float(tsamp), float(pmin), float(pmax), int(bmin), int(bmax))
                   for pmin, pmax, bmin, bmax in self.segments]
-        self.batch = BatchSearcher(series, widths, ws_budget, device, tiles)
+        self.batch = BatchSearcher(series, widths, ws_budget, device, tiles, zero_mean)
         self.n = int(n)
 
     def __call__(self, x, stream=None):

@@ -111,16 +111,17 @@ struct SeriesSpec {
     }
 };
 
-// Tile shape of a plan (0 = the largest that fits shared memory).
+// Options of a plan: tile shape (0 = the largest that fits shared memory) and the boxcar
+// template of the S/N.
 struct Tiles {
-    int subtree_rows = 0, top_levels = 0, top_rows = 0;
+    int subtree_rows = 0, top_levels = 0, top_rows = 0, boxcar = 0;
     bool operator<(const Tiles& o) const {
-        return std::tie(subtree_rows, top_levels, top_rows) <
-               std::tie(o.subtree_rows, o.top_levels, o.top_rows);
+        return std::tie(subtree_rows, top_levels, top_rows, boxcar) <
+               std::tie(o.subtree_rows, o.top_levels, o.top_rows, o.boxcar);
     }
 };
 
-ffa_status read_tiles(const ffa_tiles* t, Tiles* out) {
+ffa_status read_tiles(const ffa_plan_opts* t, Tiles* out) {
     *out = Tiles{};
     if (!t) return FFA_OK;
     if (t->subtree_rows < 0 || t->subtree_rows == 1 || t->subtree_rows > kBottomMaxRows)
@@ -129,7 +130,9 @@ ffa_status read_tiles(const ffa_tiles* t, Tiles* out) {
         return fail(FFA_ERR_ARG, "top_levels must be 0..%d", kTopMaxLevels);
     if (t->top_rows < 0 || t->top_rows > kTopMaxRows)
         return fail(FFA_ERR_ARG, "top_rows must be 0..%d", kTopMaxRows);
-    *out = Tiles{t->subtree_rows, t->top_levels, t->top_rows};
+    if (t->boxcar != FFA_BOXCAR_PLAIN && t->boxcar != FFA_BOXCAR_ZERO_MEAN)
+        return fail(FFA_ERR_ARG, "boxcar must be FFA_BOXCAR_PLAIN or FFA_BOXCAR_ZERO_MEAN");
+    *out = Tiles{t->subtree_rows, t->top_levels, t->top_rows, t->boxcar};
     return FFA_OK;
 }
 
@@ -210,7 +213,8 @@ int top_chunk(int p, int wmax, bool score) {
     return 0;
 }
 
-ffa_status make_widths(const int32_t* h_widths, int32_t nw, int limit, Widths* W) {
+ffa_status make_widths(const int32_t* h_widths, int32_t nw, int limit, Widths* W,
+                       int boxcar = FFA_BOXCAR_PLAIN) {
     if (!h_widths) return fail(FFA_ERR_ARG, "widths is null");
     if (nw < 1 || nw > kMaxWidths) return fail(FFA_ERR_ARG, "nw must be in [1, %d]", kMaxWidths);
     std::memset(W, 0, sizeof(*W));
@@ -223,6 +227,7 @@ ffa_status make_widths(const int32_t* h_widths, int32_t nw, int limit, Widths* W
         W->inv_sqrt_w[i] = (float)(1.0 / std::sqrt((double)w));
         if (w > W->wmax) W->wmax = w;
     }
+    W->boxcar = boxcar;
     return FFA_OK;
 }
 
@@ -528,7 +533,8 @@ ffa_status make_plan_series(const std::vector<SeriesSpec>& series, const int32_t
         span = std::max(span, s.x_off + s.n);
     }
     Widths W;
-    ffa_status st = make_widths(h_widths, nw, bmin_all - 1, &W);  // below the smallest base period
+    ffa_status st = make_widths(h_widths, nw, bmin_all - 1, &W,  // below the smallest base period
+                                tiles.boxcar);
     if (st != FFA_OK) return st;
     std::unique_ptr<Plan> pl;
     for (int cap = tiles.subtree_rows ? tiles.subtree_rows : kBottomMaxRows;;) {
@@ -1008,12 +1014,22 @@ ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d
 ffa_status ffa_boxcar_snr(const float* d_prof, int32_t rows, int32_t cols,
                           const int32_t* h_widths, int32_t nw, double stdnoise, float* d_snr,
                           void* stream) {
+    return ffa_boxcar_snr_template(d_prof, rows, cols, h_widths, nw, stdnoise, FFA_BOXCAR_PLAIN,
+                                   d_snr, stream);
+}
+
+ffa_status ffa_boxcar_snr_template(const float* d_prof, int32_t rows, int32_t cols,
+                                   const int32_t* h_widths, int32_t nw, double stdnoise,
+                                   int32_t boxcar, float* d_snr, void* stream) {
+    if (boxcar != FFA_BOXCAR_PLAIN && boxcar != FFA_BOXCAR_ZERO_MEAN)
+        return fail(FFA_ERR_ARG, "boxcar must be FFA_BOXCAR_PLAIN or FFA_BOXCAR_ZERO_MEAN");
     if (!d_prof || !d_snr) return fail(FFA_ERR_ARG, "null pointer");
     if (rows < 0 || cols < 1) return fail(FFA_ERR_ARG, "rows >= 0 and cols >= 1 required");
     if (cols > kMaxCols) return fail(FFA_ERR_UNSUPPORTED, "cols above %d", kMaxCols);
     if (!(stdnoise > 0.0) || !std::isfinite(stdnoise)) return fail(FFA_ERR_ARG, "stdnoise must be > 0");
     SnrParams sp{};
-    ffa_status stt = make_widths(h_widths, nw, cols, &sp.widths);
+    // the zero-mean template needs off-pulse bins: w < cols
+    ffa_status stt = make_widths(h_widths, nw, boxcar ? cols - 1 : cols, &sp.widths, boxcar);
     if (stt != FFA_OK) return stt;
     sp.prof = d_prof;
     sp.rows = rows;
@@ -1058,12 +1074,12 @@ ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out
 }
 
 // ---------------------------------------------------------------------------------
-ffa_status ffa_periodogram_plan_tiles(int64_t n, double tsamp, double pmin, double pmax,
+ffa_status ffa_periodogram_plan_opts(int64_t n, double tsamp, double pmin, double pmax,
                                       int32_t bmin, int32_t bmax, const int32_t* h_widths,
-                                      int32_t nw, const ffa_tiles* tiles, ffa_plan_info* out) {
+                                      int32_t nw, const ffa_plan_opts* opts, ffa_plan_info* out) {
     if (!out) return fail(FFA_ERR_ARG, "out is null");
     Tiles T;
-    ffa_status st = read_tiles(tiles, &T);
+    ffa_status st = read_tiles(opts, &T);
     if (st != FFA_OK) return st;
     Plan* pl = nullptr;
     st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, T, &pl);
@@ -1080,30 +1096,30 @@ ffa_status ffa_periodogram_plan_tiles(int64_t n, double tsamp, double pmin, doub
     out->snr_ops = pl->snr_ops;
     out->workspace_bytes = pl->ws_bytes;
     out->host_workspace_bytes = pl->ws_host_bytes;
-    out->tiles = ffa_tiles{std::max(pl->bottom_nmax, pl->bottom0_nmax), 0, 0};
+    out->opts = ffa_plan_opts{std::max(pl->bottom_nmax, pl->bottom0_nmax), 0, 0, pl->W.boxcar};
     for (const TransformDesc& t : pl->trs)
-        if (t.depth > 0) out->tiles.top_levels = std::max(out->tiles.top_levels, (int32_t)t.chunk);
+        if (t.depth > 0) out->opts.top_levels = std::max(out->opts.top_levels, (int32_t)t.chunk);
     for (const WorkItem& it : pl->items)
-        if (it.pass >= 0) out->tiles.top_rows = std::max(out->tiles.top_rows, (int32_t)it.rows);
+        if (it.pass >= 0) out->opts.top_rows = std::max(out->opts.top_rows, (int32_t)it.rows);
     return FFA_OK;
 }
 
 ffa_status ffa_periodogram_plan(int64_t n, double tsamp, double pmin, double pmax, int32_t bmin,
                                 int32_t bmax, const int32_t* h_widths, int32_t nw,
                                 ffa_plan_info* out) {
-    return ffa_periodogram_plan_tiles(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, nullptr, out);
+    return ffa_periodogram_plan_opts(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, nullptr, out);
 }
 
-ffa_status ffa_periodogram_tiles(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp,
+ffa_status ffa_periodogram_opts(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp,
                                  double pmin, double pmax, int32_t bmin, int32_t bmax,
-                                 const int32_t* h_widths, int32_t nw, const ffa_tiles* tiles,
+                                 const int32_t* h_widths, int32_t nw, const ffa_plan_opts* opts,
                                  double* d_periods, int32_t* d_foldbins, float* d_snr,
                                  int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream) {
     if (!d_x || !d_periods || !d_foldbins || !d_snr || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
     if (dtype != FFA_F32 && dtype != FFA_F16 && dtype != FFA_I8) return fail(FFA_ERR_ARG, "bad dtype");
     if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
     Tiles T;
-    ffa_status st = read_tiles(tiles, &T);
+    ffa_status st = read_tiles(opts, &T);
     if (st != FFA_OK) return st;
     Plan* pl = nullptr;
     st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, T, &pl);
@@ -1122,7 +1138,7 @@ ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double t
                            double pmax, int32_t bmin, int32_t bmax, const int32_t* h_widths,
                            int32_t nw, double* d_periods, int32_t* d_foldbins, float* d_snr,
                            int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream) {
-    return ffa_periodogram_tiles(d_x, dtype, n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw,
+    return ffa_periodogram_opts(d_x, dtype, n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw,
                                  nullptr, d_periods, d_foldbins, d_snr, ntrials_cap, d_ws,
                                  ws_bytes, stream);
 }
@@ -1134,13 +1150,13 @@ ffa_status ffa_plan_cache_clear(void) {
     return FFA_OK;
 }
 
-ffa_status ffa_batch_plan_tiles(const ffa_series* h_series, int32_t nseries,
+ffa_status ffa_batch_plan_opts(const ffa_series* h_series, int32_t nseries,
                                 const int32_t* h_widths, int32_t nw, size_t ws_budget,
-                                const ffa_tiles* tiles, int64_t* h_trial_offsets,
+                                const ffa_plan_opts* opts, int64_t* h_trial_offsets,
                                 ffa_batch_info* out) {
     if (!out) return fail(FFA_ERR_ARG, "out is null");
     Tiles T;
-    ffa_status st = read_tiles(tiles, &T);
+    ffa_status st = read_tiles(opts, &T);
     if (st != FFA_OK) return st;
     Batch* B = nullptr;
     st = get_batch(h_series, nseries, h_widths, nw, ws_budget, T, &B);
@@ -1160,21 +1176,21 @@ ffa_status ffa_batch_plan_tiles(const ffa_series* h_series, int32_t nseries,
 ffa_status ffa_batch_plan(const ffa_series* h_series, int32_t nseries, const int32_t* h_widths,
                           int32_t nw, size_t ws_budget, int64_t* h_trial_offsets,
                           ffa_batch_info* out) {
-    return ffa_batch_plan_tiles(h_series, nseries, h_widths, nw, ws_budget, nullptr,
+    return ffa_batch_plan_opts(h_series, nseries, h_widths, nw, ws_budget, nullptr,
                                 h_trial_offsets, out);
 }
 
-ffa_status ffa_periodogram_batch_tiles(const void* d_x, ffa_dtype dtype,
+ffa_status ffa_periodogram_batch_opts(const void* d_x, ffa_dtype dtype,
                                        const ffa_series* h_series, int32_t nseries,
                                        const int32_t* h_widths, int32_t nw, size_t ws_budget,
-                                       const ffa_tiles* tiles, double* d_periods,
+                                       const ffa_plan_opts* opts, double* d_periods,
                                        int32_t* d_foldbins, float* d_snr, int64_t ntrials_cap,
                                        void* d_ws, size_t ws_bytes, void* stream) {
     if (!d_x || !d_periods || !d_foldbins || !d_snr || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
     if (dtype != FFA_F32 && dtype != FFA_F16 && dtype != FFA_I8) return fail(FFA_ERR_ARG, "bad dtype");
     if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
     Tiles T;
-    ffa_status st = read_tiles(tiles, &T);
+    ffa_status st = read_tiles(opts, &T);
     if (st != FFA_OK) return st;
     Batch* B = nullptr;
     st = get_batch(h_series, nseries, h_widths, nw, ws_budget, T, &B);
@@ -1201,7 +1217,7 @@ ffa_status ffa_periodogram_batch(const void* d_x, ffa_dtype dtype, const ffa_ser
                                  size_t ws_budget, double* d_periods, int32_t* d_foldbins,
                                  float* d_snr, int64_t ntrials_cap, void* d_ws, size_t ws_bytes,
                                  void* stream) {
-    return ffa_periodogram_batch_tiles(d_x, dtype, h_series, nseries, h_widths, nw, ws_budget,
+    return ffa_periodogram_batch_opts(d_x, dtype, h_series, nseries, h_widths, nw, ws_budget,
                                        nullptr, d_periods, d_foldbins, d_snr, ntrials_cap, d_ws,
                                        ws_bytes, stream);
 }

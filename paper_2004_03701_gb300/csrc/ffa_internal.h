@@ -251,6 +251,7 @@ struct OctaveDesc {
 struct Widths {
     int32_t nw;
     int32_t wmax;
+    int32_t boxcar;  // template: 0 plain (1/sqrt(w) on w bins), 1 zero-mean (zero sum)
     int32_t w[kMaxWidths];
     float inv_sqrt_w[kMaxWidths];
 };

@@ -308,6 +308,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 // widths at a time with 15 shuffles.  `write` false: the half only takes part in the
 // shuffles (an odd row count) and stores nothing.
 // ---------------------------------------------------------------------------------
+// Score of width index iw from the largest boxcar sum cmax of a p-bin profile whose
+// bins sum to `total`: plain boxcar cmax / sqrt(w); zero-mean boxcar (value a on the w
+// bins, b on the others, zero sum, unit square sum) (a - b) cmax + b total, with
+// a - b = sqrt(p / (w (p - w))) and b = -sqrt(w / (p (p - w))).  Times 1 / noise std.
+__device__ __forceinline__ float snr_scale(float cmax, float total, const Widths& W, int iw,
+                                           int p, float inv_std) {
+    if (!W.boxcar) return cmax * inv_std * W.inv_sqrt_w[iw];
+    const float w = (float)W.w[iw], fp = (float)p, rest = (float)(p - W.w[iw]);
+    const float amb = sqrtf(fp / (w * rest));
+    const float b = -sqrtf(w / (fp * rest));
+    return __fmaf_rn(amb, cmax, b * total) * inv_std;
+}
+
 template <int Q>
 __device__ __forceinline__ void snr_half(const float* A, const float* B, int k, int p, float* S,
                                          const Widths& W, float inv_std, float* out, bool write,
@@ -383,7 +396,7 @@ __device__ __forceinline__ void snr_half(const float* A, const float* B, int k, 
             b[0] = fmaxf(keep, __shfl_xor_sync(kFull, send, 1, 16));
         }
         // lane h now holds width w0 + h
-        if (write && w0 + h < W.nw) out[w0 + h] = b[0] * inv_std * W.inv_sqrt_w[w0 + h];
+        if (write && w0 + h < W.nw) out[w0 + h] = snr_scale(b[0], total, W, w0 + h, p, inv_std);
     }
     __syncwarp();
 }
@@ -436,7 +449,7 @@ __device__ __noinline__ void snr_row_any(const float* prof, int p, float* S, con
         float best = -INFINITY;
         for (int k = lane; k < p; k += 32) best = fmaxf(best, S[k + w] - S[k]);
         for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
-        if (lane == 0) out[iw] = best * inv_std * W.inv_sqrt_w[iw];
+        if (lane == 0) out[iw] = snr_scale(best, S[p], W, iw, p, inv_std);
     }
     __syncwarp();
 }

@@ -203,3 +203,17 @@ def test_plan_arithmetic_counts(lib):
         adds = sum(rows(int(m)) * int(p) for m, p in zip(pl.tr_m, pl.tr_p))
         ops = sum(int(k) * int(p) * (1 + 2 * len(widths)) for k, p in zip(pl.tr_kept, pl.tr_p))
         assert info.ffa_adds == adds and info.snr_ops == ops
+
+
+def test_plan_options_boxcar_template(lib):
+    args = (262144, 1e-3, 1.0, 10.0, 240, 260, (1, 2, 4))
+    plain = ffa.periodogram_plan(*args)
+    zm = ffa.periodogram_plan(*args, zero_mean=True)
+    assert zm.ntrials == plain.ntrials and zm.workspace_bytes == plain.workspace_bytes
+    opts = ffa._PlanOpts(0, 0, 0, 7)
+    info = ffa._PlanInfo()
+    w = np.array(args[-1], np.int32)
+    st = lib.ffa_periodogram_plan_opts(*args[:-1], w.ctypes.data_as(ctypes.c_void_p), len(w),
+                                       ctypes.cast(ctypes.byref(opts), ctypes.c_void_p),
+                                       ctypes.byref(info))
+    assert st == 1 and b"boxcar" in lib.ffa_last_error()

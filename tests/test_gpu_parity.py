@@ -208,6 +208,28 @@ def test_periodogram_long_profiles(F, bins, widths):
     compare_periodogram(got, ref, _sampled_rows(pl, sel))
 
 
+@pytest.mark.parametrize("rows,cols,widths", [
+    (300, 250, synth.WIDTHS_11), (77, 17, (1, 2, 3, 16)), (41, 560, synth.WIDTHS_16),
+    (20, 1024, synth.WIDTHS_16),
+])
+def test_boxcar_snr_zero_mean(F, rows, cols, widths):
+    """The zero-mean boxcar template (zero sum, unit square sum) on both S/N paths,
+    against the FP64 oracle; profiles with a large common offset, which it ignores."""
+    prof = synth.normal_block(rows, cols, seed=cols) + np.float32(5.0)
+    got = F.boxcar_snr(dev(prof), widths, 2.5, zero_mean=True).cpu().numpy()
+    ref = oracle.boxcar_snr(prof.astype(np.float64), widths, 2.5, zero_mean=True)
+    assert np.abs(got - ref).max() <= SNR_TOL
+
+
+def test_periodogram_zero_mean_full(F):
+    """plain_small scored with the zero-mean boxcar: every trial against the oracle."""
+    w = synth.plain_small()
+    args = (w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths)
+    got = F.periodogram(dev(w.x), *args, zero_mean=True)
+    ref = oracle.periodogram(w.x, *args, zero_mean=True)
+    compare_periodogram(got, ref)
+
+
 def test_status_and_launch_accounting(F):
     w = synth.plain_small()
     s = F.Searcher(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths)
