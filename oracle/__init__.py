@@ -17,6 +17,8 @@ Paper passages followed (sections and equations of the paper):
   * boxcar S/N ...... Sec. 5.4, Sec. 3.3 (Z = x.s, unit square sum), App. A.3; the
                       zero-mean boxcar: Sec. 3.3 and 3.5 (another unit-square-sum template)
   * normalise ....... Sec. 3.1, Sec. 5.2 (zero mean, unit std from the whole series)
+  * running median .. Sec. 5.2 (de-reddening: subtract a running median, odd window,
+                      the series extended by its end samples)
 """
 from __future__ import annotations
 
@@ -83,6 +85,10 @@ def _load():
     lib.oracle_periodogram_kind.restype = _i64
     lib.oracle_periodogram_kind.argtypes = [_p, _i64, _dbl, _dbl, _dbl, _int, _int, _p, _int,
                                             _int, _p, _p, _p, _p, _i64]
+    lib.oracle_running_median.restype = _int
+    lib.oracle_running_median.argtypes = [_p, _i64, _i64, _p]
+    lib.oracle_running_median_at.restype = _int
+    lib.oracle_running_median_at.argtypes = [_p, _i64, _i64, _p, _i64, _p]
     lib.oracle_normalise.restype = _int
     lib.oracle_normalise.argtypes = [_p, _i64, _p, _p, _p]
     lib.oracle_periodogram.restype = _i64
@@ -223,6 +229,33 @@ def normalise(x: np.ndarray):
     if lib.oracle_normalise(_ptr(x), len(x), ctypes.byref(mean), ctypes.byref(std), _ptr(out)) != 0:
         raise ValueError("empty series")
     return mean.value, std.value, out
+
+
+def running_median(x: np.ndarray, width: int, at=None) -> np.ndarray:
+    """Sec. 5.2 running median of a float32 series over an odd window of ``width``
+    samples centred on each sample, the series extended by its end samples.
+    ``at``: optional sample indices; only the medians there are computed."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if at is None:
+        out = np.zeros(len(x), np.float32)
+        rc = lib.oracle_running_median(_ptr(x), len(x), int(width), _ptr(out))
+    else:
+        idx = np.ascontiguousarray(at, dtype=np.int64)
+        out = np.zeros(len(idx), np.float32)
+        rc = lib.oracle_running_median_at(_ptr(x), len(x), int(width), _ptr(idx), len(idx),
+                                          _ptr(out))
+    if rc != 0:
+        raise ValueError("invalid running-median arguments (empty series, even width, "
+                         "or index out of range)")
+    return out
+
+
+def deredden(x: np.ndarray, width: int) -> np.ndarray:
+    """Sec. 5.2 de-reddening: the series minus its running median, in float32 (one
+    rounding of the exact difference, as IEEE single subtraction gives)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    return x - running_median(x, width)
 
 
 @dataclass

@@ -15,6 +15,7 @@
  *   - trial periods, redundant rows      Sec. 2.3, Eqs. for nu_s and P_s
  *   - boxcar S/N                         Sec. 5.4, Sec. 3.3 (Z-statistic), App. A.3
  *   - normalisation                      Sec. 3.1, Sec. 5.2 (whole-series mean/std)
+ *   - running-median de-reddening        Sec. 5.2 (data whitening)
  *
  * Readings where the paper is silent (each is shared with the CUDA path as a
  * written convention, never as code):
@@ -28,6 +29,8 @@
  *   - transforms with m < 2 are skipped (P_s undefined)
  *   - boxcar S/N = max_k C_k / sqrt(m * w * V_f), with V_f = f for an integer
  *     factor and f - 1/3 otherwise                                    (Sec. 5.3, App. A.4)
+ *   - running median: odd window w = 2h + 1 centred on the sample; indices outside
+ *     [0, n) take the nearest end sample                              (Sec. 5.2)
  */
 #include "ffa_oracle_api.h"
 
@@ -313,6 +316,59 @@ int oracle_normalise(const float* x, int64_t n, double* mean, double* stdev, dou
     if (out)
         for (i = 0; i < n; ++i)
             out[i] = *stdev > 0.0 ? ((double)x[i] - *mean) / *stdev : 0.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Running median (Sec. 5.2): the low-frequency noise is removed by subtracting */
+/* a running median from the series before it is normalised.  med[i] is the    */
+/* median of the w = 2h + 1 samples x[i-h .. i+h]; an index before the start   */
+/* reads x[0] and one after the end reads x[n-1].  The window is copied out,    */
+/* sorted, and its middle element taken.                                       */
+/* ------------------------------------------------------------------------- */
+
+static int cmp_float(const void* a, const void* b)
+{
+    float u = *(const float*)a, v = *(const float*)b;
+    return (u > v) - (u < v);
+}
+
+static float window_median(const float* x, int64_t n, int64_t h, int64_t i, float* buf)
+{
+    int64_t j;
+    for (j = -h; j <= h; ++j) {
+        int64_t t = i + j;
+        buf[j + h] = x[t < 0 ? 0 : (t >= n ? n - 1 : t)];
+    }
+    qsort(buf, (size_t)(2 * h + 1), sizeof(float), cmp_float);
+    return buf[h];
+}
+
+int oracle_running_median_at(const float* x, int64_t n, int64_t w, const int64_t* idx,
+                             int64_t nidx, float* med)
+{
+    int64_t k;
+    float* buf;
+    if (n <= 0 || w < 1 || (w & 1) == 0 || nidx < 0) return -1;
+    buf = (float*)malloc((size_t)w * sizeof(float));
+    if (!buf) return -2;
+    for (k = 0; k < nidx; ++k) {
+        if (idx[k] < 0 || idx[k] >= n) { free(buf); return -1; }
+        med[k] = window_median(x, n, w / 2, idx[k], buf);
+    }
+    free(buf);
+    return 0;
+}
+
+int oracle_running_median(const float* x, int64_t n, int64_t w, float* med)
+{
+    int64_t i;
+    float* buf;
+    if (n <= 0 || w < 1 || (w & 1) == 0) return -1;
+    buf = (float*)malloc((size_t)w * sizeof(float));
+    if (!buf) return -2;
+    for (i = 0; i < n; ++i) med[i] = window_median(x, n, w / 2, i, buf);
+    free(buf);
     return 0;
 }
 

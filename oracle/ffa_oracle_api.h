@@ -29,6 +29,10 @@ int oracle_boxcar_snr_kind(const double* prof, int64_t rows, int64_t p, const in
 
 int oracle_normalise(const float* x, int64_t n, double* mean, double* stdev, double* out);
 
+int oracle_running_median(const float* x, int64_t n, int64_t w, float* med);
+int oracle_running_median_at(const float* x, int64_t n, int64_t w, const int64_t* idx,
+                             int64_t nidx, float* med);
+
 int64_t oracle_periodogram(const float* x, int64_t n, double tsamp, double pmin,
                            double pmax, int bmin, int bmax, const int* widths, int nw,
                            const unsigned char* select, double* periods, int* foldbins,
