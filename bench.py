@@ -12,6 +12,9 @@ series of U[2^20, 2^23] samples, each with its own period range in 0.1-30 s, one
 graph per step over all launch chunks); batch_int8 (1024 series of 2^21 samples,
 periods 0.1-10 s, bins 480-520, 16 widths, normalised and stored as int8).  --storage
 f16 / i8 stores the normalised input at reduced precision (sums stay FP32).
+--workload deredden times the step before the search instead: the running-median
+de-reddening of Sec. 5.2 on a 2^23-sample red-noise series at 64 us with a 1 s window
+(15625 samples); its metric is samples de-reddened per second.
 
 metric: time-series samples searched per second = samples / (device time of one step),
 summed over GPUs.  Each GPU searches its own series (independent; no collective is in
@@ -60,7 +63,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ffa", "reference"], default="ffa")
-    ap.add_argument("--workload", choices=["survey", "plain_small"] + list(BATCH_WORKLOADS),
+    ap.add_argument("--workload",
+                    choices=["survey", "plain_small", "deredden"] + list(BATCH_WORKLOADS),
                     default="survey")
     ap.add_argument("--storage", choices=["f32", "f16", "i8"], default=None,
                     help="input storage (default f32; i8 for batch_int8)")
@@ -541,6 +545,188 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- de-reddening (Sec. 5.2)
+DR_METRIC = "time-series samples de-reddened/s (running median, Sec. 5.2)"
+DR_N, DR_TSAMP, DR_SECONDS = 2 ** 23, 64e-6, 1.0
+
+
+def dr_oracle_rate(x, w, seconds=10.0, seed=0):
+    """Rate of the CPU oracle's running median (1 thread) on outputs spread over the
+    series, sized to about `seconds`; returns (rate, desc, (at, ref))."""
+    import oracle
+    r = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    probe = np.sort(r.integers(0, len(x), 64))
+    oracle.running_median(x, w, at=probe)
+    per = (time.perf_counter() - t0) / len(probe)
+    k = int(max(64, min(len(x), seconds / max(per, 1e-9))))
+    at = np.sort(r.choice(len(x), k, replace=False))
+    t0 = time.perf_counter()
+    ref = oracle.running_median(x, w, at=at)
+    dt = time.perf_counter() - t0
+    desc = ("oracle (1 thread, C: copy and sort each window) on %d outputs drawn uniformly "
+            "over the series, %.1f s measured, extrapolated per output" % (k, dt))
+    return k / dt, desc, (at, ref)
+
+
+def run_deredden(a):
+    world, rank, local = dist_env()
+    w = max(1, int(round(DR_SECONDS / DR_TSAMP))) | 1
+    x = synth.red_noise(DR_N, DR_TSAMP, seed=synth.SEED_BASE + 50 + rank)
+    cfg = {"workload": "deredden_red_2^23_64us_1s", "n": DR_N, "tsamp": DR_TSAMP,
+           "width": w, "noise": "N(0,1) + 1/f noise of equal power at 1 Hz",
+           "l2": "flushed (256 MB write) between steps",
+           "parallelism": "replicas" if world > 1 else "single"}
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        rates, desc = [], ""
+        per_step = max(2.0, 150.0 / (a.steps + a.warmup))
+        for i in range(a.warmup + a.steps):
+            rt, desc, _ = dr_oracle_rate(x, w, seconds=per_step, seed=i)
+            if i >= a.warmup:
+                rates.append(rt)
+        value = statistics.mean(rates)
+        line = {"impl": "reference", "metric": DR_METRIC, "value": value, "unit": UNIT,
+                "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": DR_N / value * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": cfg,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": "per step: " + desc},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+
+    import paper_2004_03701_gb300 as ffa
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ffa.build()
+    ffa.library()
+    xd = torch.from_numpy(x).to(dev)
+    y = torch.empty_like(xd)
+    R = ffa.RunningMedian(DR_N, w, dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, a.warmup)):
+        R(xd, y=y)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = ffa.launch_count()
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        R(xd, y=y)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    scopes = ffa.launch_count() - l0
+    barrier()
+    clk = clocks.stop()
+    t_step = sum(times) / len(times)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = world * DR_N / (t_step * 1e-3)
+    # kernels per call: level-0 count, 32 x (scan + scatter), interior and edge queries
+    h = w // 2
+    per_call = 1 + 64 + (1 if DR_N > 2 * h else 0) + 1
+    launches = per_call * a.steps
+
+    ffa.profile_reset()
+    ffa.profile_enable(True)
+    for _ in range(a.steps):
+        flush.zero_()
+        R(xd, y=y)
+    torch.cuda.synchronize()
+    ffa.profile_enable(False)
+    kern = {}
+    for name in ("median_build", "median_query"):
+        q = ffa.profile_query(name)
+        if q["launches"]:
+            kern[name] = q
+    ffa.profile_reset()
+    peak, peak_kind = measured_peaks()
+    top = max(kern, key=lambda k: kern[k]["ms"])
+    avg_s = kern[top]["ms"] / kern[top]["launches"] * 1e-3
+    # algorithmic bytes of the whole de-reddening: the series read once, y written once
+    alg = 8.0 * DR_N
+    roofline = {"bound": "hbm", "kernel": top, "achieved": alg / avg_s / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": alg / avg_s / 1e9 / peak,
+                "traffic": recorded_traffic(top, cfg["workload"]),
+                "alg_bytes_per_launch": alg,
+                "alg_bytes_def": "8 n: the series read once and the de-reddened series "
+                                 "written once (the running median has no streaming form; "
+                                 "see the build's own traffic in kernels_ms_per_step)",
+                "peak_source": peak_kind,
+                "share_of_step": kern[top]["ms"] / sum(k["ms"] for k in kern.values()),
+                "whole_step_frac": alg / (t_step * 1e-3) / 1e9 / peak}
+
+    e2e = None
+    if not a.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.empty(DR_N, dtype=torch.float32, pin_memory=True)
+        for _ in range(2):
+            xd.copy_(xh, non_blocking=True)
+            R(xd, y=y)
+            yh.copy_(y, non_blocking=True)
+            stream.synchronize()
+        et = []
+        for _ in range(a.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            xd.copy_(xh, non_blocking=True)
+            R(xd, y=y)
+            yh.copy_(y, non_blocking=True)
+            stream.synchronize()
+            et.append(time.perf_counter() - t0)
+        te = sum(et) / len(et)
+        if world > 1:
+            tt = torch.tensor([te], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": world * DR_N / te, "unit": UNIT, "h2d_bytes_per_step": 4 * DR_N,
+               "d2h_bytes_per_step": 4 * DR_N}
+
+    cpu = acc = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        rate, desc, (at, ref) = dr_oracle_rate(x, w, seconds=10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        got = y.cpu().numpy()[at]
+        acc = {"outputs_compared": int(len(at)),
+               "bit_exact": bool(np.array_equal(got, x[at] - ref))}
+    if rank == 0:
+        line = {"metric": DR_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roofline,
+                "kernels_ms_per_step": {k: v["ms"] / a.steps for k, v in kern.items()},
+                "e2e": e2e, "cpu_baseline": cpu, "accuracy": acc, "clocks": clk,
+                "gpu_launches": launches, "api_calls": scopes // 2}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 # ------------------------------------------------------------------------------- GPU
 def run_ffa(a):
     import torch
@@ -792,7 +978,9 @@ def run_e2e(job, a, torch, ffa, flush, barrier, world, dev, n_all):
 
 def main():
     a = parse()
-    if a.impl == "reference":
+    if a.workload == "deredden":
+        run_deredden(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ffa(a)

@@ -139,6 +139,25 @@ ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out
                          double* d_mean_std, void* d_ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------
+ * Running median (paper Sec. 5.2): the low-frequency ("red") noise of a series is
+ * removed by subtracting a running median before the series is normalised.
+ *   med[i] = median of x[i-h .. i+h],   width = 2h + 1 (odd),
+ * where an index before the start reads x[0] and one after the end reads x[n-1]
+ * (the series extended by its end samples), and
+ *   y[i]   = x[i] - med[i]   (one float subtraction).
+ * The median is a sample of the window, found exactly (a wavelet matrix over the
+ * series: every output is a range-quantile query), for any width.
+ * d_x: n floats (device), finite (NaN has no order).  d_med, d_y: n floats (device),
+ * either may be NULL but not both; either may equal d_x (in place), not each other.
+ * Workspace: ffa_running_median_workspace(n) bytes (about 16 n).  Deterministic.
+ * Errors: FFA_ERR_ARG (null pointers, n outside [1, 2^31 - 1], even or non-positive
+ *         width, d_med == d_y), FFA_ERR_CAPACITY (workspace too small).
+ * ---------------------------------------------------------------------------- */
+ffa_status ffa_running_median_workspace(int64_t n, size_t* bytes);
+ffa_status ffa_running_median(const float* d_x, int64_t n, int64_t width, float* d_med,
+                              float* d_y, void* d_ws, size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------
  * Periodogram search plan (paper Sec. 5.3, Fig. 4; Sec. 5.6 for the first factor).
  *   f0 = pmin / (bmin * tsamp) (must be >= 1), fg = (bmax + 1) / bmin,
  *   octave k: factor F_k = f0 * fg^k while bmin * tsamp * F_k <= pmax,

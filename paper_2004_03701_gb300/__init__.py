@@ -14,6 +14,7 @@ Calls (names follow include/ffa.h and the paper, Morello et al. 2020):
   periodogram_host(x_host, ...)                 same, host buffers in and out
   BatchSearcher(series, widths)                 many series in one buffer, Sec. 5.7
   SegmentSearcher(n, tsamp, segments, widths)   dynamic duty-cycle resolution, Sec. 5.6
+  running_median(x, width), deredden(x, width)  de-reddening before normalising, Sec. 5.2
 """
 from __future__ import annotations
 
@@ -30,7 +31,7 @@ __all__ = [
     "Series", "BatchInfo", "batch_plan", "BatchSearcher", "periodogram_batch", "shard_series",
     "Tiles", "tile_candidates", "tune", "tune_periodogram", "SegmentSearcher",
     "check", "plan_cache_clear", "launch_count", "kernel_names", "profile_enable", "profile_reset",
-    "profile_query",
+    "profile_query", "RunningMedian", "running_median", "deredden", "median_width",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -119,6 +120,8 @@ def library() -> ctypes.CDLL:
                                         sz, vp]
     L.ffa_normalise_workspace.argtypes = [i64, ctypes.POINTER(sz)]
     L.ffa_normalise.argtypes = [vp, i64, vp, i32, vp, vp, sz, vp]
+    L.ffa_running_median_workspace.argtypes = [i64, ctypes.POINTER(sz)]
+    L.ffa_running_median.argtypes = [vp, i64, i64, vp, vp, vp, sz, vp]
     L.ffa_launch_count.restype = i64
     L.ffa_kernel_kinds.restype = i32
     L.ffa_kernel_name.restype = ctypes.c_char_p
@@ -132,8 +135,8 @@ def library() -> ctypes.CDLL:
               "ffa_normalise_workspace", "ffa_normalise", "ffa_batch_plan",
               "ffa_periodogram_batch", "ffa_plan_cache_clear", "ffa_periodogram_plan_opts",
               "ffa_periodogram_opts", "ffa_batch_plan_opts", "ffa_periodogram_batch_opts",
-              "ffa_boxcar_snr_template",
-              "ffa_profile_query"):
+              "ffa_boxcar_snr_template", "ffa_running_median_workspace",
+              "ffa_running_median", "ffa_profile_query"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -201,6 +204,61 @@ def normalise(x, dtype=None, stream=None):
                            _stream_handle(stream)))
     m, s = stats.tolist()
     return out, m, s
+
+
+def median_width(seconds: float, tsamp: float) -> int:
+    """Samples of a running-median window of `seconds`, made odd (Sec. 5.2 leaves the
+    width to the user)."""
+    return max(1, int(round(seconds / tsamp))) | 1
+
+
+class RunningMedian:
+    """Running median over an odd window of `width` samples (Sec. 5.2 de-reddening),
+    for float32 CUDA series of `n` samples, with a workspace kept across calls.
+
+    ``S(x, med=None, y=None)`` writes med[i], the median of x[i-h .. i+h] with the
+    series extended by its end samples (width = 2h + 1), and/or y = x - med; either
+    output may be ``x`` itself (in place).  Asynchronous on the current stream."""
+
+    def __init__(self, n: int, width: int, device="cuda"):
+        torch = _torch()
+        L = library()
+        need = ctypes.c_size_t()
+        _check(L.ffa_running_median_workspace(int(n), ctypes.byref(need)))
+        self.n, self.width = int(n), int(width)
+        self.device = torch.device(device)
+        self.ws = _workspace(need.value, self.device)
+
+    def __call__(self, x, med=None, y=None, stream=None):
+        torch = _torch()
+        _dev_tensor(x, "x")
+        if x.dtype != torch.float32 or x.numel() != self.n:
+            raise TypeError("x must be a float32 CUDA tensor of %d samples" % self.n)
+        for t, name in ((med, "med"), (y, "y")):
+            if t is not None:
+                _dev_tensor(t, name)
+                if t.dtype != torch.float32 or t.numel() != self.n:
+                    raise TypeError("%s must be a float32 CUDA tensor of %d samples" % (name, self.n))
+        _check(library().ffa_running_median(
+            _vp(x), self.n, self.width, _vp(med) if med is not None else None,
+            _vp(y) if y is not None else None, _vp(self.ws), self.ws.numel(),
+            _stream_handle(stream)))
+        return med, y
+
+
+def running_median(x, width: int, stream=None):
+    """The running median of a float32 CUDA series (Sec. 5.2), a new tensor."""
+    med = _torch().empty_like(x)
+    RunningMedian(x.numel(), width, x.device)(x, med=med, stream=stream)
+    return med
+
+
+def deredden(x, width: int, inplace: bool = False, stream=None):
+    """x minus its running median over `width` samples (Sec. 5.2): the red-noise removal
+    that precedes `normalise`.  In place if `inplace`."""
+    y = x if inplace else _torch().empty_like(x)
+    RunningMedian(x.numel(), width, x.device)(x, y=y, stream=stream)
+    return y
 
 
 def downsample(x, factor: float, stream=None):

@@ -3,6 +3,7 @@
 // behind the C ABI declared in include/ffa.h.
 #include "ffa.h"
 #include "ffa_internal.h"
+#include "ffa_kinds.h"
 
 #include <atomic>
 #include <cmath>
@@ -65,12 +66,13 @@ std::mutex g_prof_mu;
 bool g_prof_on = false;
 std::vector<ProfRec> g_pending;
 std::vector<cudaEvent_t> g_pool;
-ProfAcc g_acc[kNumKinds];
+ProfAcc g_acc[kAllKinds];
 
-const char* kKindNames[kNumKinds] = {"prefix_partial", "prefix_top",     "prefix_final",
+const char* kKindNames[kAllKinds] = {"prefix_partial", "prefix_top",     "prefix_final",
                                      "downsample",     "ffa_bottom",     "ffa_bottom_snr",
                                      "ffa_top",        "boxcar_snr",     "normalise",
-                                     "ffa_persistent", "top_prep"};
+                                     "ffa_persistent", "top_prep",       "median_build",
+                                     "median_query"};
 
 cudaEvent_t pool_get() {
     if (!g_pool.empty()) {
@@ -848,9 +850,9 @@ const char* ffa_last_error(void) { return g_err.c_str(); }
 const char* ffa_version(void) { return "libffa 0.1 (sm_103a)"; }
 
 int64_t ffa_launch_count(void) { return g_launches.load(); }
-int32_t ffa_kernel_kinds(void) { return kNumKinds; }
+int32_t ffa_kernel_kinds(void) { return kAllKinds; }
 const char* ffa_kernel_name(int32_t kind) {
-    return (kind >= 0 && kind < kNumKinds) ? kKindNames[kind] : "";
+    return (kind >= 0 && kind < kAllKinds) ? kKindNames[kind] : "";
 }
 ffa_status ffa_profile_enable(int32_t on) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -864,7 +866,7 @@ ffa_status ffa_profile_reset(void) {
     return FFA_OK;
 }
 ffa_status ffa_profile_query(int32_t kind, int64_t* launches, double* total_ms, double* alg_bytes) {
-    if (kind < 0 || kind >= kNumKinds) return fail(FFA_ERR_ARG, "bad kernel kind");
+    if (kind < 0 || kind >= kAllKinds) return fail(FFA_ERR_ARG, "bad kernel kind");
     std::lock_guard<std::mutex> lk(g_prof_mu);
     drain_pending();
     if (launches) *launches = g_acc[kind].launches;

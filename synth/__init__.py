@@ -61,6 +61,20 @@ def white_noise(n: int, seed: int) -> np.ndarray:
     return rng(seed).standard_normal(n)
 
 
+def red_noise(n: int, tsamp: float, seed: int, f1: float = 1.0) -> np.ndarray:
+    """N(0, 1) white noise plus 1/f ("red") noise of the same power at frequency f1 (Hz):
+    a Gaussian spectrum shaped by sqrt(f1 / f), no DC term, drawn with numpy's FFT.
+    The input that running-median de-reddening (Sec. 5.2) is for."""
+    r = rng(seed)
+    white = r.standard_normal(n)
+    spec = np.fft.rfft(r.standard_normal(n))
+    f = np.fft.rfftfreq(n, tsamp)
+    shape = np.zeros_like(f)
+    shape[1:] = np.sqrt(f1 / f[1:])
+    red = np.fft.irfft(spec * shape, n)
+    return (white + red).astype(np.float32)
+
+
 def pulse_train(n: int, tsamp: float, pulse: Pulse) -> np.ndarray:
     """Gaussian pulse train sampled at t_i = i * tsamp, scaled to unit square sum
     times the amplitude.  Pulse FWHM = duty * period."""

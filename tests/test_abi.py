@@ -102,6 +102,37 @@ def test_other_calls_reject_bad_arguments(lib):
 def test_kernel_kinds(lib):
     names = ffa.kernel_names()
     assert "ffa_bottom" in names and "ffa_top" in names and "downsample" in names
+    assert "median_build" in names and "median_query" in names
+
+
+def test_running_median_rejects_bad_arguments(lib):
+    sz = ctypes.c_size_t()
+    assert lib.ffa_running_median_workspace(0, ctypes.byref(sz)) == 1
+    assert lib.ffa_running_median_workspace(1 << 31, ctypes.byref(sz)) == 1
+    assert lib.ffa_running_median_workspace(5, None) == 1
+    assert lib.ffa_running_median_workspace(2 ** 23, ctypes.byref(sz)) == 0
+    need = sz.value
+    assert 16 * 2 ** 23 <= need <= 17 * 2 ** 23
+    fake = ctypes.c_void_p(256)   # never dereferenced: rejected on the host first
+    n = 2 ** 23
+    call = lib.ffa_running_median
+    assert call(None, n, 15, fake, None, fake, need, None) == 1
+    assert call(fake, n, 15, None, None, fake, need, None) == 1       # no output
+    assert call(fake, n, 16, fake, None, fake, need, None) == 1       # even width
+    assert call(fake, n, 0, fake, None, fake, need, None) == 1
+    assert call(fake, n, -3, fake, None, fake, need, None) == 1
+    assert call(fake, 0, 15, fake, None, fake, need, None) == 1
+    assert call(fake, n, 15, fake, fake, fake, need, None) == 1       # med == y
+    assert call(fake, n, 15, fake, None, ctypes.c_void_p(260), need, None) == 1  # alignment
+    assert call(fake, n, 15, fake, None, fake, need - 1, None) == 2   # workspace too small
+    assert len(lib.ffa_last_error()) > 0
+
+
+def test_median_width():
+    assert ffa.median_width(1.0, 64e-6) == 15625
+    assert ffa.median_width(0.5, 1e-3) == 501
+    assert ffa.median_width(0.01, 1e-3) == 11
+    assert ffa.median_width(1e-6, 1e-3) == 1
 
 
 def test_width_sets_fit_the_plan(lib):
