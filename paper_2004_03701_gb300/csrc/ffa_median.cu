@@ -22,9 +22,10 @@
 // the keys in an order A_L (A_0 is the series); bit b = 31 - L of A_L[i] is stored as
 // a bit vector B_L with a rank directory, and A_{L+1} lists the keys of A_L whose bit b
 // is 0, in order, then those whose bit is 1.  Z_L is the number of zeros of level L.
-// Each level is two launches: a one-CTA scan of the per-tile zero counts, then a
-// scatter over tiles of 4096 keys that writes B_L's words (warp ballots) with their
-// rank directory and A_{L+1}, and counts next level's zeros per destination tile.
+// Each level is one launch over tiles of 4096 keys: every CTA sums the per-tile zero
+// counts before its tile (a one-CTA scan launch does it for series of more than 4096
+// tiles), writes B_L's words (warp ballots) with their rank directory and A_{L+1}, and
+// counts next level's zeros per destination tile (three count buffers rotate).
 //
 // Query.  For a range [l, r) of A_L and a rank k inside it, the zeros of B_L in the
 // range map to [rank0(l), rank0(r)) of A_{L+1} and the ones to Z_L + the same for the
@@ -32,7 +33,8 @@
 // its key.  32 levels give the key.  rank0 is one 8-byte load: {zeros before the word,
 // the word's bits}.  Each thread follows four windows at once to overlap the loads.
 // Windows that reach past an end hold c copies of an end sample besides a clamped
-// range; a count of the range's keys below each end key places the copies.
+// range; a count of the range's keys below each end key places the copies.  Both kinds
+// of output run in one launch.
 #include "ffa.h"
 #include "ffa_internal.h"
 #include "ffa_kinds.h"
@@ -53,6 +55,7 @@ constexpr int kThreads = 256;       // build CTA
 constexpr int kRounds = 16;         // keys per build thread
 constexpr int kTile = kThreads * kRounds;  // keys per build CTA (128 words of B_L)
 constexpr int kScanThreads = 1024;  // the one-CTA scan
+constexpr int kFusedPrefixMaxTiles = 4096;  // up to here each scatter CTA sums the counts
 constexpr int kQueryThreads = 256;
 constexpr int kQueryILP = 4;        // windows per query thread
 constexpr int64_t kMaxN = 2147483647;
@@ -71,12 +74,14 @@ __device__ __forceinline__ uint32_t rank0(const uint2* __restrict__ D, uint32_t 
     return e.x + __popc(~e.y & ((1u << (i & 31)) - 1u));
 }
 
-// Level 0: zero count of the top key bit per tile, and the two end keys.
+// Level 0: zero count of the top key bit per tile, the two end keys, and a cleared count
+// buffer for level 1.
 __global__ void __launch_bounds__(kThreads)
 wm_count_kernel(const float* __restrict__ x, int64_t n, uint32_t* __restrict__ tz,
-                uint32_t* __restrict__ ends) {
+                uint32_t* __restrict__ tz_clear, uint32_t* __restrict__ ends) {
     const int64_t t0 = (int64_t)blockIdx.x * kTile;
     uint32_t z = 0;
+#pragma unroll
     for (int j = 0; j < kRounds; ++j) {
         const int64_t idx = t0 + j * kThreads + threadIdx.x;
         if (idx < n) z += (float_key(x[idx]) >> 31) ^ 1u;
@@ -89,6 +94,7 @@ wm_count_kernel(const float* __restrict__ x, int64_t n, uint32_t* __restrict__ t
         uint32_t t = 0;
         for (int w = 0; w < kThreads / 32; ++w) t += s[w];
         tz[blockIdx.x] = t;
+        tz_clear[blockIdx.x] = 0;
         if (blockIdx.x == 0) {
             ends[0] = float_key(x[0]);
             ends[1] = float_key(x[n - 1]);
@@ -96,11 +102,11 @@ wm_count_kernel(const float* __restrict__ x, int64_t n, uint32_t* __restrict__ t
     }
 }
 
-// One CTA: exclusive prefix of the per-tile zero counts, Z_L, and a cleared count
-// buffer for the next level.
+// One CTA: exclusive prefix of the per-tile zero counts and Z_L, for series with more
+// tiles than the scatter CTAs sum themselves.
 __global__ void __launch_bounds__(kScanThreads)
 wm_scan_kernel(const uint32_t* __restrict__ tz, int ntiles, uint32_t* __restrict__ pre,
-               uint32_t* __restrict__ Zl, uint32_t* __restrict__ clear) {
+               uint32_t* __restrict__ Zl) {
     const int tid = threadIdx.x;
     const int per = (ntiles + kScanThreads - 1) / kScanThreads;
     const int b = tid * per, e = min(b + per, ntiles);
@@ -130,31 +136,57 @@ wm_scan_kernel(const uint32_t* __restrict__ tz, int ntiles, uint32_t* __restrict
         run += tz[i];
     }
     if (tid == kScanThreads - 1) *Zl = s[kScanThreads / 32 - 1];
-    if (clear)
-        for (int i = tid; i < ntiles; i += kScanThreads) clear[i] = 0;
 }
 
 // Level L: bit vector and rank directory of A_L, stable partition into A_{L+1}, and the
 // zero counts of the next bit per destination tile.  xsrc (level 0) or src holds A_L;
-// dst and tz_next are null at the last level.
+// dst and tz_next are null at the last level.  The zeros before this tile and Z_L come
+// from `pre` and `Zl` when a scan ran (large series); otherwise every CTA sums the tile
+// counts `tz` itself and CTA 0 stores Z_L.  The count buffer of level L + 2 is cleared
+// here (level L + 1 adds into tz_next, and level L - 1 read tz_clear).
 __global__ void __launch_bounds__(kThreads)
 wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xsrc,
-                  uint32_t* __restrict__ dst, int64_t n, int bit,
-                  const uint32_t* __restrict__ pre, const uint32_t* __restrict__ Zl,
-                  uint2* __restrict__ dir, uint32_t* __restrict__ tz_next) {
+                  uint32_t* __restrict__ dst, int64_t n, int bit, int ntiles,
+                  const uint32_t* __restrict__ tz, const uint32_t* __restrict__ pre,
+                  uint32_t* __restrict__ Zl, uint2* __restrict__ dir,
+                  uint32_t* __restrict__ tz_next, uint32_t* __restrict__ tz_clear) {
     __shared__ uint32_t s_z[kRounds * (kThreads / 32)];  // zeros per (round, warp)
+    __shared__ uint32_t s_base[2 * (kThreads / 32)];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t t0 = (int64_t)blockIdx.x * kTile;
     uint32_t key[kRounds], ones[kRounds], valid[kRounds];
+    // all loads first: the ballots below would otherwise wait on each in turn
 #pragma unroll
     for (int j = 0; j < kRounds; ++j) {
         const int64_t idx = t0 + j * kThreads + tid;
-        const bool v = idx < n;
-        key[j] = v ? (xsrc ? float_key(xsrc[idx]) : src[idx]) : 0u;
+        key[j] = idx < n ? (xsrc ? float_key(__ldg(xsrc + idx)) : __ldg(src + idx)) : 0u;
+    }
+    uint32_t before = 0, total = 0;  // zeros of the tiles before this one, and of all
+    if (!pre) {
+        for (int i = tid; i < ntiles; i += kThreads) {
+            const uint32_t c = __ldg(tz + i);
+            total += c;
+            before += i < (int)blockIdx.x ? c : 0u;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < kRounds; ++j) {
+        const bool v = t0 + j * kThreads + tid < n;
         valid[j] = __ballot_sync(0xffffffffu, v);
         ones[j] = __ballot_sync(0xffffffffu, v && ((key[j] >> bit) & 1u));
         if (lane == 0) s_z[j * (kThreads / 32) + warp] = __popc(valid[j] & ~ones[j]);
     }
+    if (!pre) {
+        for (int o = 16; o; o >>= 1) {
+            before += __shfl_xor_sync(0xffffffffu, before, o);
+            total += __shfl_xor_sync(0xffffffffu, total, o);
+        }
+        if (lane == 0) {
+            s_base[warp] = before;
+            s_base[kThreads / 32 + warp] = total;
+        }
+    }
+    if (tid == 0 && tz_clear) tz_clear[blockIdx.x] = 0;
     __syncthreads();
     if (warp == 0) {  // exclusive scan of the 128 (round, warp) counts, in position order
         uint32_t a[4], sum = 0;
@@ -176,7 +208,20 @@ wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xs
         }
     }
     __syncthreads();
-    const uint32_t base0 = pre[blockIdx.x], Z = *Zl;
+    uint32_t base0, Z;
+    if (pre) {
+        base0 = __ldg(pre + blockIdx.x);
+        Z = *Zl;
+    } else {
+        base0 = 0;
+        Z = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            base0 += s_base[w];
+            Z += s_base[kThreads / 32 + w];
+        }
+        if (blockIdx.x == 0 && tid == 0) *Zl = Z;
+    }
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < kRounds; ++j) {
@@ -252,19 +297,16 @@ __device__ __forceinline__ void emit(const float* x, float* med, float* y, int64
     if (med) med[i] = m;
 }
 
-// Windows inside the series: outputs [i0, i1) with i0 >= h and i1 <= n - h.
-__global__ void __launch_bounds__(kQueryThreads)
-wm_median_kernel(const float* x, int64_t i0, int64_t i1, int64_t h, Matrix M, float* med,
-                 float* y) {
-    __shared__ uint32_t sZ[kLevels];
-    if (threadIdx.x < kLevels) sZ[threadIdx.x] = M.Z[threadIdx.x];
-    __syncthreads();
-    const int64_t base = i0 + (int64_t)blockIdx.x * (kQueryThreads * kQueryILP) + threadIdx.x;
+// Windows inside the series, outputs [e0, e1) with e0 >= h and e1 <= n - h: four per
+// thread, their 32 levels interleaved.
+__device__ __forceinline__ void median_inner(const float* x, int64_t base, int64_t e1, int64_t h,
+                                             const Matrix& M, const uint32_t* sZ, float* med,
+                                             float* y) {
     uint32_t l[kQueryILP], r[kQueryILP], k[kQueryILP], key[kQueryILP];
 #pragma unroll
     for (int u = 0; u < kQueryILP; ++u) {
         const int64_t i = base + u * kQueryThreads;
-        const bool act = i < i1;
+        const bool act = i < e1;
         l[u] = act ? (uint32_t)(i - h) : 0u;
         r[u] = act ? (uint32_t)(i + h + 1) : 0u;
         k[u] = (uint32_t)h;
@@ -292,23 +334,16 @@ wm_median_kernel(const float* x, int64_t i0, int64_t i1, int64_t h, Matrix M, fl
 #pragma unroll
     for (int u = 0; u < kQueryILP; ++u) {
         const int64_t i = base + u * kQueryThreads;
-        if (i < i1) emit(x, med, y, i, key_float(key[u]));
+        if (i < e1) emit(x, med, y, i, key_float(key[u]));
     }
 }
 
-// Windows that reach past an end: outputs [0, e0) and [e1, n).  The window of i is the
-// clamped range [max(i - h, 0), min(i + h + 1, n)) plus c0 copies of x[0] and c1 of
-// x[n-1]; its k-th smallest is placed among those copies by two counts.
-__global__ void __launch_bounds__(kQueryThreads)
-wm_median_edge_kernel(const float* x, int64_t n, int64_t h, int64_t e0, int64_t e1, Matrix M,
-                      const uint32_t* ends, float* med, float* y) {
-    __shared__ uint32_t sZ[kLevels];
-    if (threadIdx.x < kLevels) sZ[threadIdx.x] = M.Z[threadIdx.x];
-    __syncthreads();
-    const int64_t t = (int64_t)blockIdx.x * kQueryThreads + threadIdx.x;
-    const int64_t nedge = e0 + (n - e1);
-    if (t >= nedge) return;
-    const int64_t i = t < e0 ? t : e1 + (t - e0);
+// A window that reaches past an end: the clamped range [max(i - h, 0), min(i + h + 1, n))
+// plus c0 copies of x[0] and c1 of x[n-1]; its k-th smallest is placed among the copies
+// by counts of the range's keys below each end key.
+__device__ __forceinline__ void median_edge(const float* x, int64_t n, int64_t h, int64_t i,
+                                            const Matrix& M, const uint32_t* sZ,
+                                            const uint32_t* ends, float* med, float* y) {
     const int64_t lo = i - h, hi = i + h + 1;
     const uint32_t l = (uint32_t)(lo < 0 ? 0 : lo), r = (uint32_t)(hi > n ? n : hi);
     uint32_t c0 = (uint32_t)(lo < 0 ? -lo : 0), c1 = (uint32_t)(hi > n ? hi - n : 0);
@@ -336,10 +371,29 @@ wm_median_edge_kernel(const float* x, int64_t n, int64_t h, int64_t e0, int64_t 
     emit(x, med, y, i, key_float(key));
 }
 
+// One launch for all outputs: the first `edge_blocks` CTAs take the outputs whose window
+// reaches past an end, [0, e0) and [e1, n), one per thread (their three traversals run
+// beside the inner CTAs); the others take [e0, e1).
+__global__ void __launch_bounds__(kQueryThreads)
+wm_median_kernel(const float* x, int64_t n, int64_t h, int64_t e0, int64_t e1,
+                 int64_t edge_blocks, Matrix M, const uint32_t* ends, float* med, float* y) {
+    __shared__ uint32_t sZ[kLevels];
+    if (threadIdx.x < kLevels) sZ[threadIdx.x] = M.Z[threadIdx.x];
+    __syncthreads();
+    if ((int64_t)blockIdx.x < edge_blocks) {
+        const int64_t t = (int64_t)blockIdx.x * kQueryThreads + threadIdx.x;
+        if (t < e0 + (n - e1)) median_edge(x, n, h, t < e0 ? t : e1 + (t - e0), M, sZ, ends, med, y);
+        return;
+    }
+    const int64_t base =
+        e0 + ((int64_t)blockIdx.x - edge_blocks) * (kQueryThreads * kQueryILP) + threadIdx.x;
+    median_inner(x, base, e1, h, M, sZ, med, y);
+}
+
 struct Workspace {
     uint32_t* keys[2];
     uint2* dir;
-    uint32_t* tz[2];
+    uint32_t* tz[3];
     uint32_t* pre;
     uint32_t* Z;
     uint32_t* ends;
@@ -365,6 +419,7 @@ Workspace layout(int64_t n, char* base) {
     w.dir = reinterpret_cast<uint2*>(take(8 * (size_t)w.nwords * kLevels));
     w.tz[0] = reinterpret_cast<uint32_t*>(take(4 * (size_t)w.ntiles));
     w.tz[1] = reinterpret_cast<uint32_t*>(take(4 * (size_t)w.ntiles));
+    w.tz[2] = reinterpret_cast<uint32_t*>(take(4 * (size_t)w.ntiles));
     w.pre = reinterpret_cast<uint32_t*>(take(4 * (size_t)w.ntiles));
     w.Z = reinterpret_cast<uint32_t*>(take(4 * kLevels));
     w.ends = reinterpret_cast<uint32_t*>(take(8));
@@ -410,37 +465,33 @@ extern "C" ffa_status ffa_running_median(const float* d_x, int64_t n, int64_t wi
     {
         // 32 levels: per level, reads and writes of the keys and the directory words
         LaunchScope ls(ffa::kMedianBuild, (double)kLevels * (8.0 * n + 8.0 * W.nwords), st);
-        wm_count_kernel<<<W.ntiles, kThreads, 0, st>>>(d_x, n, W.tz[0], W.ends);
+        wm_count_kernel<<<W.ntiles, kThreads, 0, st>>>(d_x, n, W.tz[0], W.tz[1], W.ends);
+        const bool scan = W.ntiles > kFusedPrefixMaxTiles;
         for (int L = 0; L < kLevels; ++L) {
             const bool last = L == kLevels - 1;
-            uint32_t* tz = W.tz[L & 1];
-            uint32_t* tzn = last ? nullptr : W.tz[(L + 1) & 1];
-            wm_scan_kernel<<<1, kScanThreads, 0, st>>>(tz, W.ntiles, W.pre, W.Z + L, tzn);
+            uint32_t* tz = W.tz[L % 3];
+            if (scan) wm_scan_kernel<<<1, kScanThreads, 0, st>>>(tz, W.ntiles, W.pre, W.Z + L);
             wm_scatter_kernel<<<W.ntiles, kThreads, 0, st>>>(
                 L ? W.keys[(L - 1) & 1] : nullptr, L ? nullptr : d_x,
-                last ? nullptr : W.keys[L & 1], n, kLevels - 1 - L, W.pre, W.Z + L,
-                W.dir + (size_t)L * W.nwords, tzn);
+                last ? nullptr : W.keys[L & 1], n, kLevels - 1 - L, W.ntiles, tz,
+                scan ? W.pre : nullptr, W.Z + L, W.dir + (size_t)L * W.nwords,
+                last ? nullptr : W.tz[(L + 1) % 3], last ? nullptr : W.tz[(L + 2) % 3]);
         }
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_err(e, "build launch");
     }
     const Matrix M{W.dir, W.nwords, W.Z};
-    // outputs whose window lies inside the series: [h, n - h)
+    // outputs whose window lies inside the series: [e0, e1) = [h, n - h)
     const int64_t e0 = h < n ? h : n;
     const int64_t e1 = n - h > e0 ? n - h : e0;
     {
         LaunchScope ls(ffa::kMedianQuery, 4.0 * n * ((d_med ? 1 : 0) + (d_y ? 2 : 0)), st);
-        if (e1 > e0) {
-            const int64_t per = (int64_t)kQueryThreads * kQueryILP;
-            const int64_t blocks = (e1 - e0 + per - 1) / per;
-            wm_median_kernel<<<(unsigned)blocks, kQueryThreads, 0, st>>>(d_x, e0, e1, h, M, d_med,
-                                                                        d_y);
-        }
         const int64_t nedge = e0 + (n - e1);
-        if (nedge > 0)
-            wm_median_edge_kernel<<<(unsigned)((nedge + kQueryThreads - 1) / kQueryThreads),
-                                    kQueryThreads, 0, st>>>(d_x, n, h, e0, e1, M, W.ends, d_med,
-                                                            d_y);
+        const int64_t eb = (nedge + kQueryThreads - 1) / kQueryThreads;
+        const int64_t per = (int64_t)kQueryThreads * kQueryILP;
+        const int64_t ib = (e1 - e0 + per - 1) / per;
+        wm_median_kernel<<<(unsigned)(eb + ib), kQueryThreads, 0, st>>>(d_x, n, h, e0, e1, eb, M,
+                                                                      W.ends, d_med, d_y);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_err(e, "query launch");
     }

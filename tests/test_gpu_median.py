@@ -2,6 +2,7 @@
 ABI: the medians are samples of the window, so the comparison is bit-exact, and so is
 y = x - med (one float subtraction on both sides).  Sizes span several build tiles of
 4096 samples and ragged tails, windows longer than the series, ties, in-place output,
+series of more than 4096 tiles (the build's scan launch),
 and the full size of a 2^23-sample series at 64 us with a 1 s window (15625 samples)
 on sampled outputs, including every output whose window reaches past an end."""
 import numpy as np
@@ -85,6 +86,21 @@ def test_full_size_survey_window(F):
     np.testing.assert_array_equal(med[at], ref)
     np.testing.assert_array_equal(y[at], x[at] - ref)
     assert np.isfinite(med).all()
+
+
+def test_series_longer_than_4096_tiles(F):
+    """More than 4096 build tiles of 4096 samples: the per-level tile prefix comes from
+    the one-CTA scan launch instead of each scatter CTA's own sum."""
+    n, w = 4096 * 4096 + 4097, 101
+    x = synth.rng(31).standard_normal(n).astype(np.float32)
+    med, y = _run(F, x, w)
+    r = synth.rng(32)
+    at = np.unique(np.concatenate([np.arange(0, 100), np.arange(n - 100, n),
+                                   np.arange(4096 * 4096 - 50, 4096 * 4096 + 50),
+                                   r.integers(0, n, 2000)]))
+    ref = oracle.running_median(x, w, at=at)
+    np.testing.assert_array_equal(med[at], ref)
+    np.testing.assert_array_equal(y[at], x[at] - ref)
 
 
 def test_deredden_then_normalise(F):
