@@ -19,10 +19,13 @@ Paper passages followed (sections and equations of the paper):
   * normalise ....... Sec. 3.1, Sec. 5.2 (zero mean, unit std from the whole series)
   * running median .. Sec. 5.2 (de-reddening: subtract a running median, odd window,
                       the series extended by its end samples)
+  * peak finding .... Sec. 5.5, Fig. 6 (per width: robust median/IQR threshold per
+                      frequency segment, polynomial fit in log frequency, clustering)
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -295,3 +298,85 @@ def periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths, select=None,
     if got != cap:
         raise ValueError("oracle periodogram failed (%d)" % got)
     return Periodogram(periods, fb, snr)
+
+
+# ----------------------------------------------------------------------------------
+# Peak finding (Sec. 5.5, Fig. 6).  Written with numpy steps (a percentile, a
+# least-squares polynomial fit, a sort) in the paper's order.  Readings where the paper
+# leaves a choice:
+#   - trial frequencies nu = 1 / P; segments of width dzseg / T start at the lowest
+#     trial frequency; segment j holds floor((nu - nu_lo) / width) == j (the highest
+#     frequency falls in the last segment); its control frequency is its centre;
+#   - median and quartiles are the linear-interpolation percentiles 50, 25 and 75
+#     (virtual index q (c - 1)); sigma = IQR / 1.349; s = median + nsigma * sigma;
+#   - segments with fewer than min_seg trials give no control point; a width with fewer
+#     than degree + 1 control points has no threshold and no peaks;
+#   - the threshold is the least-squares polynomial of the given degree in the natural
+#     log of frequency; a trial is selected when its S/N is strictly above it;
+#   - selected trials are taken in order of decreasing frequency; a new peak starts
+#     where the frequency gap to the previous selected trial exceeds clrad / T; a peak
+#     is its brightest member (the lowest trial index among equal S/N).
+# ----------------------------------------------------------------------------------
+PEAK_DEFAULTS = dict(dzseg=5.0, nsigma=6.0, degree=2, clrad=1.0, min_seg=8)
+
+
+@dataclass
+class PeakWidth:
+    ctrl_nu: np.ndarray      # control-point frequencies (Hz)
+    ctrl_s: np.ndarray       # control-point thresholds m + k sigma
+    coef: Optional[np.ndarray]  # polynomial in ln(nu), highest power first (np.polyval)
+    threshold: Optional[np.ndarray]  # per trial, or None
+    peaks: np.ndarray        # trial indices of the peaks, in order of increasing period
+
+
+def segment_controls(nu: np.ndarray, snr_w: np.ndarray, tobs: float, dzseg: float,
+                     nsigma: float, min_seg: int):
+    """Control points (nu_j, s_j) of one width's periodogram (Sec. 5.5): frequency
+    segments of dzseg / T, robust median and IQR-based sigma in each."""
+    width = dzseg / tobs
+    lo, hi = nu.min(), nu.max()
+    nseg = max(1, int(math.ceil((hi - lo) / width)))
+    j = np.minimum(np.floor((nu - lo) / width).astype(np.int64), nseg - 1)
+    cn, cs = [], []
+    for k in range(nseg):
+        v = snr_w[j == k].astype(np.float64)
+        if len(v) < min_seg:
+            continue
+        q25, q50, q75 = np.percentile(v, [25.0, 50.0, 75.0], method="linear")
+        cn.append(lo + (k + 0.5) * width)
+        cs.append(q50 + nsigma * ((q75 - q25) / 1.349))
+    return np.array(cn), np.array(cs)
+
+
+def find_peaks(periods: np.ndarray, snr: np.ndarray, tobs: float, **opts):
+    """Sec. 5.5 peak detection on a two-dimensional periodogram (trials x widths), each
+    width separately.  Returns one PeakWidth per width."""
+    o = dict(PEAK_DEFAULTS)
+    o.update(opts)
+    P = np.asarray(periods, dtype=np.float64)
+    S = np.asarray(snr)
+    if S.ndim == 1:
+        S = S[:, None]
+    nu = 1.0 / P
+    out = []
+    for iw in range(S.shape[1]):
+        sw = S[:, iw].astype(np.float64)
+        cn, cs = segment_controls(nu, sw, tobs, o["dzseg"], o["nsigma"], o["min_seg"])
+        if len(cn) < o["degree"] + 1:
+            out.append(PeakWidth(cn, cs, None, None, np.zeros(0, np.int64)))
+            continue
+        coef = np.polyfit(np.log(cn), cs, o["degree"])
+        thr = np.polyval(coef, np.log(nu))
+        sel = np.flatnonzero(sw > thr)
+        order = sel[np.argsort(-nu[sel], kind="stable")]   # decreasing frequency
+        peaks = []
+        gap = o["clrad"] / tobs
+        start = 0
+        for e in range(1, len(order) + 1):
+            if e == len(order) or nu[order[e - 1]] - nu[order[e]] > gap:
+                members = order[start:e]
+                best = members[np.lexsort((members, -sw[members]))[0]]
+                peaks.append(best)
+                start = e
+        out.append(PeakWidth(cn, cs, coef, thr, np.array(peaks, np.int64)))
+    return out
