@@ -144,7 +144,7 @@ wm_scan_kernel(const uint32_t* __restrict__ tz, int ntiles, uint32_t* __restrict
 // from `pre` and `Zl` when a scan ran (large series); otherwise every CTA sums the tile
 // counts `tz` itself and CTA 0 stores Z_L.  The count buffer of level L + 2 is cleared
 // here (level L + 1 adds into tz_next, and level L - 1 read tz_clear).
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xsrc,
                   uint32_t* __restrict__ dst, int64_t n, int bit, int ntiles,
                   const uint32_t* __restrict__ tz, const uint32_t* __restrict__ pre,
@@ -163,6 +163,7 @@ wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xs
     }
     uint32_t before = 0, total = 0;  // zeros of the tiles before this one, and of all
     if (!pre) {
+#pragma unroll 4
         for (int i = tid; i < ntiles; i += kThreads) {
             const uint32_t c = __ldg(tz + i);
             total += c;
@@ -223,6 +224,11 @@ wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xs
         if (blockIdx.x == 0 && tid == 0) *Zl = Z;
     }
     const uint32_t lt = (1u << lane) - 1u;
+    // This tile's zeros land in one run of A_{L+1} starting at base0, its ones in one run
+    // starting at Z + t0 - base0; each run (<= 4096 keys) meets at most two destination
+    // tiles.  cnt[c] counts the keys whose next bit is 0, c = 2 * side + (second tile).
+    const uint32_t tz_first = base0 / kTile, to_first = (Z + (uint32_t)t0 - base0) / kTile;
+    uint32_t cnt[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int j = 0; j < kRounds; ++j) {
         const uint32_t zw = base0 + s_z[j * (kThreads / 32) + warp];  // zeros before the word
@@ -230,19 +236,33 @@ wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xs
         if (lane == 0 && w0 < n) dir[w0 >> 5] = make_uint2(zw, ones[j]);
         if (!dst) continue;
         const bool v = (valid[j] >> lane) & 1u;
+        const bool one = (ones[j] >> lane) & 1u;
         uint32_t d = 0;
         if (v) {
             const uint32_t z = zw + __popc(valid[j] & ~ones[j] & lt);  // zeros before me
-            d = ((ones[j] >> lane) & 1u) ? Z + (uint32_t)(w0 + lane) - z : z;
+            d = one ? Z + (uint32_t)(w0 + lane) - z : z;
             dst[d] = key[j];
         }
         const bool nz = v && !((key[j] >> (bit - 1)) & 1u);
-        const uint32_t tile = nz ? d / kTile : 0xffffffffu;
-        const uint32_t grp = __match_any_sync(0xffffffffu, tile);
-        if (nz && lane == __ffs(grp) - 1) atomicAdd(tz_next + tile, (uint32_t)__popc(grp));
+        const bool second = d / kTile != (one ? to_first : tz_first);
+        cnt[0] += __popc(__ballot_sync(0xffffffffu, nz && !one && !second));
+        cnt[1] += __popc(__ballot_sync(0xffffffffu, nz && !one && second));
+        cnt[2] += __popc(__ballot_sync(0xffffffffu, nz && one && !second));
+        cnt[3] += __popc(__ballot_sync(0xffffffffu, nz && one && second));
     }
     if ((n & 31) == 0 && blockIdx.x == gridDim.x - 1 && tid == 0)
         dir[n >> 5] = make_uint2(Z, 0u);  // rank0(n) when n ends a word
+    if (!dst) return;
+    __shared__ uint32_t s_cnt[4];
+    if (tid < 4) s_cnt[tid] = 0;
+    __syncthreads();
+    if (lane < 4)  // the counts are warp-uniform: lane c adds count c
+        atomicAdd(s_cnt + lane, lane == 0 ? cnt[0] : lane == 1 ? cnt[1] : lane == 2 ? cnt[2] : cnt[3]);
+    __syncthreads();
+    if (tid < 4 && s_cnt[tid]) {
+        const uint32_t tile = ((tid >> 1) ? to_first : tz_first) + (tid & 1);
+        atomicAdd(tz_next + tile, s_cnt[tid]);
+    }
 }
 
 struct Matrix {
