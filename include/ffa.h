@@ -158,6 +158,59 @@ ffa_status ffa_running_median(const float* d_x, int64_t n, int64_t width, float*
                               float* d_y, void* d_ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------------------------
+ * Peak finding on a periodogram (paper Sec. 5.5, Fig. 6), each width on its own.
+ * With nu = 1 / P the trial frequencies and T = tobs the series length in seconds:
+ *   - segments of dzseg / T cover [nu_lo, nu_hi] from the lowest trial frequency;
+ *     segment j holds the trials with floor((nu - nu_lo) / (dzseg / T)) = j (the
+ *     highest frequency falls in the last segment);
+ *   - a segment of >= min_seg trials gives the control point
+ *       (nu_lo + (j + 1/2) dzseg / T,  m + nsigma * (q75 - q25) / 1.349),
+ *     m, q25, q75 the 50th, 25th and 75th percentiles of its S/N, interpolated linearly
+ *     between order statistics (virtual index c q + (1 - q) - 1 for c values);
+ *   - the threshold is the least-squares polynomial of the given degree in ln(nu)
+ *     through the control points (none, and no peaks, with fewer than degree + 1);
+ *   - the trials with S/N strictly above it, taken in order of decreasing frequency,
+ *     form one peak until the frequency gap to the previous one exceeds clrad / T;
+ *     a peak is reported as its brightest trial (the lowest index among equal S/N).
+ * d_periods: ntrials doubles (device), positive and non-decreasing (the order of every
+ * periodogram of this library).  d_snr: ntrials x nw floats (device, row-major).
+ * d_peaks: peak_cap records (device), written width by width and, within a width, in
+ * order of increasing period; peaks beyond peak_cap are counted but not written.
+ * d_npeaks: nw + 1 int64 (device): peaks per width, then their total.
+ * opts: NULL for the defaults (ffa_peak_opts_default).  Workspace:
+ * ffa_find_peaks_workspace bytes (about 12 bytes per trial and width, plus
+ * 16 * max_segments * nw).  Asynchronous; a device-side rejection (periods not
+ * positive and non-decreasing: bit 16; more than max_segments segments: bit 4; a
+ * segment of more than 16384 trials: bit 8, that segment gives no control point)
+ * shows in ffa_check(d_ws), and a rejected call finds no peaks.
+ * Errors: FFA_ERR_ARG (null pointers, ntrials outside [1, 2^32 - 1], nw outside
+ *         [1, 64], tobs <= 0, bad options), FFA_ERR_CAPACITY (workspace too small).
+ * ---------------------------------------------------------------------------- */
+typedef struct ffa_peak_opts {
+    double dzseg;          /* segment width in units of 1/T (default 5)            */
+    double nsigma;         /* k of the control points m + k sigma (default 6)       */
+    double clrad;          /* peak-clustering radius in units of 1/T (default 1)    */
+    int32_t degree;        /* polynomial degree, 0..6 (default 2)                   */
+    int32_t min_seg;       /* trials a segment needs for a control point (8)        */
+    int64_t max_segments;  /* workspace bound on the segment count (65536)          */
+} ffa_peak_opts;
+
+typedef struct ffa_peak {
+    int64_t trial;   /* trial index in the periodogram                               */
+    double period;   /* its period (s)                                               */
+    float snr;       /* its S/N                                                      */
+    int32_t iw;      /* width index                                                  */
+} ffa_peak;
+
+void ffa_peak_opts_default(ffa_peak_opts* opts);
+ffa_status ffa_find_peaks_workspace(int64_t ntrials, int32_t nw, const ffa_peak_opts* opts,
+                                    size_t* bytes);
+ffa_status ffa_find_peaks(const double* d_periods, const float* d_snr, int64_t ntrials,
+                          int32_t nw, double tobs, const ffa_peak_opts* opts,
+                          ffa_peak* d_peaks, int64_t peak_cap, int64_t* d_npeaks, void* d_ws,
+                          size_t ws_bytes, void* stream);
+
+/* ------------------------------------------------------------------------------
  * Periodogram search plan (paper Sec. 5.3, Fig. 4; Sec. 5.6 for the first factor).
  *   f0 = pmin / (bmin * tsamp) (must be >= 1), fg = (bmax + 1) / bmin,
  *   octave k: factor F_k = f0 * fg^k while bmin * tsamp * F_k <= pmax,

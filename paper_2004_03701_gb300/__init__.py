@@ -15,6 +15,7 @@ Calls (names follow include/ffa.h and the paper, Morello et al. 2020):
   BatchSearcher(series, widths)                 many series in one buffer, Sec. 5.7
   SegmentSearcher(n, tsamp, segments, widths)   dynamic duty-cycle resolution, Sec. 5.6
   running_median(x, width), deredden(x, width)  de-reddening before normalising, Sec. 5.2
+  find_peaks(periods, snr, tobs)                peak finding per width, Sec. 5.5, Fig. 6
 """
 from __future__ import annotations
 
@@ -32,6 +33,7 @@ __all__ = [
     "Tiles", "tile_candidates", "tune", "tune_periodogram", "SegmentSearcher",
     "check", "plan_cache_clear", "launch_count", "kernel_names", "profile_enable", "profile_reset",
     "profile_query", "RunningMedian", "running_median", "deredden", "median_width",
+    "PeakFinder", "find_peaks", "PEAK_DTYPE",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -66,6 +68,16 @@ class _Series(ctypes.Structure):
     _fields_ = [("offset", ctypes.c_int64), ("n", ctypes.c_int64), ("tsamp", ctypes.c_double),
                 ("pmin", ctypes.c_double), ("pmax", ctypes.c_double), ("bmin", ctypes.c_int32),
                 ("bmax", ctypes.c_int32)]
+
+
+class _PeakOpts(ctypes.Structure):
+    _fields_ = [("dzseg", ctypes.c_double), ("nsigma", ctypes.c_double),
+                ("clrad", ctypes.c_double), ("degree", ctypes.c_int32),
+                ("min_seg", ctypes.c_int32), ("max_segments", ctypes.c_int64)]
+
+
+# one ffa_peak record
+PEAK_DTYPE = np.dtype([("trial", "<i8"), ("period", "<f8"), ("snr", "<f4"), ("iw", "<i4")])
 
 
 class _BatchInfo(ctypes.Structure):
@@ -120,6 +132,11 @@ def library() -> ctypes.CDLL:
                                         sz, vp]
     L.ffa_normalise_workspace.argtypes = [i64, ctypes.POINTER(sz)]
     L.ffa_normalise.argtypes = [vp, i64, vp, i32, vp, vp, sz, vp]
+    L.ffa_peak_opts_default.restype = None
+    L.ffa_peak_opts_default.argtypes = [ctypes.POINTER(_PeakOpts)]
+    L.ffa_find_peaks_workspace.argtypes = [i64, i32, ctypes.POINTER(_PeakOpts), ctypes.POINTER(sz)]
+    L.ffa_find_peaks.argtypes = [vp, vp, i64, i32, dbl, ctypes.POINTER(_PeakOpts), vp, i64, vp,
+                                 vp, sz, vp]
     L.ffa_running_median_workspace.argtypes = [i64, ctypes.POINTER(sz)]
     L.ffa_running_median.argtypes = [vp, i64, i64, vp, vp, vp, sz, vp]
     L.ffa_launch_count.restype = i64
@@ -136,7 +153,8 @@ def library() -> ctypes.CDLL:
               "ffa_periodogram_batch", "ffa_plan_cache_clear", "ffa_periodogram_plan_opts",
               "ffa_periodogram_opts", "ffa_batch_plan_opts", "ffa_periodogram_batch_opts",
               "ffa_boxcar_snr_template", "ffa_running_median_workspace",
-              "ffa_running_median", "ffa_profile_query"):
+              "ffa_running_median", "ffa_find_peaks_workspace", "ffa_find_peaks",
+              "ffa_profile_query"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -259,6 +277,66 @@ def deredden(x, width: int, inplace: bool = False, stream=None):
     y = x if inplace else _torch().empty_like(x)
     RunningMedian(x.numel(), width, x.device)(x, y=y, stream=stream)
     return y
+
+
+class PeakFinder:
+    """Peak finding on periodograms of `ntrials` trials and `nw` widths (Sec. 5.5,
+    Fig. 6), with its workspace and output buffers kept across calls.
+
+    ``F(periods, snr)`` searches a periodogram on the device (float64 periods, positive
+    and non-decreasing; float32 S/N of shape (ntrials, nw)), asynchronously on the
+    current stream.  ``F.result()`` synchronises and returns the peaks (a numpy array of
+    PEAK_DTYPE: width by width, by increasing period within a width) and the number of
+    peaks per width.  Options as in ffa_peak_opts; `peak_cap` bounds the stored peaks."""
+
+    def __init__(self, ntrials: int, nw: int, tobs: float, dzseg: float = 5.0,
+                 nsigma: float = 6.0, degree: int = 2, clrad: float = 1.0, min_seg: int = 8,
+                 max_segments: int = 1 << 16, peak_cap: Optional[int] = None, device="cuda"):
+        torch = _torch()
+        L = library()
+        self.opts = _PeakOpts(float(dzseg), float(nsigma), float(clrad), int(degree),
+                              int(min_seg), int(max_segments))
+        need = ctypes.c_size_t()
+        _check(L.ffa_find_peaks_workspace(int(ntrials), int(nw), ctypes.byref(self.opts),
+                                          ctypes.byref(need)))
+        self.ntrials, self.nw, self.tobs = int(ntrials), int(nw), float(tobs)
+        self.device = torch.device(device)
+        self.ws = _workspace(need.value, self.device)
+        self.cap = int(peak_cap) if peak_cap is not None else max(1024, 4 * self.ntrials // 1000)
+        self.peaks = torch.empty(max(self.cap, 1) * PEAK_DTYPE.itemsize, dtype=torch.uint8,
+                                 device=self.device)
+        self.npeaks = torch.zeros(self.nw + 1, dtype=torch.int64, device=self.device)
+
+    def __call__(self, periods, snr, stream=None):
+        torch = _torch()
+        _dev_tensor(periods, "periods")
+        _dev_tensor(snr, "snr")
+        if periods.dtype != torch.float64 or periods.numel() != self.ntrials:
+            raise TypeError("periods must be %d float64 values" % self.ntrials)
+        if snr.dtype != torch.float32 or snr.numel() != self.ntrials * self.nw:
+            raise TypeError("snr must be %d x %d float32 values" % (self.ntrials, self.nw))
+        _check(library().ffa_find_peaks(
+            _vp(periods), _vp(snr), self.ntrials, self.nw, self.tobs, ctypes.byref(self.opts),
+            _vp(self.peaks), self.cap, _vp(self.npeaks), _vp(self.ws), self.ws.numel(),
+            _stream_handle(stream)))
+
+    def check(self, stream=None) -> None:
+        _check(library().ffa_check(_vp(self.ws), _stream_handle(stream)))
+
+    def result(self):
+        counts = self.npeaks.cpu().numpy()
+        k = int(min(counts[-1], self.cap))
+        raw = self.peaks[:k * PEAK_DTYPE.itemsize].cpu().numpy()
+        return raw.view(PEAK_DTYPE).copy(), counts[:-1].copy()
+
+
+def find_peaks(periods, snr, tobs: float, **opts):
+    """Peaks of a periodogram (Sec. 5.5): returns (peaks, counts per width); see
+    PeakFinder for the options."""
+    snr2 = snr if snr.dim() == 2 else snr.reshape(-1, 1)
+    F = PeakFinder(periods.numel(), snr2.shape[1], tobs, device=periods.device, **opts)
+    F(periods, snr2)
+    return F.result()
 
 
 def downsample(x, factor: float, stream=None):

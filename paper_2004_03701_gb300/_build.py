@@ -11,7 +11,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libffa.so")
-SOURCES = ["ffa_kernels.cu", "ffa_api.cu", "ffa_noalloc.cu", "ffa_median.cu"]
+SOURCES = ["ffa_kernels.cu", "ffa_api.cu", "ffa_noalloc.cu", "ffa_median.cu",
+           "ffa_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr",
          "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "-I" + INCLUDE, "-I" + CSRC]

@@ -72,7 +72,7 @@ const char* kKindNames[kAllKinds] = {"prefix_partial", "prefix_top",     "prefix
                                      "downsample",     "ffa_bottom",     "ffa_bottom_snr",
                                      "ffa_top",        "boxcar_snr",     "normalise",
                                      "ffa_persistent", "top_prep",       "median_build",
-                                     "median_query"};
+                                     "median_query",   "peaks"};
 
 cudaEvent_t pool_get() {
     if (!g_pool.empty()) {

@@ -102,7 +102,7 @@ def test_other_calls_reject_bad_arguments(lib):
 def test_kernel_kinds(lib):
     names = ffa.kernel_names()
     assert "ffa_bottom" in names and "ffa_top" in names and "downsample" in names
-    assert "median_build" in names and "median_query" in names
+    assert "median_build" in names and "median_query" in names and "peaks" in names
 
 
 def test_running_median_rejects_bad_arguments(lib):
@@ -126,6 +126,35 @@ def test_running_median_rejects_bad_arguments(lib):
     assert call(fake, n, 15, fake, None, ctypes.c_void_p(260), need, None) == 1  # alignment
     assert call(fake, n, 15, fake, None, fake, need - 1, None) == 2   # workspace too small
     assert len(lib.ffa_last_error()) > 0
+
+
+def test_find_peaks_rejects_bad_arguments(lib):
+    o = ffa._PeakOpts()
+    lib.ffa_peak_opts_default(ctypes.byref(o))
+    assert (o.dzseg, o.nsigma, o.clrad, o.degree, o.min_seg, o.max_segments) == \
+        (5.0, 6.0, 1.0, 2, 8, 65536)
+    sz = ctypes.c_size_t()
+    assert lib.ffa_find_peaks_workspace(662440, 11, None, ctypes.byref(sz)) == 0
+    need = sz.value
+    assert need >= 12 * 662440 * 11
+    assert lib.ffa_find_peaks_workspace(0, 11, None, ctypes.byref(sz)) == 1
+    assert lib.ffa_find_peaks_workspace(10, 65, None, ctypes.byref(sz)) == 1
+    for field, bad in (("dzseg", 0.0), ("clrad", -1.0), ("degree", 7), ("degree", -1),
+                       ("min_seg", 0), ("max_segments", 0)):
+        b = ffa._PeakOpts()
+        lib.ffa_peak_opts_default(ctypes.byref(b))
+        setattr(b, field, bad)
+        assert lib.ffa_find_peaks_workspace(10, 2, ctypes.byref(b), ctypes.byref(sz)) == 1, field
+    fake = ctypes.c_void_p(256)   # never dereferenced: rejected on the host first
+    call = lib.ffa_find_peaks
+    n = 662440
+    assert call(None, fake, n, 11, 537.0, None, fake, 10, fake, fake, need, None) == 1
+    assert call(fake, fake, n, 11, 0.0, None, fake, 10, fake, fake, need, None) == 1   # tobs
+    assert call(fake, fake, n, 11, 537.0, None, None, 10, fake, fake, need, None) == 1  # no out
+    assert call(fake, fake, n, 11, 537.0, None, fake, -1, fake, fake, need, None) == 1
+    assert call(fake, fake, n, 11, 537.0, None, fake, 10, fake, ctypes.c_void_p(264), need,
+                None) == 1                                                            # alignment
+    assert call(fake, fake, n, 11, 537.0, None, fake, 10, fake, fake, need - 1, None) == 2
 
 
 def test_median_width():
