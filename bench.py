@@ -14,7 +14,10 @@ periods 0.1-10 s, bins 480-520, 16 widths, normalised and stored as int8).  --st
 f16 / i8 stores the normalised input at reduced precision (sums stay FP32).
 --workload deredden times the step before the search instead: the running-median
 de-reddening of Sec. 5.2 on a 2^23-sample red-noise series at 64 us with a 1 s window
-(15625 samples); its metric is samples de-reddened per second.
+(15625 samples); its metric is samples de-reddened per second.  --workload peaks times
+the step after it: the peak finding of Sec. 5.5 on the survey periodogram (662,440
+trials x 11 widths, computed once before the timed steps); its metric is periodogram
+entries (trials x widths) searched per second.
 
 metric: time-series samples searched per second = samples / (device time of one step),
 summed over GPUs.  Each GPU searches its own series (independent; no collective is in
@@ -64,7 +67,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ffa", "reference"], default="ffa")
     ap.add_argument("--workload",
-                    choices=["survey", "plain_small", "deredden"] + list(BATCH_WORKLOADS),
+                    choices=["survey", "plain_small", "deredden", "peaks"] + list(BATCH_WORKLOADS),
                     default="survey")
     ap.add_argument("--storage", choices=["f32", "f16", "i8"], default=None,
                     help="input storage (default f32; i8 for batch_int8)")
@@ -727,6 +730,148 @@ def run_deredden(a):
         torch.distributed.destroy_process_group()
 
 
+# ------------------------------------------------------------- peak finding (Sec. 5.5)
+PK_METRIC = "periodogram entries (trials x widths) searched for peaks/s (Sec. 5.5)"
+PK_UNIT = "entries/s"
+
+
+def _peak_inputs(ffa, torch, dev):
+    """The survey periodogram, computed once by the library (device arrays)."""
+    wl = synth.survey()
+    S = ffa.Searcher(len(wl.x), wl.tsamp, wl.pmin, wl.pmax, wl.bmin, wl.bmax, wl.widths,
+                     device=dev)
+    S(torch.from_numpy(wl.x).to(dev))
+    torch.cuda.synchronize()
+    return wl, S.periods.clone(), S.snr.clone()
+
+
+def run_peaks(a):
+    world, rank, local = dist_env()
+    import torch
+
+    import paper_2004_03701_gb300 as ffa
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ffa.build()
+    ffa.library()
+    wl, per, snr = _peak_inputs(ffa, torch, dev)
+    T, nw = per.numel(), snr.shape[1]
+    tobs = len(wl.x) * wl.tsamp
+    cfg = {"workload": "peaks_survey_662440x11", "ntrials": T, "widths": nw, "tobs": tobs,
+           "dzseg": 5.0, "nsigma": 6.0, "degree": 2, "clrad": 1.0, "min_seg": 8,
+           "input": "the library's periodogram of survey_fp32_2^23_64us",
+           "l2": "flushed (256 MB write) between steps",
+           "parallelism": "replicas" if world > 1 else "single"}
+    if a.impl == "reference":
+        if rank == 0:
+            import oracle
+            P, S = per.cpu().numpy(), snr.cpu().numpy()
+            times = []
+            for i in range(a.warmup + a.steps):
+                t0 = time.perf_counter()
+                oracle.find_peaks(P, S, tobs)
+                if i >= a.warmup:
+                    times.append(time.perf_counter() - t0)
+            te = statistics.mean(times)
+            value = T * nw / te
+            line = {"impl": "reference", "metric": PK_METRIC, "value": value, "unit": PK_UNIT,
+                    "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+                    "ms_per_step": te * 1e3, "higher_is_better": True, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+                    "cpu_baseline": {"value": value, "unit": PK_UNIT, "cores": 1,
+                                     "kind": "oracle", "sample": "the whole periodogram"},
+                    "e2e": {"value": value, "unit": PK_UNIT, "h2d_bytes_per_step": 0,
+                            "d2h_bytes_per_step": 0}}
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    PF = ffa.PeakFinder(T, nw, tobs, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(3, a.warmup)):
+        PF(per, snr)
+    PF.check()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        PF(per, snr)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    PF.check()
+    t_step = sum(times) / len(times)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = world * T * nw / (t_step * 1e-3)
+    peak, peak_kind = measured_peaks()
+    alg = 4.0 * T * nw + 8.0 * T   # the S/N and the periods read once
+    roofline = {"bound": "hbm", "kernel": "peaks", "achieved": alg / (t_step * 1e-3) / 1e9,
+                "peak": peak, "unit": "GB/s", "frac": alg / (t_step * 1e-3) / 1e9 / peak,
+                "traffic": None, "alg_bytes_per_launch": alg,
+                "alg_bytes_def": "4 T nw + 8 T: the periodogram's S/N and periods read once "
+                                 "(the whole peak-finding call, 8 launches, as one unit)",
+                "peak_source": peak_kind}
+    e2e = None
+    if not a.no_e2e:
+        ph = per.cpu().pin_memory()
+        sh = snr.cpu().pin_memory()
+        pd, sd = torch.empty_like(per), torch.empty_like(snr)
+        et = []
+        for i in range(a.steps + 2):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pd.copy_(ph, non_blocking=True)
+            sd.copy_(sh, non_blocking=True)
+            PF(pd, sd)
+            pk, counts = PF.result()
+            if i >= 2:
+                et.append(time.perf_counter() - t0)
+        te = sum(et) / len(et)
+        e2e = {"value": world * T * nw / te, "unit": PK_UNIT,
+               "h2d_bytes_per_step": 8 * T + 4 * T * nw,
+               "d2h_bytes_per_step": 8 * (nw + 1) + int(counts.sum()) * 24}
+    cpu = acc = None
+    pk, counts = PF.result()
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        import oracle
+        P, S = per.cpu().numpy(), snr.cpu().numpy()
+        t0 = time.perf_counter()
+        ref = oracle.find_peaks(P, S, tobs)
+        dt = time.perf_counter() - t0
+        cpu = {"value": T * nw / dt, "unit": PK_UNIT, "cores": 1, "kind": "oracle",
+               "sample": "the whole periodogram, %.2f s (numpy)" % dt}
+        want = np.concatenate([r.peaks for r in ref])
+        acc = {"peaks": int(len(pk)), "identical_to_oracle":
+               bool(np.array_equal(pk["trial"], want) and
+                    list(counts) == [len(r.peaks) for r in ref])}
+    if rank == 0:
+        line = {"metric": PK_METRIC, "value": value, "unit": PK_UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64 thresholds, f32 S/N", "data": "synthetic", "config": cfg,
+                "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "accuracy": acc,
+                "clocks": clk, "gpu_launches": 8 * a.steps, "peaks_per_width": [int(c) for c in counts]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 # ------------------------------------------------------------------------------- GPU
 def run_ffa(a):
     import torch
@@ -980,6 +1125,8 @@ def main():
     a = parse()
     if a.workload == "deredden":
         run_deredden(a)
+    elif a.workload == "peaks":
+        run_peaks(a)
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -93,15 +93,16 @@ __device__ __forceinline__ long long seg_of(double P, const Hdr& h) {
     return j < h.nseg - 1 ? j : h.nseg - 1;
 }
 
+// reduction over the block; `id` is the identity of `op` (fills the missing warps)
 template <typename T, typename Op>
-__device__ T block_reduce(T v, Op op, T* sh) {
+__device__ T block_reduce(T v, Op op, T id, T* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
     __syncthreads();
     if (lane == 0) sh[warp] = v;
     __syncthreads();
     if (warp == 0) {
-        v = lane < nwarps ? sh[lane] : sh[0];
+        v = lane < nwarps ? sh[lane] : id;
         for (int o = 16; o; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
         if (lane == 0) sh[0] = v;
     }
@@ -163,9 +164,9 @@ __global__ void __launch_bounds__(kRangeThreads) pk_range_kernel(Params p) {
         lo = nu < lo ? nu : lo;
         hi = nu > hi ? nu : hi;
     }
-    lo = block_reduce(lo, MinOp(), shd);
-    hi = block_reduce(hi, MaxOp(), shd);
-    bad = block_reduce(bad, OrOp(), shu);
+    lo = block_reduce(lo, MinOp(), (double)INFINITY, shd);
+    hi = block_reduce(hi, MaxOp(), -(double)INFINITY, shd);
+    bad = block_reduce(bad, OrOp(), 0u, shu);
     if (threadIdx.x == 0) {
         // the first launch of a call: it sets the status word, the others only add bits
         const double q = ceil(__ddiv_rn(__dsub_rn(hi, lo), p.width));
@@ -277,8 +278,8 @@ __global__ void __launch_bounds__(kFitThreads) pk_fit_kernel(Params p) {
             sx += log(c.x);
         }
     }
-    cnt = block_reduce(cnt, AddOp(), shd);
-    sx = block_reduce(sx, AddOp(), shd);
+    cnt = block_reduce(cnt, AddOp(), 0.0, shd);
+    sx = block_reduce(sx, AddOp(), 0.0, shd);
     Fit* f = p.fit + iw;
     if (cnt < (double)na) {
         if (threadIdx.x == 0) f->valid = 0;
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(kFitThreads) pk_fit_kernel(Params p) {
             sq += u * u;
         }
     }
-    sq = block_reduce(sq, AddOp(), shd);
+    sq = block_reduce(sq, AddOp(), 0.0, shd);
     const double xs = sq > 0.0 ? sqrt(sq / cnt) : 1.0;
     // pass 2: sums of u^a (a <= 2d) and u^a s (a <= d)
     double acc[3 * kMaxDegree + 3];
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kFitThreads) pk_fit_kernel(Params p) {
     for (int a = 0; a < 3 * kMaxDegree + 3; ++a) {
         const bool used = a <= 2 * d || (a >= 2 * kMaxDegree + 1 && a <= 2 * kMaxDegree + 1 + d);
         if (!used) continue;
-        const double t = block_reduce(acc[a], AddOp(), shd);
+        const double t = block_reduce(acc[a], AddOp(), 0.0, shd);
         if (threadIdx.x == 0) s_sum[a] = t;
     }
     __syncthreads();
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(kSelThreads) pk_count_kernel(Params p) {
     if (p.hdr->nseg == 0 || !f.valid) return;
     bool sel[kSelPer];
     const double k = (double)select_chunk(p, f, iw, blockIdx.x, sel);
-    const double tot = block_reduce(k, AddOp(), shd);
+    const double tot = block_reduce(k, AddOp(), 0.0, shd);
     if (threadIdx.x == 0) p.ccount[(size_t)iw * p.nchunks + blockIdx.x] = (long long)tot;
 }
 
