@@ -9,7 +9,10 @@
 // reported as its brightest trial.
 //
 // Launches (all on the caller's stream, no host synchronisation):
-//   pk_range_kernel    one CTA: frequency range, segment count, input checks;
+//   pk_prep_kernel     per trial: input checks, nu = 1 / P and ln nu, once (FP64 divides
+//                      and logarithms are slow on this GPU: nothing later repeats them);
+//   pk_range_kernel    one thread: frequency range (the ends of the sorted trials) and
+//                      segment count;
 //   pk_segment_kernel  one CTA per (segment, width): the segment's trials are one index
 //                      range (periods are non-decreasing), found by binary search; their
 //                      S/N values are sorted in shared memory (bitonic) and the quartiles
@@ -18,8 +21,8 @@
 //                      centred and scaled log frequency, solved by Gaussian elimination
 //                      with partial pivoting, in FP64;
 //   pk_count_kernel,   selection of the trials above the threshold, in chunks of 4096
-//   pk_offsets_kernel, trials per (chunk, width): counts, their prefix per width, and
-//   pk_write_kernel    the selected trials written in order;
+//   pk_offsets_kernel, trials per (chunk, width): flags and counts, their prefix per
+//   pk_write_kernel    width, and the selected trials written in order;
 //   pk_cluster_kernel  one CTA per width: peaks along the selected trials (block scans)
 //                      and the brightest trial of every peak;
 //   pk_output_kernel   one CTA: widths' peaks packed width by width into the output.
@@ -41,7 +44,7 @@ namespace {
 
 using ffa::LaunchScope;
 
-constexpr int kRangeThreads = 1024;
+constexpr int kPrepThreads = 256;
 constexpr int kSegThreads = 512;
 constexpr int kSortCap = 16384;  // trials of one segment sorted in shared memory
 constexpr int kFitThreads = 256;
@@ -69,6 +72,9 @@ struct Fit {
 
 struct Params {
     const double* periods;
+    double* nu;          // [ntrials]: 1 / P
+    double* lnnu;        // [ntrials]: ln(1 / P)
+    uint8_t* flags;      // [nw][ntrials]: selected
     const float* snr;
     long long ntrials;
     int nw;
@@ -87,8 +93,7 @@ struct Params {
     long long* coff;     // [nw][nchunks]: their exclusive prefix
 };
 
-__device__ __forceinline__ long long seg_of(double P, const Hdr& h) {
-    const double nu = __ddiv_rn(1.0, P);
+__device__ __forceinline__ long long seg_of(double nu, const Hdr& h) {
     const long long j = (long long)floor(__ddiv_rn(__dsub_rn(nu, h.nu_lo), h.width));
     return j < h.nseg - 1 ? j : h.nseg - 1;
 }
@@ -138,52 +143,38 @@ __device__ long long block_scan(long long v, long long* sh, long long* total) {
     return ex;
 }
 
-struct MinOp {
-    __device__ double operator()(double a, double b) const { return a < b ? a : b; }
-};
-struct MaxOp {
-    __device__ double operator()(double a, double b) const { return a > b ? a : b; }
-};
-struct OrOp {
-    __device__ unsigned operator()(unsigned a, unsigned b) const { return a | b; }
-};
 struct AddOp {
     __device__ double operator()(double a, double b) const { return a + b; }
 };
 
-__global__ void __launch_bounds__(kRangeThreads) pk_range_kernel(Params p) {
-    __shared__ double shd[32];
-    __shared__ unsigned shu[32];
-    double lo = INFINITY, hi = -INFINITY;
-    unsigned bad = 0;
-    for (long long t = threadIdx.x; t < p.ntrials; t += blockDim.x) {
-        const double P = p.periods[t];
-        if (!(P > 0.0) || !isfinite(P)) bad = 1;
-        if (t + 1 < p.ntrials && !(P <= p.periods[t + 1])) bad = 1;
-        const double nu = __ddiv_rn(1.0, P);
-        lo = nu < lo ? nu : lo;
-        hi = nu > hi ? nu : hi;
+__global__ void __launch_bounds__(kPrepThreads) pk_prep_kernel(Params p) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p.ntrials) return;
+    const double P = p.periods[t];
+    bool bad = !(P > 0.0) || !isfinite(P);
+    if (t + 1 < p.ntrials && !(P <= p.periods[t + 1])) bad = true;
+    if (bad) atomicOr(p.status, kPkBadPeriods);
+    const double nu = __ddiv_rn(1.0, P);
+    p.nu[t] = nu;
+    p.lnnu[t] = log(nu);
+}
+
+// The trial frequencies fall with the trial index (periods checked non-decreasing), so
+// the range is their two ends.
+__global__ void pk_range_kernel(Params p) {
+    if (threadIdx.x != 0) return;
+    const double lo = p.nu[p.ntrials - 1], hi = p.nu[0];
+    const double q = ceil(__ddiv_rn(__dsub_rn(hi, lo), p.width));
+    long long nseg = q > 1.0 ? (long long)q : 1;
+    if (*p.status & kPkBadPeriods) {
+        nseg = 0;
+    } else if (!(q <= (double)p.max_segments)) {
+        atomicOr(p.status, kPkTooManySegments);
+        nseg = 0;
     }
-    lo = block_reduce(lo, MinOp(), (double)INFINITY, shd);
-    hi = block_reduce(hi, MaxOp(), -(double)INFINITY, shd);
-    bad = block_reduce(bad, OrOp(), 0u, shu);
-    if (threadIdx.x == 0) {
-        // the first launch of a call: it sets the status word, the others only add bits
-        const double q = ceil(__ddiv_rn(__dsub_rn(hi, lo), p.width));
-        long long nseg = q > 1.0 ? (long long)q : 1;
-        unsigned st = 0;
-        if (bad) {
-            st = kPkBadPeriods;
-            nseg = 0;
-        } else if (!(q <= (double)p.max_segments)) {
-            st = kPkTooManySegments;
-            nseg = 0;
-        }
-        *p.status = st;
-        p.hdr->nu_lo = lo;
-        p.hdr->width = p.width;
-        p.hdr->nseg = nseg;
-    }
+    p.hdr->nu_lo = lo;
+    p.hdr->width = p.width;
+    p.hdr->nseg = nseg;
 }
 
 // Linear interpolation between order statistics, as the "linear" sample quantile of
@@ -214,7 +205,7 @@ __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
             long long a = 0, b = p.ntrials;
             while (a < b) {
                 const long long m = (a + b) >> 1;
-                if (seg_of(p.periods[m], h) <= target)
+                if (seg_of(p.nu[m], h) <= target)
                     b = m;
                 else
                     a = m + 1;
@@ -353,8 +344,8 @@ __global__ void __launch_bounds__(kFitThreads) pk_fit_kernel(Params p) {
     f->valid = 1;
 }
 
-__device__ __forceinline__ double threshold(const Fit& f, int d, double nu) {
-    const double u = (log(nu) - f.xbar) / f.xscale;
+__device__ __forceinline__ double threshold(const Fit& f, int d, double lnnu) {
+    const double u = (lnnu - f.xbar) / f.xscale;
     double t = f.c[d];
     for (int a = d - 1; a >= 0; --a) t = t * u + f.c[a];
     return t;
@@ -376,10 +367,7 @@ __device__ __forceinline__ int select_chunk(const Params& p, const Fit& f, int i
     for (int u = 0; u < kSelPer; ++u) {
         const long long t = c * kSelTile + (long long)threadIdx.x * kSelPer + u;
         sel[u] = false;
-        if (t < p.ntrials) {
-            const double nu = __ddiv_rn(1.0, p.periods[t]);
-            sel[u] = (double)p.snr[t * p.nw + iw] > threshold(f, p.degree, nu);
-        }
+        if (t < p.ntrials) sel[u] = (double)p.snr[t * p.nw + iw] > threshold(f, p.degree, p.lnnu[t]);
         k += sel[u];
     }
     return k;
@@ -392,6 +380,12 @@ __global__ void __launch_bounds__(kSelThreads) pk_count_kernel(Params p) {
     if (p.hdr->nseg == 0 || !f.valid) return;
     bool sel[kSelPer];
     const double k = (double)select_chunk(p, f, iw, blockIdx.x, sel);
+    uint8_t* fl = p.flags + (size_t)iw * p.ntrials;
+#pragma unroll
+    for (int u = 0; u < kSelPer; ++u) {
+        const long long t = (long long)blockIdx.x * kSelTile + (long long)threadIdx.x * kSelPer + u;
+        if (t < p.ntrials) fl[t] = sel[u];
+    }
     const double tot = block_reduce(k, AddOp(), 0.0, shd);
     if (threadIdx.x == 0) p.ccount[(size_t)iw * p.nchunks + blockIdx.x] = (long long)tot;
 }
@@ -426,7 +420,14 @@ __global__ void __launch_bounds__(kSelThreads) pk_write_kernel(Params p) {
     const Fit f = p.fit[iw];
     if (p.hdr->nseg == 0 || !f.valid) return;
     bool sel[kSelPer];
-    const long long k = select_chunk(p, f, iw, blockIdx.x, sel);
+    const uint8_t* fl = p.flags + (size_t)iw * p.ntrials;
+    long long k = 0;
+#pragma unroll
+    for (int u = 0; u < kSelPer; ++u) {
+        const long long t = (long long)blockIdx.x * kSelTile + (long long)threadIdx.x * kSelPer + u;
+        sel[u] = t < p.ntrials && fl[t];
+        k += sel[u];
+    }
     long long tot;
     long long off = p.coff[(size_t)iw * p.nchunks + blockIdx.x] + block_scan(k, shl, &tot);
     uint32_t* L = p.list + (size_t)iw * p.ntrials;
@@ -449,8 +450,7 @@ __global__ void __launch_bounds__(kSelThreads) pk_cluster_kernel(Params p) {
     const long long e0 = threadIdx.x * per, e1 = e0 + per < nsel ? e0 + per : nsel;
     auto starts = [&](long long e) {
         if (e == 0) return true;
-        const double gp = __dsub_rn(__ddiv_rn(1.0, p.periods[L[e - 1]]),
-                                    __ddiv_rn(1.0, p.periods[L[e]]));
+        const double gp = __dsub_rn(p.nu[L[e - 1]], p.nu[L[e]]);
         return gp > p.gap;
     };
     long long ns = 0;
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(1024) pk_output_kernel(Params p, ffa_peak* out
 size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t status, hdr, ctrl, fit, list, best, counts, ccount, coff, bytes;
+    size_t status, hdr, ctrl, fit, list, best, counts, ccount, coff, nu, lnnu, flags, bytes;
 };
 
 Layout layout(long long ntrials, int nw, long long max_segments) {
@@ -522,6 +522,9 @@ Layout layout(long long ntrials, int nw, long long max_segments) {
     const size_t nchunks = (size_t)((ntrials + kSelTile - 1) / kSelTile);
     L.ccount = take(sizeof(long long) * nchunks * nw);
     L.coff = take(sizeof(long long) * nchunks * nw);
+    L.nu = take(sizeof(double) * (size_t)ntrials);
+    L.lnnu = take(sizeof(double) * (size_t)ntrials);
+    L.flags = take((size_t)ntrials * nw);
     L.bytes = off;
     return L;
 }
@@ -614,6 +617,9 @@ extern "C" ffa_status ffa_find_peaks(const double* d_periods, const float* d_snr
     p.nchunks = (ntrials + kSelTile - 1) / kSelTile;
     p.ccount = reinterpret_cast<long long*>(ws + L.ccount);
     p.coff = reinterpret_cast<long long*>(ws + L.coff);
+    p.nu = reinterpret_cast<double*>(ws + L.nu);
+    p.lnnu = reinterpret_cast<double*>(ws + L.lnnu);
+    p.flags = reinterpret_cast<uint8_t*>(ws + L.flags);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     static bool attr_set = false;
     if (!attr_set) {
@@ -626,7 +632,13 @@ extern "C" ffa_status ffa_find_peaks(const double* d_periods, const float* d_snr
     }
     {
         LaunchScope ls(ffa::kPeaks, 4.0 * (double)ntrials * nw + 8.0 * ntrials, s);
-        pk_range_kernel<<<1, kRangeThreads, 0, s>>>(p);
+        if (cudaMemsetAsync(p.status, 0, sizeof(unsigned), s) != cudaSuccess) {
+            cudaGetLastError();
+            return ffa::set_error(FFA_ERR_CUDA, "ffa_find_peaks: status reset");
+        }
+        pk_prep_kernel<<<(unsigned)((ntrials + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0,
+                         s>>>(p);
+        pk_range_kernel<<<1, 32, 0, s>>>(p);
         pk_segment_kernel<<<kSegGrid, kSegThreads, kSortCap * sizeof(float), s>>>(p);
         pk_fit_kernel<<<nw, kFitThreads, 0, s>>>(p);
         const dim3 grid((unsigned)p.nchunks, (unsigned)nw);
