@@ -13,10 +13,11 @@
 //                      and logarithms are slow on this GPU: nothing later repeats them);
 //   pk_range_kernel    one thread: frequency range (the ends of the sorted trials) and
 //                      segment count;
-//   pk_segment_kernel  one CTA per (segment, width): the segment's trials are one index
-//                      range (periods are non-decreasing), found by binary search; their
-//                      S/N values are sorted in shared memory (bitonic) and the quartiles
-//                      interpolated linearly between order statistics;
+//   pk_bounds_kernel   per segment, its first trial (binary search: the segments fall
+//                      with the trial index, periods being non-decreasing);
+//   pk_segment_kernel  one CTA per segment, all widths: the S/N values of each width are
+//                      sorted in shared memory (bitonic) and the quartiles interpolated
+//                      linearly between order statistics;
 //   pk_fit_kernel      one CTA per width: normal equations of the polynomial in the
 //                      centred and scaled log frequency, solved by Gaussian elimination
 //                      with partial pivoting, in FP64;
@@ -65,7 +66,7 @@ struct Hdr {
 };
 
 struct Fit {
-    double xbar, xscale;
+    double xbar, xscale, inv_xscale;
     double c[kMaxDegree + 1];  // threshold = sum_a c[a] u^a, u = (ln nu - xbar) / xscale
     int valid;
 };
@@ -74,7 +75,8 @@ struct Params {
     const double* periods;
     double* nu;          // [ntrials]: 1 / P
     double* lnnu;        // [ntrials]: ln(1 / P)
-    uint8_t* flags;      // [nw][ntrials]: selected
+    uint8_t* flags;      // [ntrials][nw]: selected (the S/N's layout)
+    long long* first;    // [max_segments]: first trial of segment <= j
     const float* snr;
     long long ntrials;
     int nw;
@@ -191,64 +193,77 @@ __device__ double quantile(const float* v, long long c, double q) {
     return g >= 0.5 ? __dsub_rn(b, __dmul_rn(d, __dsub_rn(1.0, g))) : __dadd_rn(a, __dmul_rn(d, g));
 }
 
+// first[j] = the first trial whose segment is <= j (segments fall with the trial index),
+// so segment j is [first[j], first[j - 1]) with first[-1] = ntrials.
+__global__ void __launch_bounds__(256) pk_bounds_kernel(Params p) {
+    const Hdr h = *p.hdr;
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < h.nseg;
+         j += (long long)gridDim.x * blockDim.x) {
+        long long a = 0, b = p.ntrials;
+        while (a < b) {
+            const long long m = (a + b) >> 1;
+            if (seg_of(p.nu[m], h) <= j)
+                b = m;
+            else
+                a = m + 1;
+        }
+        p.first[j] = a;
+    }
+}
+
+// One CTA per segment, all widths: the segment's S/N rows are read once (coalesced),
+// as many widths as fit shared memory are sorted together (independent bitonic
+// networks), and one thread per width interpolates its quartiles.
 __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
     extern __shared__ float v[];
-    __shared__ long long s_range[2];
     const Hdr h = *p.hdr;
-    const long long npairs = h.nseg * p.nw;
-    for (long long q = blockIdx.x; q < npairs; q += gridDim.x) {
-        const long long j = q / p.nw;
-        const int iw = (int)(q % p.nw);
-        if (threadIdx.x < 2) {
-            // first trial whose segment is <= j - threadIdx.x (segments fall with t)
-            const long long target = j - threadIdx.x;
-            long long a = 0, b = p.ntrials;
-            while (a < b) {
-                const long long m = (a + b) >> 1;
-                if (seg_of(p.nu[m], h) <= target)
-                    b = m;
-                else
-                    a = m + 1;
-            }
-            s_range[threadIdx.x] = a;
-        }
-        __syncthreads();
-        const long long t0 = s_range[0], t1 = j ? s_range[1] : p.ntrials;
+    const int nw = p.nw;
+    for (long long j = blockIdx.x; j < h.nseg; j += gridDim.x) {
+        const long long t0 = p.first[j], t1 = j ? p.first[j - 1] : p.ntrials;
         const long long c = t1 - t0;
         const double nu_c = __dadd_rn(h.nu_lo, __dmul_rn((double)j + 0.5, h.width));
         if (c < p.min_seg || c > kSortCap) {
-            if (threadIdx.x == 0) {
-                if (c > kSortCap) atomicOr(p.status, kPkSegmentTooLarge);
-                p.ctrl[q] = make_double2(nu_c, __longlong_as_double(0x7ff8000000000000LL));
-            }
-            __syncthreads();
+            if (threadIdx.x == 0 && c > kSortCap) atomicOr(p.status, kPkSegmentTooLarge);
+            for (int iw = threadIdx.x; iw < nw; iw += blockDim.x)
+                p.ctrl[j * nw + iw] = make_double2(nu_c, __longlong_as_double(0x7ff8000000000000LL));
             continue;
         }
-        int m = 1;
-        while (m < c) m <<= 1;
-        for (int i = threadIdx.x; i < m; i += blockDim.x)
-            v[i] = i < c ? p.snr[(t0 + i) * p.nw + iw] : INFINITY;
-        __syncthreads();
-        for (int k = 2; k <= m; k <<= 1) {
-            for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                for (int i = threadIdx.x; i < m; i += blockDim.x) {
-                    const int ixj = i ^ jj;
-                    if (ixj > i) {
-                        const float x = v[i], y = v[ixj];
-                        if ((x > y) == ((i & k) == 0)) {
-                            v[i] = y;
-                            v[ixj] = x;
+        int lm = 0;
+        while ((1LL << lm) < c) ++lm;
+        const int m = 1 << lm;
+        const int G = kSortCap >> lm;  // widths per pass
+        for (int w0 = 0; w0 < nw; w0 += G) {
+            const int gn = nw - w0 < G ? nw - w0 : G;
+            __syncthreads();  // the previous pass's quartiles are read
+            for (int e = threadIdx.x; e < gn * m; e += blockDim.x) {
+                const int i = e / gn, g = e - i * gn;
+                v[g * m + i] = i < c ? p.snr[(t0 + i) * nw + w0 + g] : INFINITY;
+            }
+            __syncthreads();
+            for (int k = 2; k <= m; k <<= 1) {
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                    for (int e = threadIdx.x; e < gn * m; e += blockDim.x) {
+                        const int i = e & (m - 1), ixj = i ^ jj;
+                        if (ixj > i) {
+                            float* w = v + (e - i);
+                            const float x = w[i], y = w[ixj];
+                            if ((x > y) == ((i & k) == 0)) {
+                                w[i] = y;
+                                w[ixj] = x;
+                            }
                         }
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
             }
-        }
-        if (threadIdx.x == 0) {
-            const double q25 = quantile(v, c, 0.25), q50 = quantile(v, c, 0.5),
-                         q75 = quantile(v, c, 0.75);
-            const double sigma = __ddiv_rn(__dsub_rn(q75, q25), 1.349);
-            p.ctrl[q] = make_double2(nu_c, __dadd_rn(q50, __dmul_rn(p.nsigma, sigma)));
+            if (threadIdx.x < gn) {
+                const float* w = v + threadIdx.x * m;
+                const double q25 = quantile(w, c, 0.25), q50 = quantile(w, c, 0.5),
+                             q75 = quantile(w, c, 0.75);
+                const double sigma = __ddiv_rn(__dsub_rn(q75, q25), 1.349);
+                p.ctrl[j * nw + w0 + threadIdx.x] =
+                    make_double2(nu_c, __dadd_rn(q50, __dmul_rn(p.nsigma, sigma)));
+            }
         }
         __syncthreads();
     }
@@ -341,11 +356,12 @@ __global__ void __launch_bounds__(kFitThreads) pk_fit_kernel(Params p) {
     }
     f->xbar = xbar;
     f->xscale = xs;
+    f->inv_xscale = 1.0 / xs;
     f->valid = 1;
 }
 
 __device__ __forceinline__ double threshold(const Fit& f, int d, double lnnu) {
-    const double u = (lnnu - f.xbar) / f.xscale;
+    const double u = (lnnu - f.xbar) * f.inv_xscale;
     double t = f.c[d];
     for (int a = d - 1; a >= 0; --a) t = t * u + f.c[a];
     return t;
@@ -358,36 +374,36 @@ __device__ __forceinline__ uint64_t best_key(float s, long long t) {
     return ((uint64_t)u << 32) | (uint64_t)(0xffffffffu - (uint32_t)t);
 }
 
-// Selection over chunks of kSelTile consecutive trials, kSelPer per thread: a trial is
-// selected when its S/N is strictly above the threshold.
-__device__ __forceinline__ int select_chunk(const Params& p, const Fit& f, int iw, long long c,
-                                            bool* sel) {
-    int k = 0;
-#pragma unroll
-    for (int u = 0; u < kSelPer; ++u) {
-        const long long t = c * kSelTile + (long long)threadIdx.x * kSelPer + u;
-        sel[u] = false;
-        if (t < p.ntrials) sel[u] = (double)p.snr[t * p.nw + iw] > threshold(f, p.degree, p.lnnu[t]);
-        k += sel[u];
-    }
-    return k;
-}
-
+// Selection over chunks of kSelTile consecutive trials, all widths per CTA (the S/N rows
+// read whole, coalesced): a trial is selected for a width when its S/N is strictly above
+// that width's threshold.  Flags are kept in the S/N's layout; counts per (chunk, width).
 __global__ void __launch_bounds__(kSelThreads) pk_count_kernel(Params p) {
-    __shared__ double shd[32];
-    const int iw = blockIdx.y;
-    const Fit f = p.fit[iw];
-    if (p.hdr->nseg == 0 || !f.valid) return;
-    bool sel[kSelPer];
-    const double k = (double)select_chunk(p, f, iw, blockIdx.x, sel);
-    uint8_t* fl = p.flags + (size_t)iw * p.ntrials;
-#pragma unroll
-    for (int u = 0; u < kSelPer; ++u) {
-        const long long t = (long long)blockIdx.x * kSelTile + (long long)threadIdx.x * kSelPer + u;
-        if (t < p.ntrials) fl[t] = sel[u];
+    __shared__ Fit s_fit[ffa::kMaxWidths];
+    __shared__ unsigned s_cnt[ffa::kMaxWidths];
+    const int nw = p.nw;
+    const bool live = p.hdr->nseg != 0;
+    for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
+        s_fit[iw] = p.fit[iw];
+        s_cnt[iw] = 0;
     }
-    const double tot = block_reduce(k, AddOp(), 0.0, shd);
-    if (threadIdx.x == 0) p.ccount[(size_t)iw * p.nchunks + blockIdx.x] = (long long)tot;
+    __syncthreads();
+    const long long t0 = (long long)blockIdx.x * kSelTile;
+    const long long ct = p.ntrials - t0 < kSelTile ? p.ntrials - t0 : kSelTile;
+    const long long ne = ct * nw;
+    const float* S = p.snr + t0 * nw;
+    uint8_t* fl = p.flags + t0 * nw;
+    for (long long e = threadIdx.x; e < ne; e += blockDim.x) {
+        const long long tl = e / nw;
+        const int iw = (int)(e - tl * nw);
+        const Fit& f = s_fit[iw];
+        const bool sel = live && f.valid &&
+                         (double)S[e] > threshold(f, p.degree, p.lnnu[t0 + tl]);
+        fl[e] = sel;
+        if (sel) atomicAdd(s_cnt + iw, 1u);
+    }
+    __syncthreads();
+    for (int iw = threadIdx.x; iw < nw; iw += blockDim.x)
+        p.ccount[(size_t)iw * p.nchunks + blockIdx.x] = s_cnt[iw];
 }
 
 __global__ void __launch_bounds__(kSelThreads) pk_offsets_kernel(Params p) {
@@ -420,12 +436,11 @@ __global__ void __launch_bounds__(kSelThreads) pk_write_kernel(Params p) {
     const Fit f = p.fit[iw];
     if (p.hdr->nseg == 0 || !f.valid) return;
     bool sel[kSelPer];
-    const uint8_t* fl = p.flags + (size_t)iw * p.ntrials;
     long long k = 0;
 #pragma unroll
     for (int u = 0; u < kSelPer; ++u) {
         const long long t = (long long)blockIdx.x * kSelTile + (long long)threadIdx.x * kSelPer + u;
-        sel[u] = t < p.ntrials && fl[t];
+        sel[u] = t < p.ntrials && p.flags[t * p.nw + iw];
         k += sel[u];
     }
     long long tot;
@@ -501,7 +516,7 @@ __global__ void __launch_bounds__(1024) pk_output_kernel(Params p, ffa_peak* out
 size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t status, hdr, ctrl, fit, list, best, counts, ccount, coff, nu, lnnu, flags, bytes;
+    size_t status, hdr, ctrl, fit, list, best, counts, ccount, coff, nu, lnnu, flags, first, bytes;
 };
 
 Layout layout(long long ntrials, int nw, long long max_segments) {
@@ -525,6 +540,7 @@ Layout layout(long long ntrials, int nw, long long max_segments) {
     L.nu = take(sizeof(double) * (size_t)ntrials);
     L.lnnu = take(sizeof(double) * (size_t)ntrials);
     L.flags = take((size_t)ntrials * nw);
+    L.first = take(sizeof(long long) * (size_t)max_segments);
     L.bytes = off;
     return L;
 }
@@ -620,6 +636,7 @@ extern "C" ffa_status ffa_find_peaks(const double* d_periods, const float* d_snr
     p.nu = reinterpret_cast<double*>(ws + L.nu);
     p.lnnu = reinterpret_cast<double*>(ws + L.lnnu);
     p.flags = reinterpret_cast<uint8_t*>(ws + L.flags);
+    p.first = reinterpret_cast<long long*>(ws + L.first);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     static bool attr_set = false;
     if (!attr_set) {
@@ -639,10 +656,11 @@ extern "C" ffa_status ffa_find_peaks(const double* d_periods, const float* d_snr
         pk_prep_kernel<<<(unsigned)((ntrials + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0,
                          s>>>(p);
         pk_range_kernel<<<1, 32, 0, s>>>(p);
+        pk_bounds_kernel<<<152, 256, 0, s>>>(p);
         pk_segment_kernel<<<kSegGrid, kSegThreads, kSortCap * sizeof(float), s>>>(p);
         pk_fit_kernel<<<nw, kFitThreads, 0, s>>>(p);
         const dim3 grid((unsigned)p.nchunks, (unsigned)nw);
-        pk_count_kernel<<<grid, kSelThreads, 0, s>>>(p);
+        pk_count_kernel<<<(unsigned)p.nchunks, kSelThreads, 0, s>>>(p);
         pk_offsets_kernel<<<nw, kSelThreads, 0, s>>>(p);
         pk_write_kernel<<<grid, kSelThreads, 0, s>>>(p);
         pk_cluster_kernel<<<nw, kSelThreads, 0, s>>>(p);
