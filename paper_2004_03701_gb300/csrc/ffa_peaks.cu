@@ -15,7 +15,7 @@
 //                      segment count;
 //   pk_bounds_kernel   per segment, its first trial (binary search: the segments fall
 //                      with the trial index, periods being non-decreasing);
-//   pk_segment_kernel  one CTA per segment, all widths: the S/N values of each width are
+//   pk_segment_kernel  one CTA per (segment, 4 widths): the S/N values of each width are
 //                      sorted in shared memory (bitonic) and the quartiles interpolated
 //                      linearly between order statistics;
 //   pk_fit_kernel      one CTA per width: normal equations of the polynomial in the
@@ -54,6 +54,7 @@ constexpr int kSelPer = 4;                      // trials per thread of a select
 constexpr int kSelTile = kSelThreads * kSelPer;
 constexpr int kMaxDegree = 6;
 constexpr int kSegGrid = 152 * 8;
+constexpr int kGroupW = 4;       // widths per segment work item
 
 // device status bits of the peak finder (first word of its workspace)
 constexpr unsigned kPkTooManySegments = 4u;
@@ -211,20 +212,26 @@ __global__ void __launch_bounds__(256) pk_bounds_kernel(Params p) {
     }
 }
 
-// One CTA per segment, all widths: the segment's S/N rows are read once (coalesced),
-// as many widths as fit shared memory are sorted together (independent bitonic
-// networks), and one thread per width interpolates its quartiles.
+// Work items of (segment, group of kGroupW widths): the rows of the segment are read
+// once per group (coalesced across its widths), as many widths as fit shared memory are
+// sorted together (independent bitonic networks, one comparator per thread and step),
+// and one thread per width interpolates its quartiles.
 __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
     extern __shared__ float v[];
     const Hdr h = *p.hdr;
     const int nw = p.nw;
-    for (long long j = blockIdx.x; j < h.nseg; j += gridDim.x) {
+    const int ngroups = (nw + kGroupW - 1) / kGroupW;
+    const long long nitems = h.nseg * ngroups;
+    for (long long q = blockIdx.x; q < nitems; q += gridDim.x) {
+        const long long j = q / ngroups;
+        const int wa = (int)(q - j * ngroups) * kGroupW;
+        const int wb = wa + kGroupW < nw ? wa + kGroupW : nw;
         const long long t0 = p.first[j], t1 = j ? p.first[j - 1] : p.ntrials;
         const long long c = t1 - t0;
         const double nu_c = __dadd_rn(h.nu_lo, __dmul_rn((double)j + 0.5, h.width));
         if (c < p.min_seg || c > kSortCap) {
             if (threadIdx.x == 0 && c > kSortCap) atomicOr(p.status, kPkSegmentTooLarge);
-            for (int iw = threadIdx.x; iw < nw; iw += blockDim.x)
+            for (int iw = wa + threadIdx.x; iw < wb; iw += blockDim.x)
                 p.ctrl[j * nw + iw] = make_double2(nu_c, __longlong_as_double(0x7ff8000000000000LL));
             continue;
         }
@@ -232,25 +239,25 @@ __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
         while ((1LL << lm) < c) ++lm;
         const int m = 1 << lm;
         const int G = kSortCap >> lm;  // widths per pass
-        for (int w0 = 0; w0 < nw; w0 += G) {
-            const int gn = nw - w0 < G ? nw - w0 : G;
+        for (int w0 = wa; w0 < wb; w0 += G) {
+            const int gn = wb - w0 < G ? wb - w0 : G;
             __syncthreads();  // the previous pass's quartiles are read
             for (int e = threadIdx.x; e < gn * m; e += blockDim.x) {
                 const int i = e / gn, g = e - i * gn;
                 v[g * m + i] = i < c ? p.snr[(t0 + i) * nw + w0 + g] : INFINITY;
             }
             __syncthreads();
+            const int half = m >> 1, ncmp = gn * half;
             for (int k = 2; k <= m; k <<= 1) {
                 for (int jj = k >> 1; jj > 0; jj >>= 1) {
-                    for (int e = threadIdx.x; e < gn * m; e += blockDim.x) {
-                        const int i = e & (m - 1), ixj = i ^ jj;
-                        if (ixj > i) {
-                            float* w = v + (e - i);
-                            const float x = w[i], y = w[ixj];
-                            if ((x > y) == ((i & k) == 0)) {
-                                w[i] = y;
-                                w[ixj] = x;
-                            }
+                    for (int cq = threadIdx.x; cq < ncmp; cq += blockDim.x) {
+                        const int g = cq >> (lm - 1), r = cq & (half - 1);
+                        const int i = ((r & ~(jj - 1)) << 1) | (r & (jj - 1));  // bit jj clear
+                        float* w = v + g * m;
+                        const float x = w[i], y = w[i + jj];
+                        if ((x > y) == ((i & k) == 0)) {
+                            w[i] = y;
+                            w[i + jj] = x;
                         }
                     }
                     __syncthreads();
@@ -374,32 +381,57 @@ __device__ __forceinline__ uint64_t best_key(float s, long long t) {
     return ((uint64_t)u << 32) | (uint64_t)(0xffffffffu - (uint32_t)t);
 }
 
-// Selection over chunks of kSelTile consecutive trials, all widths per CTA (the S/N rows
-// read whole, coalesced): a trial is selected for a width when its S/N is strictly above
-// that width's threshold.  Flags are kept in the S/N's layout; counts per (chunk, width).
+// Selection over chunks of kSelTile consecutive trials, all widths per CTA, one trial
+// per thread and step (its S/N row read whole): a trial is selected for a width when
+// its S/N is strictly above that width's threshold.  The threshold is first evaluated in
+// FP32; only an S/N within a guard band of it (1e-3 (1 + |threshold|), far above the
+// FP32 evaluation's error) is decided by the FP64 polynomial, so every decision is the
+// FP64 one.  Flags are kept in the S/N's layout; counts per (chunk, width).
+struct Fit32 {
+    float xbar, inv, c[kMaxDegree + 1];
+};
+
 __global__ void __launch_bounds__(kSelThreads) pk_count_kernel(Params p) {
     __shared__ Fit s_fit[ffa::kMaxWidths];
+    __shared__ Fit32 s_f32[ffa::kMaxWidths];
     __shared__ unsigned s_cnt[ffa::kMaxWidths];
-    const int nw = p.nw;
+    const int nw = p.nw, d = p.degree;
     const bool live = p.hdr->nseg != 0;
     for (int iw = threadIdx.x; iw < nw; iw += blockDim.x) {
-        s_fit[iw] = p.fit[iw];
+        const Fit f = p.fit[iw];
+        s_fit[iw] = f;
+        Fit32 g;
+        g.xbar = (float)f.xbar;
+        g.inv = (float)f.inv_xscale;
+        for (int a = 0; a <= kMaxDegree; ++a) g.c[a] = (float)f.c[a];
+        s_f32[iw] = g;
         s_cnt[iw] = 0;
     }
     __syncthreads();
     const long long t0 = (long long)blockIdx.x * kSelTile;
-    const long long ct = p.ntrials - t0 < kSelTile ? p.ntrials - t0 : kSelTile;
-    const long long ne = ct * nw;
-    const float* S = p.snr + t0 * nw;
-    uint8_t* fl = p.flags + t0 * nw;
-    for (long long e = threadIdx.x; e < ne; e += blockDim.x) {
-        const long long tl = e / nw;
-        const int iw = (int)(e - tl * nw);
-        const Fit& f = s_fit[iw];
-        const bool sel = live && f.valid &&
-                         (double)S[e] > threshold(f, p.degree, p.lnnu[t0 + tl]);
-        fl[e] = sel;
-        if (sel) atomicAdd(s_cnt + iw, 1u);
+    const long long t1 = t0 + kSelTile < p.ntrials ? t0 + kSelTile : p.ntrials;
+    for (long long t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const double ln = p.lnnu[t];
+        const float l32 = (float)ln;
+        const float* S = p.snr + t * nw;
+        uint8_t* fl = p.flags + t * nw;
+        for (int iw = 0; iw < nw; ++iw) {
+            const float s = S[iw];
+            bool sel = false;
+            if (live && s_fit[iw].valid) {
+                const Fit32& g = s_f32[iw];
+                const float u = (l32 - g.xbar) * g.inv;
+                float th = g.c[d];
+                for (int a = d - 1; a >= 0; --a) th = fmaf(th, u, g.c[a]);
+                const float guard = 1e-3f * (1.0f + fabsf(th));
+                if (s > th + guard)
+                    sel = true;
+                else if (s >= th - guard)
+                    sel = (double)s > threshold(s_fit[iw], d, ln);
+            }
+            fl[iw] = sel;
+            if (sel) atomicAdd(s_cnt + iw, 1u);
+        }
     }
     __syncthreads();
     for (int iw = threadIdx.x; iw < nw; iw += blockDim.x)
