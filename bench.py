@@ -7,11 +7,14 @@ series shape, Sec. 5.8), N(0,1) noise plus three Gaussian pulse trains, periods
 one whole periodogram (prefix sums, downsampling of all 55 pseudo-octaves, 1155 FFA
 transforms, boxcar S/N of 662,440 trials).
 
-Other workloads: plain_small (2^18 samples at 1 ms, periods 1-10 s); batch_uneven (256
+Other workloads: plain_small (2^18 samples at 1 ms, periods 1-10 s); segments (the
+survey series over three period segments with 100-110, 400-440 and 1000-1100 bins:
+dynamic duty-cycle resolution, Sec. 5.6); batch_uneven (256
 series of U[2^20, 2^23] samples, each with its own period range in 0.1-30 s, one CUDA
 graph per step over all launch chunks); batch_int8 (1024 series of 2^21 samples,
 periods 0.1-10 s, bins 480-520, 16 widths, normalised and stored as int8).  --storage
 f16 / i8 stores the normalised input at reduced precision (sums stay FP32).
+--template zero_mean scores with the zero-sum boxcar instead of the plain one.
 --workload deredden times the step before the search instead: the running-median
 de-reddening of Sec. 5.2 on a 2^23-sample red-noise series at 64 us with a 1 s window
 (15625 samples); its metric is samples de-reddened per second.  --workload peaks times
@@ -57,6 +60,7 @@ def _log(msg):
 
 
 METRIC = "time-series samples searched/s (FFA periodogram)"
+ZERO_MEAN = False   # boxcar template of the timed searches (set from --template)
 UNIT = "samples/s"
 
 
@@ -75,6 +79,9 @@ def parse():
                     help="time a small grid of tile shapes first and bench the fastest")
     ap.add_argument("--ws-budget-gb", type=float, default=48.0,
                     help="workspace budget of one launch chunk of a batch")
+    ap.add_argument("--template", choices=["plain", "zero_mean"], default="plain",
+                    help="boxcar template of the S/N (Sec. 5.4; zero-mean: the unit-square-sum "
+                         "template with zero sum)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-stride", type=int, default=8)
@@ -201,7 +208,7 @@ def oracle_sample_time(w, stride, offset=0, full_ds=True):
     sel = np.zeros(pl.n_transforms, bool)
     sel[offset % stride::stride] = True
     t0 = time.perf_counter()
-    ref = oracle.periodogram(w.x, *args, w.widths, select=sel)
+    ref = oracle.periodogram(w.x, *args, w.widths, select=sel, zero_mean=ZERO_MEAN)
     t_sel = time.perf_counter() - t0
     folded = (pl.tr_m * pl.tr_p).astype(np.float64)
     ratio = folded.sum() / max(folded[sel].sum(), 1.0)
@@ -242,7 +249,8 @@ def oracle_parallel_rate(w, stride, threads):
     masks = [m for m in masks if m.any()]
     t0 = time.perf_counter()
     with ThreadPoolExecutor(len(masks)) as ex:
-        list(ex.map(lambda m: oracle.periodogram(w.x, *args, w.widths, select=m), masks))
+        list(ex.map(lambda m: oracle.periodogram(w.x, *args, w.widths, select=m,
+                                                 zero_mean=ZERO_MEAN), masks))
     wall = time.perf_counter() - t0
     ratio = folded.sum() / folded[sel].sum()
     desc = ("oracle (C, FP64) on %d threads: every %d-th of %d transforms (%.1f%% of folded "
@@ -272,9 +280,13 @@ def oracle_rate(job, stride, offset=0, full_ds=True):
         w = synth.Workload("s%d" % i, x, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax, b.widths)
         est, desc, chk = oracle_sample_time(w, stride, offset, full_ds)
         tot_t += est
-        tot_n += s.n
+        tot_n += s.n if not b.shared else 0
         descs.append("series %d (n=%d): %s" % (i, s.n, desc))
         checks.append((i,) + chk)
+    if b.shared:  # period segments of one series: its samples over all segments' time
+        tot_n = b.n
+        return tot_n / tot_t, "all %d period segments of the one series, rate = its " \
+            "samples / their estimated time; " % len(b.series) + " | ".join(descs), checks
     return tot_n / tot_t, "%d of %d series of the batch, rate = their samples / their " \
         "estimated time; " % (len(pick), len(b.series)) + " | ".join(descs), checks
 
@@ -322,7 +334,7 @@ def quantisation_error(job, checks):
             s = job.batch.series[i]
             x, args = job.batch.series_x(i), (s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax,
                                               job.batch.widths)
-        ref = oracle.periodogram(oracle.normalise(x)[2], *args, select=sel)
+        ref = oracle.periodogram(oracle.normalise(x)[2], *args, select=sel, zero_mean=ZERO_MEAN)
         got = job.searcher.series_result(i) if i is not None else \
             (job.searcher.periods, job.searcher.foldbins, job.searcher.snr)
         snr = got[2].cpu().numpy()[rows].astype(np.float64)
@@ -352,7 +364,7 @@ def profile_error(job, check):
 
 
 # --------------------------------------------------------------------------- workloads
-BATCH_WORKLOADS = ("batch_uneven", "batch_int8")
+BATCH_WORKLOADS = ("batch_uneven", "batch_int8", "segments")
 
 
 class Job:
@@ -372,6 +384,8 @@ class Job:
             self.batch = self._shard(synth.batch_uneven, 256, rank, world)
         elif name == "batch_int8":
             self.batch = self._shard(synth.batch_int8_stress, 1024, rank, world)
+        elif name == "segments":
+            self.batch = synth.survey_segments()
         else:
             raise ValueError(name)
         self._deq = {}
@@ -418,11 +432,11 @@ class Job:
         if self.batch is None:
             w = self.single
             return ffa.Searcher(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths,
-                                device=dev, tiles=tiles)
+                                device=dev, tiles=tiles, zero_mean=ZERO_MEAN)
         ser = [ffa.Series(s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax)
                for s in self.batch.series]
         return ffa.BatchSearcher(ser, self.batch.widths, ws_budget=self.ws_budget, device=dev,
-                                 tiles=tiles)
+                                 tiles=tiles, zero_mean=ZERO_MEAN)
 
     def tune(self, repeats=2):
         """Picks the fastest tile shape of a small grid around the automatic one (every
@@ -1022,6 +1036,7 @@ def run_ffa(a):
 
     if rank == 0:
         cfg = job.config()
+        cfg["template"] = "zero_mean" if ZERO_MEAN else "plain"
         cfg["l2"] = "flushed (256 MB write) between steps"
         cfg["parallelism"] = "replicas" if world > 1 else "single"
         line = {
@@ -1122,7 +1137,9 @@ def run_e2e(job, a, torch, ffa, flush, barrier, world, dev, n_all):
 
 
 def main():
+    global ZERO_MEAN
     a = parse()
+    ZERO_MEAN = a.template == "zero_mean"
     if a.workload == "deredden":
         run_deredden(a)
     elif a.workload == "peaks":

@@ -117,6 +117,21 @@ def survey(seed: Optional[int] = None) -> Workload:
                     0.2, 20.0, 240, 260, WIDTHS_11, pulses)
 
 
+# Period segments of the survey series for dynamic duty-cycle resolution (Sec. 5.6):
+# about 100 bins down to 0.1 s, more bins at longer periods, 1000-1100 from 2 s to 20 s.
+SURVEY_SEGMENTS = ((0.1, 0.5, 100, 110), (0.5, 2.0, 400, 440), (2.0, 20.0, 1000, 1100))
+
+
+def survey_segments(seed: Optional[int] = None) -> BatchWorkload:
+    """The survey series searched over SURVEY_SEGMENTS: one batch whose three series
+    are the same samples, each with its own period and bins range; 11 widths (all
+    below the smallest bmin)."""
+    w = survey(seed)
+    series = [SeriesParams(0, w.n, w.tsamp, pmin, pmax, bmin, bmax, list(w.pulses))
+              for pmin, pmax, bmin, bmax in SURVEY_SEGMENTS]
+    return BatchWorkload("survey_segments_2^23_64us", w.x, series, WIDTHS_11, shared=True)
+
+
 def custom(n: int, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,
            widths, seed: int, pulses=()) -> Workload:
     return Workload("custom", make_series(n, tsamp, seed, pulses), tsamp, pmin, pmax,
@@ -153,9 +168,13 @@ class BatchWorkload:
     x: np.ndarray                   # float32, all series one after another
     series: List[SeriesParams]
     widths: Tuple[int, ...]
+    shared: bool = False            # all "series" are period segments of one series
 
     @property
     def n(self) -> int:
+        """Input samples searched: the series' total, or the one series' length."""
+        if self.shared:
+            return int(max(s.offset + s.n for s in self.series))
         return int(sum(s.n for s in self.series))
 
     def series_x(self, i: int) -> np.ndarray:
