@@ -1058,8 +1058,9 @@ def run_ffa(a):
 def run_e2e(job, a, torch, ffa, flush, barrier, world, dev, n_all):
     s = job.searcher
     T, nw = job.ntrials, len(job.widths)
-    if job.batch is None and job.store == "f32":
-        # the library's host-buffer call: copies in, searches, copies out, synchronises
+    if job.batch is None and job.store == "f32" and not ZERO_MEAN:
+        # the library's host-buffer call (plain boxcar): copies in, searches, copies out,
+        # synchronises
         xh = torch.from_numpy(job.single.x).pin_memory()
         per_h = torch.empty(max(T, 1), dtype=torch.float64).pin_memory()
         fb_h = torch.empty(max(T, 1), dtype=torch.int32).pin_memory()
