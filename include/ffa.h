@@ -178,8 +178,8 @@ ffa_status ffa_running_median(const float* d_x, int64_t n, int64_t width, float*
  * order of increasing period; peaks beyond peak_cap are counted but not written.
  * d_npeaks: nw + 1 int64 (device): peaks per width, then their total.
  * opts: NULL for the defaults (ffa_peak_opts_default).  Workspace:
- * ffa_find_peaks_workspace bytes (about 12 bytes per trial and width, plus
- * 16 * max_segments * nw).  Asynchronous; a device-side rejection (periods not
+ * ffa_find_peaks_workspace bytes (about 13 bytes per trial and width, 16 per trial,
+ * plus 16 * max_segments * (nw + 1)).  Asynchronous; a device-side rejection (periods not
  * positive and non-decreasing: bit 16; more than max_segments segments: bit 4; a
  * segment of more than 16384 trials: bit 8, that segment gives no control point)
  * shows in ffa_check(d_ws), and a rejected call finds no peaks.

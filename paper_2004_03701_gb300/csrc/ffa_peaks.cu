@@ -33,6 +33,7 @@
 #include "ffa_internal.h"
 #include "ffa_kinds.h"
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -670,14 +671,21 @@ extern "C" ffa_status ffa_find_peaks(const double* d_periods, const float* d_snr
     p.flags = reinterpret_cast<uint8_t*>(ws + L.flags);
     p.first = reinterpret_cast<long long*>(ws + L.first);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    static bool attr_set = false;
-    if (!attr_set) {
+    // the segment kernel's shared-memory size, once per device (setting it twice from two
+    // threads is harmless)
+    static std::atomic<unsigned char> attr_done[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ffa::set_error(FFA_ERR_CUDA, "ffa_find_peaks: no current device");
+    }
+    if (dev < 0 || dev >= 64 || !attr_done[dev].load(std::memory_order_acquire)) {
         if (cudaFuncSetAttribute(pk_segment_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSortCap * (int)sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return ffa::set_error(FFA_ERR_CUDA, "ffa_find_peaks: shared-memory attribute");
         }
-        attr_set = true;
+        if (dev >= 0 && dev < 64) attr_done[dev].store(1, std::memory_order_release);
     }
     {
         LaunchScope ls(ffa::kPeaks, 4.0 * (double)ntrials * nw + 8.0 * ntrials, s);
