@@ -215,9 +215,8 @@ __global__ void __launch_bounds__(256) pk_bounds_kernel(Params p) {
 
 // Work items of (segment, group of kGroupW widths): the rows of the segment are read
 // once per group (coalesced across its widths), as many widths as fit shared memory are
-// sorted together (independent bitonic networks: steps between elements 32 or more
-// apart one comparator per thread in shared memory, shorter steps on warp shuffles), and
-// one thread per width interpolates its quartiles.
+// sorted together (independent bitonic networks, one comparator per thread and step),
+// and one thread per width interpolates its quartiles.
 __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
     extern __shared__ float v[];
     const Hdr h = *p.hdr;
@@ -249,11 +248,9 @@ __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
                 v[g * m + i] = i < c ? p.snr[(t0 + i) * nw + w0 + g] : INFINITY;
             }
             __syncthreads();
-            const int half = m >> 1, ncmp = gn * half, tot = gn * m;
-            const int iters = (tot + blockDim.x - 1) / blockDim.x;  // uniform over the CTA
+            const int half = m >> 1, ncmp = gn * half;
             for (int k = 2; k <= m; k <<= 1) {
-                int jj = k >> 1;
-                for (; jj >= 32; jj >>= 1) {  // partners in other warps: shared memory
+                for (int jj = k >> 1; jj > 0; jj >>= 1) {
                     for (int cq = threadIdx.x; cq < ncmp; cq += blockDim.x) {
                         const int g = cq >> (lm - 1), r = cq & (half - 1);
                         const int i = ((r & ~(jj - 1)) << 1) | (r & (jj - 1));  // bit jj clear
@@ -266,23 +263,6 @@ __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
                     }
                     __syncthreads();
                 }
-                // steps jj < 32: element e sits in lane e mod 32 and its partner e ^ jj in
-                // the same warp (blockDim is a multiple of 32), so the steps run on shuffles;
-                // slots past the data hold +inf and pair with each other (tot is a
-                // multiple of m, and e ^ jj stays inside e's block of m)
-                for (int u = 0; u < iters; ++u) {
-                    const int e = u * blockDim.x + threadIdx.x;
-                    const bool in = e < tot;
-                    float x = in ? v[e] : INFINITY;
-                    const int i = e & (m - 1);
-                    for (int s = jj; s > 0; s >>= 1) {
-                        const float y = __shfl_xor_sync(0xffffffffu, x, s);
-                        const bool keep_min = ((i & s) == 0) == ((i & k) == 0);
-                        x = keep_min ? fminf(x, y) : fmaxf(x, y);
-                    }
-                    if (in) v[e] = x;
-                }
-                __syncthreads();
             }
             if (threadIdx.x < gn) {
                 const float* w = v + threadIdx.x * m;
