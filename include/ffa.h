@@ -373,8 +373,9 @@ ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, doubl
                                 void* d_ws, size_t ws_bytes, void* stream);
 
 /* Synchronises `stream`, reads and clears the device status word of a workspace used
- * by ffa_periodogram / ffa_transform / ffa_downsample.  FFA_OK if no device-side
- * check failed, else FFA_ERR_TIMEOUT or FFA_ERR_DEVICE. */
+ * by ffa_periodogram / ffa_transform / ffa_downsample / ffa_find_peaks.  FFA_OK if no
+ * device-side check failed, else FFA_ERR_TIMEOUT or FFA_ERR_DEVICE (the message names
+ * the failed checks). */
 ffa_status ffa_check(void* d_ws, void* stream);
 
 /* ------------------------------------------------------------------------------

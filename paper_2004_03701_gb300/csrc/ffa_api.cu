@@ -1263,7 +1263,14 @@ ffa_status ffa_check(void* d_ws, void* stream) {
     FFA_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     FFA_CUDA(cudaMemsetAsync(d_ws, 0, sizeof(v), s), "clear status");
     if (v & kDevTimeout) return fail(FFA_ERR_TIMEOUT, "a device-side wait ran out of time");
-    if (v) return fail(FFA_ERR_DEVICE, "device status 0x%x", v);
+    if (v) {
+        // bits 4, 8, 16: the peak finder's input checks (ffa_peaks.cu)
+        return fail(FFA_ERR_DEVICE, "device status 0x%x%s%s%s%s", v,
+                    (v & 2u) ? "; a work item out of range" : "",
+                    (v & 4u) ? "; peak finding: more segments than max_segments" : "",
+                    (v & 8u) ? "; peak finding: a segment above 16384 trials" : "",
+                    (v & 16u) ? "; peak finding: periods not positive and non-decreasing" : "");
+    }
     return FFA_OK;
 }
 
