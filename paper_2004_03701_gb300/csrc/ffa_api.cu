@@ -71,7 +71,7 @@ ProfAcc g_acc[kAllKinds];
 const char* kKindNames[kAllKinds] = {"prefix_partial", "prefix_top",     "prefix_final",
                                      "downsample",     "ffa_bottom",     "ffa_bottom_snr",
                                      "ffa_top",        "boxcar_snr",     "normalise",
-                                     "ffa_persistent", "top_prep",       "median_build",
+                                     "ffa_persistent", "item_records",   "median_build",
                                      "median_query",   "peaks"};
 
 cudaEvent_t pool_get() {
@@ -150,7 +150,6 @@ struct Plan {
     std::vector<OctaveDesc> oct;
     std::vector<TransformDesc> trs;
     std::vector<WorkItem> items;
-    int ntop = 0;                 // top-pass items (records in the workspace)
     std::vector<int2> ds_blocks;  // downsampling CTAs: {octave, first output}
     std::vector<PrefixSeg> segs;  // prefix-sum pass: one per series
     std::vector<int> blk_seg;     // series of each prefix chunk
@@ -188,8 +187,8 @@ constexpr int64_t kBatchFloats = int64_t(6) << 20;  // folded samples per batch 
 // layout fits in shared memory.
 int max_subtree_rows(int p, int row_cap) {
     int n = std::min(row_cap, kBottomMaxRows);
-    // + 16 bytes: the persistent kernel's queue slot after the layout
-    while (n > 1 && bottom_layout(n, n * p, 0).total * 4 + 16 > kBottomSmemBytes) --n;
+    // + the persistent kernel's queue slot and item records after the layout
+    while (n > 1 && bottom_layout(n, n * p, 0).total * 4 + kPersistExtraBytes > kBottomSmemBytes) --n;
     return std::max(n, 1);
 }
 int depth_for(int m, int p, int row_cap = kBottomMaxRows) {
@@ -202,7 +201,7 @@ int depth_for(int m, int p, int row_cap = kBottomMaxRows) {
 // Rows per top-kernel CTA: the most that fit in shared memory (at most kTopMaxRows).
 int top_rows(int p, int L, bool score, int wmax) {
     for (int K = kTopMaxRows; K >= 1; --K)
-        if (top_layout(K, L, p, wmax, score).total * 4 + 16 <= kTopSmemBytes) return K;
+        if (top_layout(K, L, p, wmax, score).total * 4 + kPersistExtraBytes <= kTopSmemBytes) return K;
     return 0;
 }
 
@@ -427,8 +426,8 @@ ffa_status build_plan(Plan& pl) {
                 const int lim = score ? d.kept : nmax;
                 const int nb = (lim + K - 1) / K;
                 const int cnt = score ? nb : (1 << dout) * nb;
-                for (int i = 0; i < cnt; ++i)  // pad: the item's record (built on the device)
-                    sv[j + 1].push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, pl.ntop++});
+                for (int i = 0; i < cnt; ++i)
+                    sv[j + 1].push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, 0});
                 pl.stage_count[(size_t)t * kMaxStages + j + 1] = cnt;
             }
         }
@@ -443,7 +442,8 @@ ffa_status build_plan(Plan& pl) {
     if (pl.bottom_nmax)
         pl.smem_floats =
             std::max(pl.smem_floats, bottom_layout(pl.bottom_nmax, pl.bottom_elems, 0).total);
-    if ((pl.smem_floats + 4) * 4 > kSmemBytes) return kRetrySmaller;
+    pl.smem_floats = (int)round4(pl.smem_floats);  // the queue slot after it is 16-byte aligned
+    if (pl.smem_floats * 4 + kPersistExtraBytes > kSmemBytes) return kRetrySmaller;
     pl.nitems = (int)pl.items.size();
 
     // Tables: octaves | transforms | items | downsampling CTAs | stage counts | prefix
@@ -466,7 +466,7 @@ ffa_status build_plan(Plan& pl) {
     pl.tables_bytes = std::max<size_t>(o, 256);
 
     // Workspace: status | tables | prefix | chunk sums | octave series | scratch 0 |
-    // scratch 1 | stage counters | top-pass records
+    // scratch 1 | stage counters | item records
     pl.nchunks = (int64_t)pl.blk_seg.size();
     size_t w = kStatusBytes;
     pl.o_tables = w;
@@ -484,8 +484,8 @@ ffa_status build_plan(Plan& pl) {
     pl.o_counters = w;  // queue counter, then per transform and stage completions
     pl.counter_bytes = (1 + pl.trs.size() * kMaxStages) * sizeof(int);
     w = align_up(w + pl.counter_bytes, 256);
-    pl.o_recs = w;  // top-pass item records
-    w = align_up(w + (size_t)pl.ntop * kTopRecInts * sizeof(int), 256);
+    pl.o_recs = w;  // one record per queue position (built on the device)
+    w = align_up(w + (size_t)pl.nitems * sizeof(ItemRec), 256);
     pl.ws_bytes = w;
     // host-buffer variant: + input and outputs
     pl.o_hx = w;
@@ -683,7 +683,7 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
 // Issues the whole periodogram on `st`: tables upload, prefix, downsampling, then
 // the FFA + S/N launches group by group.
 // A second stream per host thread and device, with a fork and a join event: the
-// top-pass records are made on it while the prefix sums and downsampling run.  Made on
+// item records are made on it while the prefix sums and downsampling run.  Made on
 // a thread's first periodogram call on a device (so that call should precede any stream
 // capture); if it cannot be made, everything runs on the caller's stream.
 struct SideStream {
@@ -727,7 +727,7 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     float* s0 = reinterpret_cast<float*>(ws + pl.o_s0);
     float* s1 = reinterpret_cast<float*>(ws + pl.o_s1);
 
-    // ---- parameters of the persistent launch (the top-pass records are made first)
+    // ---- parameters of the persistent launch (the item records are made first)
     int* counters = reinterpret_cast<int*>(ws + pl.o_counters);
     PersistentParams pp{};
     BottomParams& bp = pp.bottom;
@@ -756,26 +756,26 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     tp.foldbins = d_foldbins;
     tp.snr = d_snr;
     tp.status = status;
-    int* recs = reinterpret_cast<int*>(ws + pl.o_recs);
-    tp.recs = recs;
+    ItemRec* recs = reinterpret_cast<ItemRec*>(ws + pl.o_recs);
     tp.items = d_items;
-    pp.items = d_items;
     pp.nitems = pl.nitems;
     pp.queue = counters;
     pp.done = counters + 1;
-    pp.stage_count = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt);
+    pp.recs = recs;
     pp.smem_floats = pl.smem_floats;
 
-    // ---- top-pass records on a side stream, concurrent with prefix sums and
+    // ---- item records on a side stream, concurrent with prefix sums and
     //      downsampling (they need only the tables); joined before the FFA launch
     SideStream* side = side_stream();
     cudaStream_t sp = st;
-    if (side && pl.ntop > 0) {
+    if (side && pl.nitems > 0) {
         FFA_CUDA(cudaEventRecord(side->fork, st), "cudaEventRecord(fork)");
         FFA_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0), "cudaStreamWaitEvent(fork)");
         sp = side->s;
     }
-    FFA_CUDA(launch_top_prep(tp, pl.nitems, pl.ntop, recs, sp), "top_prep launch");
+    FFA_CUDA(launch_item_recs(tp, reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt),
+                              pl.nitems, recs, sp),
+             "item record launch");
     if (sp != st) {
         FFA_CUDA(cudaEventRecord(side->join, sp), "cudaEventRecord(join)");
     }
@@ -808,7 +808,8 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     if (sp != st) FFA_CUDA(cudaStreamWaitEvent(st, side->join, 0), "cudaStreamWaitEvent(join)");
     {
         LaunchScope ls(kFfaPersistent, pl.ffa_bytes, st);
-        FFA_CUDA(launch_persistent(pp, (pl.smem_floats + 4) * 4, st), "ffa_persistent launch");
+        FFA_CUDA(launch_persistent(pp, pl.smem_floats * 4 + kPersistExtraBytes, st),
+                 "ffa_persistent launch");
     }
     return FFA_OK;
 }

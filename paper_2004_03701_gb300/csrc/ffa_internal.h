@@ -268,7 +268,7 @@ enum KernelKind : int {
     kBoxcarSnr,
     kNormalise,
     kFfaPersistent,
-    kTopPrep,
+    kItemRecs,
     kNumKinds
 };
 
@@ -343,23 +343,38 @@ struct TopParams {
     int32_t* foldbins;
     float* snr;                     // null: the last pass stores the transform instead
     unsigned* status;
-    const int* recs;                // per-item records (WorkItem::pad), or null: built in the CTA
     int single_pass;                // pass and rows per block when items is null
     int single_rows;
 };
 
 constexpr int kMaxStages = 16;  // sub-trees + up to 15 top passes per transform
 
+// Everything a persistent CTA needs to start the item at one queue position, in one
+// record that it fetches by a single bulk copy while the item before it runs: the work
+// item, its transform, the number of items of the stage it waits for, and for a top-pass
+// item its interval table and shared-memory layout (see kTopRecInts).
+struct ItemRec {
+    WorkItem item;
+    TransformDesc tr;
+    int32_t need;                   // items of stage s - 1 of its transform (stage s > 0)
+    int32_t pad0;
+    int32_t top[kTopRecInts];
+    int32_t pad1[12];
+};
+static_assert(sizeof(ItemRec) == 640, "ItemRec layout (a multiple of 16 bytes)");
+// Shared memory of the persistent kernel after the item layouts: the queue slot (16 B),
+// two record barriers (16 B) and two records (the running item's and the next one's).
+constexpr int kPersistExtraBytes = 32 + 2 * (int)sizeof(ItemRec);
+
 struct PersistentParams {
     BottomParams bottom;            // sub-tree items (pass -1)
     BottomParams bottom_snr;        // whole-tree items scored directly (pass -2)
     TopParams top;                  // top-pass items (pass >= 0)
-    const WorkItem* items;          // queue order
+    const ItemRec* recs;            // one per queue position
     int nitems;
     int* queue;                     // dispatch counter, zero at launch
     int* done;                      // per transform and stage: items completed, zero at launch
-    const int* stage_count;         // per transform and stage: items listed
-    int smem_floats;                // dynamic shared floats before the 16-byte queue slot
+    int smem_floats;                // dynamic shared floats before the queue slot (a multiple of 4)
 };
 
 struct SnrParams {
@@ -389,7 +404,8 @@ cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bo
                           cudaStream_t s);
 cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s);
 cudaError_t launch_persistent(const PersistentParams& P, int smem_bytes, cudaStream_t s);
-cudaError_t launch_top_prep(const TopParams& P, int nitems, int ntop, int* recs, cudaStream_t s);
+cudaError_t launch_item_recs(const TopParams& P, const int* stage_count, int nitems, ItemRec* recs,
+                             cudaStream_t s);
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s);
 cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s);
 constexpr int kNormaliseBlocks = 1216;  // 8 CTAs per SM

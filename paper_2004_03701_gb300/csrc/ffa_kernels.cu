@@ -5,8 +5,9 @@
 //                 5.3, App. A.4) costs two lookups instead of re-reading ~f raw samples.
 //   downsample    all pseudo-octaves of all series in one launch; window edges i*f in
 //                 exact 64.64 fixed point, partial samples weighted by their overlap.
-//   top_prep      the records of all top-pass work items (row intervals, shared-memory
-//                 offsets, bulk-copy bytes), one thread per item.
+//   item_rec      the record of every queue position (work item, transform, stage count
+//                 and, for top passes, row intervals, shared-memory offsets and bulk-copy
+//                 bytes), one thread per item.
 //   ffa_persistent  one CTA per SM takes work items from a queue until the periodogram
 //                 is done.  Sub-tree items (bottom_item): the rows of a node arrive by
 //                 one bulk asynchronous copy (cp.async.bulk + mbarrier), nodes of up to
@@ -275,6 +276,21 @@ __device__ __forceinline__ void bulk_store_wait() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// ---------------------------------------------------------------------------------
+// What a persistent CTA does for its neighbours in the queue while an item's own bulk
+// copies are in flight (thread 0): release the completion of the item before (its
+// stores have long drained by then, so the device-scope fence costs little), and fetch
+// the record of the item it runs next.  A CTA releases before it waits on anyone, so
+// a held completion never blocks another CTA's progress.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void release_count(int* cnt) {
+    // the item's bulk stores complete and are ordered before the generic-proxy fence that
+    // releases them together with every thread's stores (ordered before it by the item's
+    // last barrier, which precedes this release in causality order)
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(cnt) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
                                          uint64_t* bar) {
     asm volatile(
@@ -291,6 +307,52 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     }
     return true;
 }
+
+struct QueueHook {
+    static constexpr bool kInitEachItem = false;  // the copy barrier is made once per CTA
+    unsigned cpar = 0;              // parity of the copy barrier's next phase (all threads)
+    bool failed = false;            // a copy wait of the item ran out (all threads)
+    int* pend = nullptr;            // completion counter of the item before, not yet released
+    const ItemRec* src = nullptr;   // record of the next item (null: none)
+    ItemRec* dst = nullptr;         // its shared-memory buffer and barrier
+    uint64_t* bar = nullptr;
+    unsigned inflight = 0;          // bit per record buffer: a fetch is in flight
+    unsigned bit = 0;
+    bool armed = false;
+    __device__ __forceinline__ void run() {
+        if (threadIdx.x != 0 || !armed) return;
+        armed = false;
+        if (pend) {
+            release_count(pend);
+            pend = nullptr;
+        }
+        if (src) {
+            // the buffer was last read through the generic proxy (the item before)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(bar, (unsigned)sizeof(ItemRec));
+            bulk_g2s(dst, src, (unsigned)sizeof(ItemRec), bar);
+            inflight |= bit;
+        }
+    }
+    // the shared memory of the item's bulk stores may be reused (their global completion
+    // is awaited when the item's completion is released)
+    __device__ __forceinline__ void store_wait() {
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+    __device__ __forceinline__ unsigned parity() const { return cpar; }
+    __device__ __forceinline__ void copied() { cpar ^= 1u; }
+    __device__ __forceinline__ void fail() { failed = true; }
+};
+// Stand-alone launches: a copy barrier per item, nothing to do for other items, stores
+// complete before the CTA exits.
+struct NoHook {
+    static constexpr bool kInitEachItem = true;
+    __device__ __forceinline__ void run() {}
+    __device__ __forceinline__ void store_wait() { bulk_store_wait(); }
+    __device__ __forceinline__ unsigned parity() const { return 0u; }
+    __device__ __forceinline__ void copied() {}
+    __device__ __forceinline__ void fail() {}
+};
 
 // ---------------------------------------------------------------------------------
 // ---------------------------------------------------------------------------------
@@ -615,15 +677,15 @@ __device__ __forceinline__ void reg_strip_any(float* sm, int in, int out, int st
 }
 
 
-template <bool kSnr>
-__device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkItem item, float* smem) {
+template <bool kSnr, class Hook>
+__device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkItem item,
+                                            const TransformDesc& tr, float* smem, Hook& hook) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kBottomThreads / 32;
     const BottomLayout lay = bottom_layout(P.nmax, P.elems_max, P.snr_floats);
     int2* desc = reinterpret_cast<int2*>(smem + lay.desc);  // nmax per shared-memory level
 
-    const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
     const int p = tr.p;
 
     // Node `idx` at depth `depth`: descend by the bits of idx (head = 0, tail = 1).
@@ -637,8 +699,10 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     const float* src = P.src + tr.src_off + (int64_t)start * p;
     const int total = n * p;
     const int a0 = lay.buf_a + (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
-    if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
+    if constexpr (Hook::kInitEachItem) {
+        if (tid == 0) mbar_init(bar, 1);
+        __syncthreads();
+    }
     const unsigned bytes = bulk_bytes(src, total);
     if (tid == 0 && bytes) {
         mbar_expect_tx(bar, bytes);  // the single arrival of this barrier phase
@@ -670,14 +734,17 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
         const int l = e / n, r = e - l * n;
         desc[l * P.nmax + r] = bottom_desc(n, kRegLevels + 1 + l, r, p);
     }
-    const bool landed = bytes == 0 || mbar_wait_bounded(bar, 0);
+    hook.run();
+    const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity());
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
             atomicOr(P.status, kDevTimeout);
-            mbar_wait_bounded(bar, 0);  // let a late copy land before the CTA exits
+            mbar_wait_bounded(bar, hook.parity());  // let a late copy land before the CTA exits
         }
+        hook.fail();
         return;
     }
+    if (bytes) hook.copied();
 
     // ---- register stage: complete transforms of the nodes of <= 16 rows, A -> B
     // Rows after the register stage sit at the 16-byte phase of their destination in
@@ -717,7 +784,7 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
 
     if constexpr (!kSnr) {
         // the 16-byte-aligned interior by one bulk copy, up to 3 floats at either end by
-        // plain stores; the copy completes before the item ends (the buffers are reused)
+        // plain stores; the copy has read the buffer before the item ends (it is reused)
         const int lead = bulk_lead(dst_g);
         const unsigned bytes = bulk_bytes(dst_g, total);
         if (tid == 0 && bytes) {
@@ -729,7 +796,7 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
             const int q = e < lead ? e : tail0 + (e - lead);
             dst_g[q] = smem[in + q];
         }
-        if (tid == 0 && bytes) bulk_store_wait();
+        if (tid == 0 && bytes) hook.store_wait();
     } else {
         // The sub-tree is the whole transform: score rows s < kept (Sec. 2.3).
         float* S = smem + out + warp * snr_warp_floats(p, P.widths.wmax);
@@ -751,14 +818,16 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
         }
     }
     __syncthreads();
-    if (tid == 0) mbar_inval(bar);
+    if (Hook::kInitEachItem && tid == 0) mbar_inval(bar);
 }
 
 template <bool kSnr>
 __global__ void __launch_bounds__(kBottomThreads, kBottomMinBlocks) ffa_bottom_kernel(BottomParams P) {
     extern __shared__ __align__(16) float smem[];
     const WorkItem item = P.items ? P.items[blockIdx.x] : WorkItem{0, (int)blockIdx.x, 0, 0, 0};
-    bottom_item<kSnr>(P, item, smem);
+    const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
+    NoHook hook;
+    bottom_item<kSnr>(P, item, tr, smem, hook);
 }
 
 // ---------------------------------------------------------------------------------
@@ -827,22 +896,34 @@ __device__ void top_record(const TopParams& P, const TransformDesc& tr, const Wo
     r[kRecBytes] = (int)bytes;
 }
 
-// Records of all top-pass items of a queue, one thread each.
+// The records of all queue positions (ItemRec), one thread each: the work item, its
+// transform, the item count of the stage it waits for and, for a top-pass item, its
+// interval table and layout.
 constexpr int kPrepThreads = 64;  // small CTAs: the work is one latency-bound chain per item
-__global__ void __launch_bounds__(kPrepThreads) top_prep_kernel(TopParams P, int nitems, int* recs) {
+__global__ void __launch_bounds__(kPrepThreads) item_rec_kernel(TopParams P, const int* stage_count,
+                                                                int nitems, ItemRec* recs) {
     const int q = blockIdx.x * kPrepThreads + threadIdx.x;
     if (q >= nitems) return;
     const WorkItem item = P.items[q];
-    if (item.pass < 0) return;
-    top_record(P, P.trs[item.tr], item, recs + (int64_t)item.pad * kTopRecInts);
+    const TransformDesc tr = P.trs[item.tr];
+    ItemRec* r = recs + q;
+    r->item = item;
+    r->tr = tr;
+    const int stage = item.pass < 0 ? 0 : item.pass + 1;
+    r->need = stage > 0 ? stage_count[item.tr * kMaxStages + stage - 1] : 0;
+    if (item.pass >= 0) top_record(P, tr, item, r->top);
 }
 
-__device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item, float* smem) {
+// Returns whether a later stage of the transform waits for this item (not the last pass).
+// `rec`: the item's interval table and layout (top_record), or null to build it here.
+template <class Hook>
+__device__ __forceinline__ bool top_item(const TopParams& P, const WorkItem item,
+                                         const TransformDesc& tr, const int* rec, float* smem,
+                                         Hook& hook) {
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = kTopThreads / 32;
 
-    const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
     const int p = tr.p, m = tr.m;
     const int npass = top_passes(tr.depth, tr.chunk);
     const int pass = item.pass;
@@ -857,20 +938,21 @@ __device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item
     const TopLayout lay = top_layout(K, L, p, P.widths.wmax, score);
 
     // ---- the item's record: intervals, shared-memory layout, descriptor counts
-    int* tab = reinterpret_cast<int*>(smem + lay.table);
-    const int* lvl_desc = tab + kRecLvl;  // first descriptor of each level, levels L-1..0, + end
-    if (P.recs) {
-        const int* src = P.recs + (int64_t)item.pad * kTopRecInts;
-        if (tid < kTopRecInts) tab[tid] = src[tid];
-    } else if (tid == 0) {
-        top_record(P, tr, item, tab);
+    const int* tab = rec;
+    if (!rec) {
+        int* t = reinterpret_cast<int*>(smem + lay.table);
+        if (tid == 0) top_record(P, tr, item, t);
+        tab = t;
     }
-    if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
+    const int* lvl_desc = tab + kRecLvl;  // first descriptor of each level, levels L-1..0, + end
+    if constexpr (Hook::kInitEachItem) {
+        if (tid == 0) mbar_init(bar, 1);
+        __syncthreads();
+    }
     const int st0 = tab[0], lo0 = tab[2], hi0 = tab[3];
     if (lo0 > hi0) {  // uniform: block past the end of a smaller node
-        if (tid == 0) mbar_inval(bar);
-        return;
+        if (Hook::kInitEachItem && tid == 0) mbar_inval(bar);
+        return !last;
     }
 
     // ---- gather the needed rows of the depth-d_in transforms: one bulk copy per interval,
@@ -920,14 +1002,17 @@ __device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item
         desc[q] = d;
     }
 
-    const bool landed = bytes == 0 || mbar_wait_bounded(bar, 0);
+    hook.run();
+    const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity());
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
             atomicOr(P.status, kDevTimeout);
-            mbar_wait_bounded(bar, 0);
+            mbar_wait_bounded(bar, hook.parity());
         }
-        return;
+        hook.fail();
+        return !last;
     }
+    if (bytes) hook.copied();
 
     // ---- merge levels L-1 .. 1, and level 0 unless it is scored straight from level 1
     const bool fused = score && p <= kSnrHalfMaxP;
@@ -968,7 +1053,8 @@ __device__ __forceinline__ void top_item(const TopParams& P, const WorkItem item
         for (int e = tid; e < rows0 * p; e += kTopThreads) dst[e] = smem[o0 + e];
     }
     __syncthreads();
-    if (tid == 0) mbar_inval(bar);
+    if (Hook::kInitEachItem && tid == 0) mbar_inval(bar);
+    return !last;
 }
 
 __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(TopParams P) {
@@ -976,7 +1062,9 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
     const WorkItem item = P.items ? P.items[blockIdx.x]
                                   : WorkItem{0, (int)blockIdx.x, (int16_t)P.single_pass,
                                              (int16_t)P.single_rows, 0};
-    top_item(P, item, smem);
+    const TransformDesc tr = P.trs ? P.trs[item.tr] : P.single;
+    NoHook hook;
+    top_item(P, item, tr, nullptr, smem, hook);
 }
 
 // ---------------------------------------------------------------------------------
@@ -986,62 +1074,123 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
 // first waits until every item of stage s - 1 of its transform has completed.  The
 // queue lists all items of a stage before any item of the next stage of the same
 // transform, and a CTA never waits on an item listed after its own, so every wait
-// ends: the items it waits on were taken earlier by CTAs that are running.  Waits are
-// bounded (about 1 s); on expiry the status word gets kDevTimeout and all CTAs stop.
-// Completion: every thread fences its stores, the CTA synchronises, one thread adds to
-// the stage counter.  The waiting thread acquires the counter, then orders the async
-// (bulk-copy) proxy after it before the item's rows are copied in.
+// ends: the items it waits on were taken earlier by CTAs that are running (a CTA may
+// hold two claimed items ahead of the one it runs; claims are in queue order, so the
+// smallest unfinished item is always running).  Completions are released one item
+// late, at the next item's copy wait or before any wait of the CTA, so a held
+// completion never blocks anyone.  Waits are bounded (about 1 s); on expiry the
+// status word gets kDevTimeout and all CTAs stop at their next claim.
+// Each item starts from its record (ItemRec), fetched by one bulk copy while the item
+// before it runs.  Completion: the CTA synchronises, then one thread waits for its bulk
+// stores, fences at device scope and adds to the stage counter.  The waiting thread
+// acquires the counter, then orders the async (bulk-copy) proxy after it before the
+// item's rows are copied in.
 // ---------------------------------------------------------------------------------
 static_assert(kBottomThreads == kTopThreads, "persistent CTAs run both item kinds");
 __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_kernel(PersistentParams P) {
     extern __shared__ __align__(16) float smem[];
-    int* slot = reinterpret_cast<int*>(smem + P.smem_floats);  // queue broadcast
+    int* slot = reinterpret_cast<int*>(smem + P.smem_floats);    // [0]: the item to run
+    uint64_t* rbar = reinterpret_cast<uint64_t*>(slot + 4);      // barriers of the two records
+    ItemRec* rbuf = reinterpret_cast<ItemRec*>(slot + 8);        // the two record buffers
     const int tid = threadIdx.x;
-    // Thread 0 claims the next item while the current one runs, so the atomic's latency
-    // is hidden.  The claimed item is always listed after the running one, so the
-    // smallest unfinished item is always running and every wait still ends.
-    int next = 0;
-    if (tid == 0) next = atomicAdd(P.queue, 1);
+    // thread 0: queue positions claimed (a runs next, then b, then c); the status word is
+    // read one item ahead too (a relaxed load whose latency the item's work hides)
+    int a = P.nitems, b = P.nitems, c = P.nitems;
+    unsigned stat = 0, rpar = 0;  // rpar: parity of each record barrier's next phase
+    int rb = 0;                   // record buffer of the running item (all threads)
+    QueueHook hook;
+    if (tid == 0) {
+        mbar_init(&rbar[0], 1);
+        mbar_init(&rbar[1], 1);
+        mbar_init(reinterpret_cast<uint64_t*>(smem), 1);  // the items' copy barrier
+        a = atomicAdd(P.queue, 1);
+        b = atomicAdd(P.queue, 1);
+        if (a < P.nitems) {
+            mbar_expect_tx(&rbar[0], (unsigned)sizeof(ItemRec));
+            bulk_g2s(&rbuf[0], P.recs + a, (unsigned)sizeof(ItemRec), &rbar[0]);
+            hook.inflight = 1u;
+        }
+    }
     for (;;) {
+        // thread 0 alone waits for the item's record and, for a stage s > 0, for all items of
+        // stage s - 1 of its transform; the barrier then hands both to the CTA.  slot[0] is
+        // rewritten only after the barrier at the end of the item, when every thread has
+        // read it.
         if (tid == 0) {
-            int q = next;
-            if (*reinterpret_cast<volatile unsigned*>(P.bottom.status) & kDevTimeout) q = P.nitems;
+            int q = (stat & kDevTimeout) ? P.nitems : a;
+            if (q < P.nitems) {
+                if (!mbar_wait_bounded(&rbar[rb], (rpar >> rb) & 1u)) {
+                    atomicOr(P.bottom.status, kDevTimeout);
+                    q = P.nitems;
+                } else {
+                    rpar ^= 1u << rb;
+                    hook.inflight &= ~(1u << rb);
+                    const ItemRec& R = rbuf[rb];
+                    const int stage = R.item.pass < 0 ? 0 : R.item.pass + 1;
+                    if (stage > 0) {
+                        if (hook.pend) {  // release before waiting on anyone
+                            release_count(hook.pend);
+                            hook.pend = nullptr;
+                        }
+                        const int* cnt = P.done + R.item.tr * kMaxStages + stage - 1;
+                        const long long t0 = clock64();
+                        for (;;) {
+                            int seen;
+                            asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(seen) : "l"(cnt) : "memory");
+                            if (seen >= R.need) break;
+                            if (clock64() - t0 > (1LL << 31)) {
+                                atomicOr(P.bottom.status, kDevTimeout);
+                                q = P.nitems;
+                                break;
+                            }
+                            __nanosleep(256);
+                        }
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                    }
+                }
+            }
             slot[0] = q;
         }
         __syncthreads();
         const int q = slot[0];
-        __syncthreads();
         if (q >= P.nitems) break;
-        if (tid == 0) next = atomicAdd(P.queue, 1);
-        const WorkItem item = P.items[q];
+        const ItemRec& R = rbuf[rb];
+        const WorkItem item = R.item;
+        const TransformDesc tr = R.tr;
         const int stage = item.pass < 0 ? 0 : item.pass + 1;
-        if (stage > 0) {
-            if (tid == 0) {
-                const int* cnt = P.done + item.tr * kMaxStages + stage - 1;
-                const int need = P.stage_count[item.tr * kMaxStages + stage - 1];
-                const long long t0 = clock64();
-                int seen = 0;
-                for (;;) {
-                    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(seen) : "l"(cnt) : "memory");
-                    if (seen >= need) break;
-                    if (clock64() - t0 > (1LL << 31)) {
-                        atomicOr(P.bottom.status, kDevTimeout);
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-                asm volatile("fence.proxy.async.global;" ::: "memory");
-                slot[1] = seen >= need;
-            }
-            __syncthreads();
-            if (!slot[1]) break;
+        if (tid == 0) {
+            c = atomicAdd(P.queue, 1);
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(stat) : "l"(P.bottom.status) : "memory");
+            // the next item's record goes to the other buffer
+            hook.armed = true;
+            hook.src = b < P.nitems ? P.recs + b : nullptr;
+            hook.dst = &rbuf[rb ^ 1];
+            hook.bar = &rbar[rb ^ 1];
+            hook.bit = 1u << (rb ^ 1);
         }
-        if (item.pass == -2) bottom_item<true>(P.bottom_snr, item, smem);
-        else if (item.pass == -1) bottom_item<false>(P.bottom, item, smem);
-        else top_item(P.top, item, smem);
-        __threadfence();
+        bool signal = false;
+        if (item.pass == -2) bottom_item<true>(P.bottom_snr, item, tr, smem, hook);
+        else if (item.pass == -1) {
+            bottom_item<false>(P.bottom, item, tr, smem, hook);
+            signal = true;
+        } else {
+            signal = top_item(P.top, item, tr, R.top, smem, hook);
+        }
         __syncthreads();
-        if (tid == 0 && item.pass != -2) atomicAdd(P.done + item.tr * kMaxStages + stage, 1);
+        if (hook.failed) break;  // a copy wait ran out (uniform)
+        if (tid == 0) {
+            hook.run();  // an item that returned before its copy wait
+            if (signal) hook.pend = P.done + item.tr * kMaxStages + stage;
+        }
+        rb ^= 1;
+        a = b;
+        b = c;
+    }
+    if (tid == 0) {
+        if (hook.pend) release_count(hook.pend);
+        // a record fetch still in flight lands before the CTA exits
+        for (int j = 0; j < 2; ++j)
+            if ((hook.inflight >> j) & 1u) mbar_wait_bounded(&rbar[j], (rpar >> j) & 1u);
     }
 }
 
@@ -1233,11 +1382,12 @@ cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_top_prep(const TopParams& P, int nitems, int ntop, int* recs, cudaStream_t s) {
-    if (nitems <= 0 || ntop <= 0) return cudaSuccess;
-    LaunchScope ls(kTopPrep, 16.0 * nitems + 4.0 * kTopRecInts * ntop, s);
-    top_prep_kernel<<<(unsigned)((nitems + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
-        P, nitems, recs);
+cudaError_t launch_item_recs(const TopParams& P, const int* stage_count, int nitems, ItemRec* recs,
+                             cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    LaunchScope ls(kItemRecs, (16.0 + sizeof(TransformDesc) + sizeof(ItemRec)) * nitems, s);
+    item_rec_kernel<<<(unsigned)((nitems + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
+        P, stage_count, nitems, recs);
     return cudaGetLastError();
 }
 
