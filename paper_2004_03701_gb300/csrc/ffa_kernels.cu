@@ -524,41 +524,65 @@ __device__ __forceinline__ double trial_period(double tau, int p, int m, int s) 
 // One merge (Eq. ffa_merge_rule) of shared-memory rows by one warp:
 //   sm[o + x] = sm[a + x] + sm[b + (x + k) mod p],   0 <= k < p.
 // Offsets are in floats from the shared-memory base; lanes take consecutive columns.
-// A lane's columns are taken in groups of 4, all 8 loads of a group before its adds,
-// so that a warp keeps many shared-memory loads in flight.
-__device__ __forceinline__ void merge_row(float* sm, int o, int a, int b, int k, int p, int lane) {
-    const float* pa = sm + a + lane;
-    const float* pb = sm + b + k + lane;  // T[(x + k) mod p] = pb[32 t], or pb[32 t - p] once wrapped
-    float* po = sm + o + lane;
-    const int wrap = p - k - lane;        // column slot t has wrapped once 32 t >= wrap
-    const int nslot = (p - lane + 31) >> 5;
-    for (int t0 = 0; t0 < nslot; t0 += 4) {
-        float hv[4], tv[4];
+// Columns x0 + lane + 32 t, t < NS: the body is fully unrolled and every load of the
+// lane is issued before its first add (a runtime-bounded slot loop runs at two thirds of
+// this rate).  A slot past the end of the row neither loads nor stores.
+template <int NS>
+__device__ __forceinline__ void merge_cols(float* sm, int o, int a, int b, int k, int p, int x0,
+                                           int lane) {
+    int kb = x0 + k;  // (x0 + k) mod p, for x0, k < p
+    if (kb >= p) kb -= p;
+    const float* pa = sm + a + x0 + lane;
+    const float* pb = sm + b + kb + lane;  // T[(x + k) mod p] = pb[32 t], or pb[32 t - p] once wrapped
+    float* po = sm + o + x0 + lane;
+    const int wrap = p - kb - lane;        // slot t has wrapped once 32 t >= wrap
+    const int lim = p - x0 - lane;         // slot t lies in the row while 32 t < lim
+    float hv[NS], tv[NS];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int t = t0 + u;
-            if (t < nslot) {
-                hv[u] = pa[32 * t];
-                tv[u] = pb[32 * t - (32 * t >= wrap ? p : 0)];
-            }
+    for (int t = 0; t < NS; ++t) {
+        if (32 * t < lim) {
+            hv[t] = pa[32 * t];
+            tv[t] = pb[32 * t - (32 * t >= wrap ? p : 0)];
+        } else {
+            hv[t] = 0.f;
+            tv[t] = 0.f;
         }
+    }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (t0 + u < nslot) po[32 * (t0 + u)] = __fadd_rn(hv[u], tv[u]);
+    for (int t = 0; t < NS; ++t)
+        if (32 * t < lim) po[32 * t] = __fadd_rn(hv[t], tv[t]);
+}
+template <int NS>
+__device__ __forceinline__ void copy_cols(float* sm, int o, int a, int p, int x0, int lane) {
+    const float* pa = sm + a + x0 + lane;
+    float* po = sm + o + x0 + lane;
+    const int lim = p - x0 - lane;
+    float v[NS];
+#pragma unroll
+    for (int t = 0; t < NS; ++t) v[t] = 32 * t < lim ? pa[32 * t] : 0.f;
+#pragma unroll
+    for (int t = 0; t < NS; ++t)
+        if (32 * t < lim) po[32 * t] = v[t];
+}
+// A whole row: one unrolled body for rows of up to 512 columns, 256-column pieces beyond.
+__device__ __forceinline__ void merge_row(float* sm, int o, int a, int b, int k, int p, int lane) {
+    switch ((p + 31) >> 5) {
+#define FFA_MR(N) case N: merge_cols<N>(sm, o, a, b, k, p, 0, lane); return;
+        FFA_MR(1) FFA_MR(2) FFA_MR(3) FFA_MR(4) FFA_MR(5) FFA_MR(6) FFA_MR(7) FFA_MR(8)
+        FFA_MR(9) FFA_MR(10) FFA_MR(11) FFA_MR(12) FFA_MR(13) FFA_MR(14) FFA_MR(15) FFA_MR(16)
+#undef FFA_MR
+        default:
+            for (int x0 = 0; x0 < p; x0 += 256) merge_cols<8>(sm, o, a, b, k, p, x0, lane);
     }
 }
 __device__ __forceinline__ void copy_row(float* sm, int o, int a, int p, int lane) {
-    const float* pa = sm + a + lane;
-    float* po = sm + o + lane;
-    const int nslot = (p - lane + 31) >> 5;
-    for (int t0 = 0; t0 < nslot; t0 += 4) {
-        float v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (t0 + u < nslot) v[u] = pa[32 * (t0 + u)];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (t0 + u < nslot) po[32 * (t0 + u)] = v[u];
+    switch ((p + 31) >> 5) {
+#define FFA_CR(N) case N: copy_cols<N>(sm, o, a, p, 0, lane); return;
+        FFA_CR(1) FFA_CR(2) FFA_CR(3) FFA_CR(4) FFA_CR(5) FFA_CR(6) FFA_CR(7) FFA_CR(8)
+        FFA_CR(9) FFA_CR(10) FFA_CR(11) FFA_CR(12) FFA_CR(13) FFA_CR(14) FFA_CR(15) FFA_CR(16)
+#undef FFA_CR
+        default:
+            for (int x0 = 0; x0 < p; x0 += 256) copy_cols<8>(sm, o, a, p, x0, lane);
     }
 }
 
