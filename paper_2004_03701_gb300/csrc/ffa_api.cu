@@ -157,6 +157,10 @@ struct Plan {
     int bottom0_snr_floats = 0;
     int row_cap = kBottomMaxRows;  // sub-tree row limit (lowered if a launch's mix overflows)
     std::vector<int> stage_count;
+    std::vector<int> batch_top;   // per scratch batch: its last-pass items
+    int ring = 1, nbatches = 0;   // scratch ring slots; batch b uses slot b % ring
+    int64_t slot_floats = 0;      // floats of one ring slot (per scratch buffer)
+    int ntop = 0;                 // top-pass items (tables made on the device)
     int bottom_nmax = 0, bottom_elems = 0;
     int smem_floats = 0;
     int nitems = 0;
@@ -167,7 +171,8 @@ struct Plan {
     int max_rows = 0, max_p = 0;
     int64_t nchunks = 0, prefix_len = 0, input_total = 0;
     // workspace layout (bytes)
-    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, o_dsblk = 0, o_stcnt = 0, o_recs = 0;
+    size_t o_tables = 0, o_oct = 0, o_trs = 0, o_items = 0, o_dsblk = 0, o_stcnt = 0, o_btop = 0;
+    size_t o_heads = 0, o_toptab = 0;
     size_t o_segs = 0, o_blkseg = 0;
     size_t tables_bytes = 0;
     size_t o_prefix = 0, o_partial = 0, o_ds = 0, o_s0 = 0, o_s1 = 0, ws_bytes = 0;
@@ -181,7 +186,22 @@ struct Plan {
 constexpr size_t kStatusBytes = 256;
 constexpr ffa_status kRetrySmaller = -1;  // internal: a launch's sub-tree mix overflows
 std::mutex g_plan_mu;
-constexpr int64_t kBatchFloats = int64_t(6) << 20;  // folded samples per batch of transforms
+// Folded samples per scratch batch of transforms.  The queue lists stage s of batch b on
+// diagonal b + kStageStride * s, so that the items of a stage are listed about two
+// diagonals (several batches of work) after the items they wait for.  The scratch is a
+// ring of slots, one batch in each, reused by the batch `ring` places later, with ring =
+// kStageStride * (the most stages of any transform): the sub-trees that overwrite a slot
+// are then listed about kStageStride diagonals after the last reads of the batch it held.
+// With 3M floats per batch the ring of two buffers is 144 MB for three stages (about the
+// 126 MB L2; the slots last written are the ones read next).
+#ifndef FFA_BATCH_MFLOATS
+#define FFA_BATCH_MFLOATS 3
+#endif
+#ifndef FFA_STAGE_STRIDE
+#define FFA_STAGE_STRIDE 2
+#endif
+constexpr int64_t kBatchFloats = int64_t(FFA_BATCH_MFLOATS) << 20;
+constexpr int kStageStride = FFA_STAGE_STRIDE;
 
 // Rows of one shared-memory sub-tree of p bins: the most (at most row_cap) whose
 // layout fits in shared memory.
@@ -381,9 +401,12 @@ ffa_status build_plan(Plan& pl) {
     }
     std::vector<std::vector<int>> batches;
     {
-        int64_t bf = 0, scratch = 0;
+        int64_t bf = 0;
+        std::vector<int64_t> off;  // offset of each transform within its batch
+        off.assign(pl.trs.size(), 0);
         for (size_t t = 0; t < pl.trs.size(); ++t) {
             TransformDesc& d = pl.trs[t];
+            d.batch = -1;
             if (d.depth == 0) continue;
             const int64_t need = (int64_t)d.m * d.p;
             if (batches.empty() || bf + need > kBatchFloats) {
@@ -391,14 +414,17 @@ ffa_status build_plan(Plan& pl) {
                 bf = 0;
             }
             batches.back().push_back((int)t);
-            bf += need;
-            d.scratch_off = scratch;
-            scratch += (int64_t)align_up((size_t)need, 4);
+            d.batch = (int)batches.size() - 1;
+            off[t] = bf;
+            bf += (int64_t)align_up((size_t)need, 4);
+            pl.slot_floats = std::max(pl.slot_floats, bf);
         }
-        pl.scratch_floats = scratch;
+        pl.nbatches = (int)batches.size();
+        for (size_t t = 0; t < pl.trs.size(); ++t) pl.trs[t].scratch_off = off[t];  // + slot, below
     }
     // items of each (batch, stage)
     std::vector<std::vector<std::vector<WorkItem>>> st_items(batches.size());
+    pl.batch_top.assign(batches.size(), 0);
     int max_stage = 0;
     for (size_t b = 0; b < batches.size(); ++b) {
         auto& sv = st_items[b];
@@ -426,16 +452,29 @@ ffa_status build_plan(Plan& pl) {
                 const int lim = score ? d.kept : nmax;
                 const int nb = (lim + K - 1) / K;
                 const int cnt = score ? nb : (1 << dout) * nb;
-                for (int i = 0; i < cnt; ++i)
-                    sv[j + 1].push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, 0});
+                for (int i = 0; i < cnt; ++i)  // pad: the item's table (made on the device)
+                    sv[j + 1].push_back(WorkItem{t, i, (int16_t)j, (int16_t)K, pl.ntop++});
                 pl.stage_count[(size_t)t * kMaxStages + j + 1] = cnt;
+                if (score) pl.batch_top[b] += cnt;
             }
         }
         max_stage = std::max(max_stage, (int)sv.size());
     }
-    for (int diag = 0; diag < (int)batches.size() + max_stage; ++diag)
+    // The ring: batch b writes slot b % ring once batch b - ring has finished reading it.
+    // Batch b's sub-trees are listed on diagonal b, after every item of batch b - ring
+    // (diagonals up to b - ring + kStageStride (max_stage - 1) < b), so the wait always
+    // ends; within a diagonal the later stages come first.
+#ifdef FFA_RING_SLOTS
+    pl.ring = std::max(1, std::min(std::max(FFA_RING_SLOTS, kStageStride * max_stage), std::max(pl.nbatches, 1)));
+#else
+    pl.ring = std::max(1, std::min(kStageStride * max_stage, std::max(pl.nbatches, 1)));
+#endif
+    for (TransformDesc& d : pl.trs)
+        if (d.batch >= 0) d.scratch_off += (int64_t)(d.batch % pl.ring) * pl.slot_floats;
+    pl.scratch_floats = (int64_t)pl.ring * pl.slot_floats;
+    for (int diag = 0; diag < (int)batches.size() + kStageStride * max_stage; ++diag)
         for (int s = max_stage - 1; s >= 0; --s) {
-            const int b = diag - s;
+            const int b = diag - kStageStride * s;
             if (b < 0 || b >= (int)batches.size() || s >= (int)st_items[b].size()) continue;
             pl.items.insert(pl.items.end(), st_items[b][s].begin(), st_items[b][s].end());
         }
@@ -446,8 +485,8 @@ ffa_status build_plan(Plan& pl) {
     if (pl.smem_floats * 4 + kPersistExtraBytes > kSmemBytes) return kRetrySmaller;
     pl.nitems = (int)pl.items.size();
 
-    // Tables: octaves | transforms | items | downsampling CTAs | stage counts | prefix
-    // series | prefix chunks, each 256-byte aligned.
+    // Tables: octaves | transforms | items | downsampling CTAs | stage counts | batch
+    // top-pass counts | prefix series | prefix chunks, each 256-byte aligned.
     size_t o = 0;
     pl.o_oct = o;
     o = align_up(o + pl.oct.size() * sizeof(OctaveDesc), 256);
@@ -459,14 +498,16 @@ ffa_status build_plan(Plan& pl) {
     o = align_up(o + pl.ds_blocks.size() * sizeof(int2), 256);
     pl.o_stcnt = o;
     o = align_up(o + pl.stage_count.size() * sizeof(int), 256);
+    pl.o_btop = o;
+    o = align_up(o + pl.batch_top.size() * sizeof(int), 256);
     pl.o_segs = o;
     o = align_up(o + pl.segs.size() * sizeof(PrefixSeg), 256);
     pl.o_blkseg = o;
     o = align_up(o + pl.blk_seg.size() * sizeof(int), 256);
     pl.tables_bytes = std::max<size_t>(o, 256);
 
-    // Workspace: status | tables | prefix | chunk sums | octave series | scratch 0 |
-    // scratch 1 | stage counters | item records
+    // Workspace: status | tables | prefix | chunk sums | octave series | scratch ring 0 |
+    // scratch ring 1 | completion counters | item heads | top-pass tables
     pl.nchunks = (int64_t)pl.blk_seg.size();
     size_t w = kStatusBytes;
     pl.o_tables = w;
@@ -481,11 +522,13 @@ ffa_status build_plan(Plan& pl) {
     w = align_up(w + (size_t)pl.scratch_floats * 4, 256);
     pl.o_s1 = w;
     w = align_up(w + (size_t)pl.scratch_floats * 4, 256);
-    pl.o_counters = w;  // queue counter, then per transform and stage completions
-    pl.counter_bytes = (1 + pl.trs.size() * kMaxStages) * sizeof(int);
+    pl.o_counters = w;  // queue counter, then per (transform, stage) and per batch completions
+    pl.counter_bytes = (1 + pl.trs.size() * kMaxStages + pl.batch_top.size()) * sizeof(int);
     w = align_up(w + pl.counter_bytes, 256);
-    pl.o_recs = w;  // one record per queue position (built on the device)
-    w = align_up(w + (size_t)pl.nitems * sizeof(ItemRec), 256);
+    pl.o_heads = w;  // one head per queue position (made on the device)
+    w = align_up(w + (size_t)pl.nitems * sizeof(ItemHead), 256);
+    pl.o_toptab = w;  // one table per top-pass item (made on the device)
+    w = align_up(w + (size_t)pl.ntop * kTopRecBytes, 256);
     pl.ws_bytes = w;
     // host-buffer variant: + input and outputs
     pl.o_hx = w;
@@ -515,6 +558,7 @@ ffa_status ensure_pinned(Plan& pl) {
     std::memcpy(h + pl.o_items, pl.items.data(), pl.items.size() * sizeof(WorkItem));
     std::memcpy(h + pl.o_dsblk, pl.ds_blocks.data(), pl.ds_blocks.size() * sizeof(int2));
     std::memcpy(h + pl.o_stcnt, pl.stage_count.data(), pl.stage_count.size() * sizeof(int));
+    std::memcpy(h + pl.o_btop, pl.batch_top.data(), pl.batch_top.size() * sizeof(int));
     std::memcpy(h + pl.o_segs, pl.segs.data(), pl.segs.size() * sizeof(PrefixSeg));
     std::memcpy(h + pl.o_blkseg, pl.blk_seg.data(), pl.blk_seg.size() * sizeof(int));
     pl.pinned = p;
@@ -630,9 +674,11 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
         }
     }
     auto B = std::make_unique<Batch>();
-    // workspace of each series searched alone, the unit of the chunk budget
-    std::vector<size_t> est(nseries);
-    std::map<SeriesSpec, size_t> alone;  // series of the same shape plan alike
+    // workspace of each series searched alone, the unit of the chunk budget: its own
+    // part (tables, prefix sums, octave series, records) and its scratch ring, which the
+    // series of a chunk share (a chunk's ring is about the largest of theirs)
+    std::vector<size_t> est(nseries), ring(nseries);
+    std::map<SeriesSpec, std::pair<size_t, size_t>> alone;  // series of the same shape plan alike
     for (int i = 0; i < nseries; ++i) {
         SeriesSpec s = all[i];
         s.x_off = 0;
@@ -641,16 +687,22 @@ ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t*
             std::unique_ptr<Plan> p1;
             ffa_status st = make_plan_series({s}, h_widths, nw, tiles, &p1);
             if (st != FFA_OK) return st;
-            it = alone.emplace(s, p1->ws_bytes).first;
+            const size_t r = 2 * (size_t)p1->scratch_floats * 4;
+            it = alone.emplace(s, std::make_pair(p1->ws_bytes - std::min(r, p1->ws_bytes), r)).first;
         }
-        est[i] = it->second;
+        est[i] = it->second.first;
+        ring[i] = it->second.second;
     }
     std::map<std::vector<SeriesSpec>, std::shared_ptr<Plan>> shapes;
     int64_t trial = 0;
     for (int i = 0; i < nseries;) {
         int j = i;
-        size_t acc = 0;
-        while (j < nseries && (j == i || acc + est[j] <= budget)) acc += est[j++];
+        size_t acc = 0, rmax = 0;
+        while (j < nseries && (j == i || acc + est[j] + std::max(rmax, ring[j]) <= budget)) {
+            acc += est[j];
+            rmax = std::max(rmax, ring[j]);
+            ++j;
+        }
         std::vector<SeriesSpec> part(all.begin() + i, all.begin() + j);
         int64_t lo = part[0].x_off;
         for (const SeriesSpec& s : part) lo = std::min(lo, s.x_off);
@@ -756,13 +808,25 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     tp.foldbins = d_foldbins;
     tp.snr = d_snr;
     tp.status = status;
-    ItemRec* recs = reinterpret_cast<ItemRec*>(ws + pl.o_recs);
     tp.items = d_items;
+    ItemHead* heads = reinterpret_cast<ItemHead*>(ws + pl.o_heads);
+    int* toptab = reinterpret_cast<int*>(ws + pl.o_toptab);
+    pp.heads = heads;
+    pp.tables = toptab;
     pp.nitems = pl.nitems;
     pp.queue = counters;
     pp.done = counters + 1;
-    pp.recs = recs;
     pp.smem_floats = pl.smem_floats;
+    RecParams rp{};
+    rp.top = tp;
+    rp.stage_count = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt);
+    rp.batch_top = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_btop);
+    rp.nitems = pl.nitems;
+    rp.ring = pl.ring;
+    rp.nbatches = pl.nbatches;
+    rp.batch_base = (int)(pl.trs.size() * kMaxStages);
+    rp.heads = heads;
+    rp.tables = toptab;
 
     // ---- item records on a side stream, concurrent with prefix sums and
     //      downsampling (they need only the tables); joined before the FFA launch
@@ -773,9 +837,7 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
         FFA_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0), "cudaStreamWaitEvent(fork)");
         sp = side->s;
     }
-    FFA_CUDA(launch_item_recs(tp, reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt),
-                              pl.nitems, recs, sp),
-             "item record launch");
+    FFA_CUDA(launch_item_recs(rp, sp), "item record launch");
     if (sp != st) {
         FFA_CUDA(cudaEventRecord(side->join, sp), "cudaEventRecord(join)");
     }

@@ -96,7 +96,7 @@ __host__ __device__ inline void top_intervals(int st0, int n0, int lo0, int hi0,
 // One FFA transform of a search: base period p (bins), m rows of the octave series.
 struct TransformDesc {
     int64_t src_off;      // float offset of row 0 in the source buffer
-    int64_t scratch_off;  // float offset of row 0 in the scratch buffers
+    int64_t scratch_off;  // float offset of row 0 in the scratch buffers (its ring slot)
     int64_t trial0;       // index of its first trial in the periodogram
     double tau;           // sampling time of its octave (s)
     int32_t p;            // bins per row
@@ -105,8 +105,10 @@ struct TransformDesc {
     int32_t depth;        // depth of the shared-memory sub-trees (0 = whole tree)
     float inv_std;        // 1 / sqrt(m V_f): noise std of one folded bin, inverted
     int32_t chunk;        // merge levels per top pass (1..kTopMaxLevels)
+    int32_t batch;        // scratch batch of the transform (-1: whole tree, no scratch)
+    int32_t pad;
 };
-static_assert(sizeof(TransformDesc) == 56, "TransformDesc layout");
+static_assert(sizeof(TransformDesc) == 64, "TransformDesc layout");
 
 // A CTA's share of a launch: transform index, node / row-block index, and for the
 // top kernel the pass index and the rows per block.
@@ -349,32 +351,49 @@ struct TopParams {
 
 constexpr int kMaxStages = 16;  // sub-trees + up to 15 top passes per transform
 
-// Everything a persistent CTA needs to start the item at one queue position, in one
-// record that it fetches by a single bulk copy while the item before it runs: the work
-// item, its transform, the number of items of the stage it waits for, and for a top-pass
-// item its interval table and shared-memory layout (see kTopRecInts).
-struct ItemRec {
+// Everything a persistent CTA needs to start the item at one queue position, fetched by
+// one bulk copy two items ahead: the work item (for a top pass, WorkItem::pad indexes its
+// interval table, kTopRecInts ints fetched one item ahead), its transform, the completion
+// counter it waits for and the count that counter must reach, and the counter the item
+// releases when it completes.  Counters: per (transform, stage), the items of that stage
+// completed; per scratch batch, its last-pass items completed (the batch's ring slot is
+// free for the batch `ring` places later once all of them have read it).
+struct ItemHead {
     WorkItem item;
     TransformDesc tr;
-    int32_t need;                   // items of stage s - 1 of its transform (stage s > 0)
-    int32_t pad0;
-    int32_t top[kTopRecInts];
-    int32_t pad1[12];
+    int32_t wait;                   // counter index (-1: none)
+    int32_t need;
+    int32_t rel[2];                 // counter released on completion (-1: none); rel[1] unused
 };
-static_assert(sizeof(ItemRec) == 640, "ItemRec layout (a multiple of 16 bytes)");
+static_assert(sizeof(ItemHead) == 96, "ItemHead layout (a multiple of 16 bytes)");
+constexpr int kTopRecBytes = kTopRecInts * 4;
 // Shared memory of the persistent kernel after the item layouts: the queue slot (16 B),
-// two record barriers (16 B) and two records (the running item's and the next one's).
-constexpr int kPersistExtraBytes = 32 + 2 * (int)sizeof(ItemRec);
+// five barriers (three heads, two tables; 48 B with padding), three heads and two tables.
+constexpr int kPersistExtraBytes = 64 + 3 * (int)sizeof(ItemHead) + 2 * kTopRecBytes;
 
 struct PersistentParams {
     BottomParams bottom;            // sub-tree items (pass -1)
     BottomParams bottom_snr;        // whole-tree items scored directly (pass -2)
     TopParams top;                  // top-pass items (pass >= 0)
-    const ItemRec* recs;            // one per queue position
+    const ItemHead* heads;          // one per queue position
+    const int* tables;              // kTopRecInts per top-pass item (WorkItem::pad)
     int nitems;
     int* queue;                     // dispatch counter, zero at launch
-    int* done;                      // per transform and stage: items completed, zero at launch
+    int* done;                      // completion counters, zero at launch
     int smem_floats;                // dynamic shared floats before the queue slot (a multiple of 4)
+};
+
+// The per-item records of a queue, made on the device before the FFA launch.
+struct RecParams {
+    TopParams top;                  // items, transforms, scratch buffers (for the tables)
+    const int* stage_count;         // per transform and stage: items listed
+    const int* batch_top;           // per scratch batch: its last-pass items
+    int nitems;
+    int ring;                       // scratch ring slots (a batch reuses slot batch % ring)
+    int nbatches;
+    int batch_base;                 // index of batch 0's counter among the counters
+    ItemHead* heads;
+    int* tables;
 };
 
 struct SnrParams {
@@ -404,8 +423,7 @@ cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bo
                           cudaStream_t s);
 cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s);
 cudaError_t launch_persistent(const PersistentParams& P, int smem_bytes, cudaStream_t s);
-cudaError_t launch_item_recs(const TopParams& P, const int* stage_count, int nitems, ItemRec* recs,
-                             cudaStream_t s);
+cudaError_t launch_item_recs(const RecParams& R, cudaStream_t s);
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s);
 cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s);
 constexpr int kNormaliseBlocks = 1216;  // 8 CTAs per SM

@@ -263,9 +263,19 @@ __device__ __forceinline__ void mbar_inval(uint64_t* bar) {
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// L2 policy of the scratch ring: keep its lines (they are read a few batches later and
+// then overwritten, so written back to memory only if evicted).
+__device__ __forceinline__ uint64_t policy_keep() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(float* p, float v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
 __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, unsigned bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
-                 "r"(smem_addr(src)), "r"(bytes)
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+                 "r"(smem_addr(src)), "r"(bytes), "l"(policy_keep())
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
@@ -291,6 +301,15 @@ __device__ __forceinline__ void release_count(int* cnt) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(cnt) : "memory");
 }
+// Global -> shared bulk copy of scratch-ring rows (the ring's L2 policy).
+__device__ __forceinline__ void bulk_g2s_keep(void* dst, const void* src, unsigned bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy_keep())
+        : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
                                          uint64_t* bar) {
     asm volatile(
@@ -312,26 +331,48 @@ struct QueueHook {
     static constexpr bool kInitEachItem = false;  // the copy barrier is made once per CTA
     unsigned cpar = 0;              // parity of the copy barrier's next phase (all threads)
     bool failed = false;            // a copy wait of the item ran out (all threads)
-    int* pend = nullptr;            // completion counter of the item before, not yet released
-    const ItemRec* src = nullptr;   // record of the next item (null: none)
-    ItemRec* dst = nullptr;         // its shared-memory buffer and barrier
-    uint64_t* bar = nullptr;
-    unsigned inflight = 0;          // bit per record buffer: a fetch is in flight
-    unsigned bit = 0;
+    // thread 0 only:
+    int* done = nullptr;            // the completion counters
+    int pend[2] = {-1, -1};         // counters of the item before, not yet released
+    const ItemHead* next = nullptr; // head of the next item (in shared memory), or null
+    uint64_t* next_bar = nullptr;   // its barrier, whose phase `next_par` completes it
+    unsigned next_par = 0;
+    const int* table_src = nullptr; // the top-pass tables in global memory
+    int* table_dst = nullptr;       // the next item's table buffer and barrier
+    uint64_t* table_bar = nullptr;
+    const ItemHead* head_src = nullptr;  // head of the item after the next, or null
+    ItemHead* head_dst = nullptr;
+    uint64_t* head_bar = nullptr;
+    unsigned issued = 0;            // set: the table copy was issued (bit 0), the head copy (bit 1)
     bool armed = false;
+    bool timed_out = false;
+    __device__ __forceinline__ void release() {
+        for (int j = 0; j < 2; ++j)
+            if (pend[j] >= 0) {
+                release_count(done + pend[j]);
+                pend[j] = -1;
+            }
+    }
     __device__ __forceinline__ void run() {
         if (threadIdx.x != 0 || !armed) return;
         armed = false;
-        if (pend) {
-            release_count(pend);
-            pend = nullptr;
+        release();
+        // (the buffers were last read by earlier items, whose reads had all returned
+        // before the barrier that ended them, so the copies may overwrite them)
+        if (next) {  // the next item's head (fetched one item ago) says whether it has a table
+            if (!mbar_wait_bounded(next_bar, next_par)) {
+                timed_out = true;
+            } else if (next->item.pass >= 0) {
+                mbar_expect_tx(table_bar, (unsigned)kTopRecBytes);
+                bulk_g2s(table_dst, table_src + (int64_t)next->item.pad * kTopRecInts,
+                         (unsigned)kTopRecBytes, table_bar);
+                issued |= 1u;
+            }
         }
-        if (src) {
-            // the buffer was last read through the generic proxy (the item before)
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(bar, (unsigned)sizeof(ItemRec));
-            bulk_g2s(dst, src, (unsigned)sizeof(ItemRec), bar);
-            inflight |= bit;
+        if (head_src) {
+            mbar_expect_tx(head_bar, (unsigned)sizeof(ItemHead));
+            bulk_g2s(head_dst, head_src, (unsigned)sizeof(ItemHead), head_bar);
+            issued |= 2u;
         }
     }
     // the shared memory of the item's bulk stores may be reused (their global completion
@@ -599,10 +640,12 @@ __device__ __forceinline__ unsigned bulk_bytes(const float* src, int total) {
     return total > lead ? (unsigned)(((total - lead) & ~3) * 4) : 0u;
 }
 __device__ __forceinline__ void issue_rows_copy(float* sm, int dst, const float* src, int total,
-                                                uint64_t* bar) {
+                                                uint64_t* bar, bool keep = false) {
     const int lead = bulk_lead(src);
     const unsigned bytes = bulk_bytes(src, total);
-    if (bytes) bulk_g2s(sm + dst + lead, src + lead, bytes, bar);
+    if (!bytes) return;
+    if (keep) bulk_g2s_keep(sm + dst + lead, src + lead, bytes, bar);
+    else bulk_g2s(sm + dst + lead, src + lead, bytes, bar);
 }
 __device__ __forceinline__ void load_row_ends(float* sm, int dst, const float* src, int total,
                                               int tid, int nthreads) {
@@ -723,42 +766,51 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     const float* src = P.src + tr.src_off + (int64_t)start * p;
     const int total = n * p;
     const int a0 = lay.buf_a + (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
-    if constexpr (Hook::kInitEachItem) {
-        if (tid == 0) mbar_init(bar, 1);
-        __syncthreads();
-    }
-    const unsigned bytes = bulk_bytes(src, total);
-    if (tid == 0 && bytes) {
-        mbar_expect_tx(bar, bytes);  // the single arrival of this barrier phase
-        issue_rows_copy(smem, a0, src, total, bar);
-    }
-    load_row_ends(smem, a0, src, total, tid, kBottomThreads);
-    const int H = tree_height(n);
-    // nodes of the register stage: height <= kRegLevels, parent higher (one per start row)
     int* rnodes = reinterpret_cast<int*>(smem + lay.nodes);
     int& nreg = reinterpret_cast<int*>(smem)[2];           // header: barrier, then 2 ints
     int& regmax = reinterpret_cast<int*>(smem)[3];
-    if (tid == 0) { nreg = 0; regmax = 1; }
-    __syncthreads();
-    for (int r = tid; r < n; r += kBottomThreads) {
-        int st = 0, sz = n;
-        while (tree_height(sz) > kRegLevels) {
-            const int nh = sz >> 1;
-            if (r - st >= nh) { st += nh; sz -= nh; } else { sz = nh; }
+    if constexpr (Hook::kInitEachItem) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            nreg = 0;
+            regmax = 1;
         }
-        if (r == st) {
-            const int q = atomicAdd(&nreg, 1);
-            rnodes[q] = st | (sz << 16);
-            atomicMax(&regmax, sz);
+        __syncthreads();
+    }
+    const unsigned bytes = bulk_bytes(src, total);
+    const int H = tree_height(n);
+    // Warp 0 runs the hook (thread 0: release the item before, fetch the next records)
+    // while warps 1.. issue the copy and make the item's tables (the persistent loop has
+    // reset nreg and regmax before its claim barrier).
+    if (warp == 0) {
+        hook.run();
+    } else {
+        const int t = tid - 32, nt = kBottomThreads - 32;
+        if (t == 0 && bytes) {
+            mbar_expect_tx(bar, bytes);  // the single arrival of this barrier phase
+            issue_rows_copy(smem, a0, src, total, bar);
+        }
+        load_row_ends(smem, a0, src, total, t, nt);
+        // nodes of the register stage: height <= kRegLevels, parent higher (one per start row)
+        for (int r = t; r < n; r += nt) {
+            int st = 0, sz = n;
+            while (tree_height(sz) > kRegLevels) {
+                const int nh = sz >> 1;
+                if (r - st >= nh) { st += nh; sz -= nh; } else { sz = nh; }
+            }
+            if (r == st) {
+                const int q = atomicAdd(&nreg, 1);
+                rnodes[q] = st | (sz << 16);
+                atomicMax(&regmax, sz);
+            }
+        }
+        // row descriptors of every shared-memory level, made while the rows are in flight
+        const int nlev = H - kRegLevels;
+        for (int e = t; e < nlev * n; e += nt) {
+            const int l = e / n, r = e - l * n;
+            desc[l * P.nmax + r] = bottom_desc(n, kRegLevels + 1 + l, r, p);
         }
     }
-    // row descriptors of every shared-memory level, made while the rows are in flight
-    const int nlev = H - kRegLevels;
-    for (int e = tid; e < nlev * n; e += kBottomThreads) {
-        const int l = e / n, r = e - l * n;
-        desc[l * P.nmax + r] = bottom_desc(n, kRegLevels + 1 + l, r, p);
-    }
-    hook.run();
     const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity());
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
@@ -920,22 +972,44 @@ __device__ void top_record(const TopParams& P, const TransformDesc& tr, const Wo
     r[kRecBytes] = (int)bytes;
 }
 
-// The records of all queue positions (ItemRec), one thread each: the work item, its
-// transform, the item count of the stage it waits for and, for a top-pass item, its
-// interval table and layout.
+// The records of all queue positions, one thread each: the head (work item, transform,
+// the counter it waits for and the counters it releases) and, for a top-pass item, its
+// interval table and layout (top_record).
 constexpr int kPrepThreads = 64;  // small CTAs: the work is one latency-bound chain per item
-__global__ void __launch_bounds__(kPrepThreads) item_rec_kernel(TopParams P, const int* stage_count,
-                                                                int nitems, ItemRec* recs) {
+__global__ void __launch_bounds__(kPrepThreads) item_rec_kernel(RecParams R) {
     const int q = blockIdx.x * kPrepThreads + threadIdx.x;
-    if (q >= nitems) return;
-    const WorkItem item = P.items[q];
-    const TransformDesc tr = P.trs[item.tr];
-    ItemRec* r = recs + q;
-    r->item = item;
-    r->tr = tr;
+    if (q >= R.nitems) return;
+    const WorkItem item = R.top.items[q];
+    const TransformDesc tr = R.top.trs[item.tr];
+    ItemHead h;
+    h.item = item;
+    h.tr = tr;
+    h.wait = -1;
+    h.need = 0;
+    h.rel[0] = -1;
+    h.rel[1] = -1;
     const int stage = item.pass < 0 ? 0 : item.pass + 1;
-    r->need = stage > 0 ? stage_count[item.tr * kMaxStages + stage - 1] : 0;
-    if (item.pass >= 0) top_record(P, tr, item, r->top);
+    if (stage > 0) {  // every item of the stage before, in this transform
+        h.wait = item.tr * kMaxStages + stage - 1;
+        h.need = R.stage_count[h.wait];
+    } else if (item.pass == -1 && tr.batch >= R.ring) {
+        // a sub-tree writes its batch's ring slot once the batch that used it before has
+        // finished reading it: all of that batch's last-pass items
+        h.wait = R.batch_base + tr.batch - R.ring;
+        h.need = R.batch_top[tr.batch - R.ring];
+    }
+    if (item.pass != -2) {
+        const int npass = top_passes(tr.depth, tr.chunk);
+        if (item.pass < npass - 1) {
+            h.rel[0] = item.tr * kMaxStages + stage;  // a later stage of the transform waits
+        } else if (tr.batch + R.ring < R.nbatches) {
+            // the last pass: the batch's slot is free once all of these are done (the earlier
+            // passes of a transform end before its last one starts)
+            h.rel[0] = R.batch_base + tr.batch;
+        }
+    }
+    R.heads[q] = h;
+    if (item.pass >= 0) top_record(R.top, tr, item, R.tables + (int64_t)item.pad * kTopRecInts);
 }
 
 // Returns whether a later stage of the transform waits for this item (not the last pass).
@@ -981,52 +1055,58 @@ __device__ __forceinline__ bool top_item(const TopParams& P, const WorkItem item
 
     // ---- gather the needed rows of the depth-d_in transforms: one bulk copy per interval,
     //      all counted by a single arrival on the barrier; the unaligned ends of all
-    //      intervals by plain loads, one element per thread
+    //      intervals by plain loads, one element per thread.  Warp 0 runs the hook
+    //      (thread 0: release the item before, fetch the next records) meanwhile.
     const unsigned bytes = (unsigned)tab[kRecBytes];
-    if (tid == 0 && bytes) {
-        mbar_expect_tx(bar, bytes);
-        for (int j = 0; j < (1 << L); ++j) {
-            const int e = (1 << L) - 1 + j;
-            const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
-            issue_rows_copy(smem, tab[8 * e + 4], g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p, bar);
-        }
-    }
-    for (int u = tid; u < (8 << L); u += kTopThreads) {
-        const int e = (1 << L) - 1 + (u >> 3), c = u & 7;
-        const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
-        const int total = (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p;
-        const int lead = bulk_lead(g);
-        const int tail0 = lead + (int)(bulk_bytes(g, total) / 4);
-        if (c < lead + (total - tail0)) {  // at most 3 + 3 ends per interval
-            const int q = c < lead ? c : tail0 + (c - lead);
-            smem[tab[8 * e + 4] + q] = g[q];
-        }
-    }
-    // ---- row descriptors {out, head row, tail row, shift} for levels L-1 .. 0, made
-    //      while the bulk copies are in flight
     int4* desc = reinterpret_cast<int4*>(smem + lay.desc);
-    const int ndesc = lvl_desc[L];
-    for (int q = tid; q < ndesc; q += kTopThreads) {
-        int l = L - 1;
-        while (q >= lvl_desc[L - l]) --l;  // level of descriptor q
-        int r = q - lvl_desc[L - 1 - l];
-        int e = (1 << l) - 1;
-        while (r > tab[8 * e + 3] - tab[8 * e + 2]) {
-            r -= tab[8 * e + 3] - tab[8 * e + 2] + 1;
-            ++e;
+    if (warp == 0) {
+        hook.run();
+    } else {
+        const int t = tid - 32, nt = kTopThreads - 32;
+        if (t == 0 && bytes) {
+            mbar_expect_tx(bar, bytes);
+            for (int j = 0; j < (1 << L); ++j) {
+                const int e = (1 << L) - 1 + j;
+                const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
+                issue_rows_copy(smem, tab[8 * e + 4], g, (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p,
+                                bar, true);
+            }
         }
-        const int s = tab[8 * e + 2] + r;
-        const Split sp = merge_split(tab[8 * e + 1], s);
-        const int eh = 2 * e + 1, et = 2 * e + 2;
-        int4 d;
-        d.x = tab[8 * e + 4] + r * p;
-        d.y = tab[8 * eh + 4] + (sp.i - tab[8 * eh + 2]) * p;
-        d.z = tab[8 * et + 4] + (sp.j - tab[8 * et + 2]) * p;
-        d.w = sp.shift % p;
-        desc[q] = d;
+        for (int u = t; u < (8 << L); u += nt) {
+            const int e = (1 << L) - 1 + (u >> 3), c = u & 7;
+            const float* g = in + (int64_t)(tab[8 * e] + tab[8 * e + 2]) * p;
+            const int total = (tab[8 * e + 3] - tab[8 * e + 2] + 1) * p;
+            const int lead = bulk_lead(g);
+            const int tail0 = lead + (int)(bulk_bytes(g, total) / 4);
+            if (c < lead + (total - tail0)) {  // at most 3 + 3 ends per interval
+                const int q = c < lead ? c : tail0 + (c - lead);
+                smem[tab[8 * e + 4] + q] = g[q];
+            }
+        }
+        // ---- row descriptors {out, head row, tail row, shift} for levels L-1 .. 0, made
+        //      while the bulk copies are in flight
+        const int ndesc = lvl_desc[L];
+        for (int q = t; q < ndesc; q += nt) {
+            int l = L - 1;
+            while (q >= lvl_desc[L - l]) --l;  // level of descriptor q
+            int r = q - lvl_desc[L - 1 - l];
+            int e = (1 << l) - 1;
+            while (r > tab[8 * e + 3] - tab[8 * e + 2]) {
+                r -= tab[8 * e + 3] - tab[8 * e + 2] + 1;
+                ++e;
+            }
+            const int s = tab[8 * e + 2] + r;
+            const Split sp = merge_split(tab[8 * e + 1], s);
+            const int eh = 2 * e + 1, et = 2 * e + 2;
+            int4 d;
+            d.x = tab[8 * e + 4] + r * p;
+            d.y = tab[8 * eh + 4] + (sp.i - tab[8 * eh + 2]) * p;
+            d.z = tab[8 * et + 4] + (sp.j - tab[8 * et + 2]) * p;
+            d.w = sp.shift % p;
+            desc[q] = d;
+        }
     }
 
-    hook.run();
     const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity());
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
@@ -1074,7 +1154,8 @@ __device__ __forceinline__ bool top_item(const TopParams& P, const WorkItem item
         }
     } else {
         float* dst = out + (int64_t)(st0 + lo0) * p;
-        for (int e = tid; e < rows0 * p; e += kTopThreads) dst[e] = smem[o0 + e];
+        const uint64_t pol = policy_keep();
+        for (int e = tid; e < rows0 * p; e += kTopThreads) st_keep(dst + e, smem[o0 + e], pol);
     }
     __syncthreads();
     if (Hook::kInitEachItem && tid == 0) mbar_inval(bar);
@@ -1104,8 +1185,8 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_top_kernel(Top
 // late, at the next item's copy wait or before any wait of the CTA, so a held
 // completion never blocks anyone.  Waits are bounded (about 1 s); on expiry the
 // status word gets kDevTimeout and all CTAs stop at their next claim.
-// Each item starts from its record (ItemRec), fetched by one bulk copy while the item
-// before it runs.  Completion: the CTA synchronises, then one thread waits for its bulk
+// Each item starts from its head (ItemHead), fetched by one bulk copy two items ahead,
+// and, for a top pass, its interval table, fetched one item ahead.  Completion: the CTA synchronises, then one thread waits for its bulk
 // stores, fences at device scope and adds to the stage counter.  The waiting thread
 // acquires the counter, then orders the async (bulk-copy) proxy after it before the
 // item's rows are copied in.
@@ -1114,107 +1195,149 @@ static_assert(kBottomThreads == kTopThreads, "persistent CTAs run both item kind
 __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_kernel(PersistentParams P) {
     extern __shared__ __align__(16) float smem[];
     int* slot = reinterpret_cast<int*>(smem + P.smem_floats);    // [0]: the item to run
-    uint64_t* rbar = reinterpret_cast<uint64_t*>(slot + 4);      // barriers of the two records
-    ItemRec* rbuf = reinterpret_cast<ItemRec*>(slot + 8);        // the two record buffers
+    uint64_t* hbar = reinterpret_cast<uint64_t*>(slot + 4);      // barriers of the three heads
+    uint64_t* tbar = hbar + 3;                                   // ... and of the two tables
+    ItemHead* hbuf = reinterpret_cast<ItemHead*>(slot + 16);     // three head buffers
+    int* tbuf = reinterpret_cast<int*>(hbuf + 3);                // two table buffers
     const int tid = threadIdx.x;
-    // thread 0: queue positions claimed (a runs next, then b, then c); the status word is
-    // read one item ahead too (a relaxed load whose latency the item's work hides)
-    int a = P.nitems, b = P.nitems, c = P.nitems;
-    unsigned stat = 0, rpar = 0;  // rpar: parity of each record barrier's next phase
-    int rb = 0;                   // record buffer of the running item (all threads)
+    const int N = P.nitems;
+    // thread 0: queue positions claimed in order (a runs now, then b, then c; d is being
+    // claimed), the barrier parities (bits 0-2 heads, 3-4 tables) and the copies in flight;
+    // the status word is read one item ahead (a relaxed load whose latency the item's work
+    // hides).  All threads: head buffer `ha` and table buffer `ta` of the running item.
+    int a = N, b = N, c = N, d = N;
+    unsigned stat = 0, par = 0, inflight = 0;
+    int ha = 0, ta = 0;
     QueueHook hook;
     if (tid == 0) {
-        mbar_init(&rbar[0], 1);
-        mbar_init(&rbar[1], 1);
+        hook.done = P.done;
+        for (int j = 0; j < 5; ++j) mbar_init(&hbar[j], 1);
         mbar_init(reinterpret_cast<uint64_t*>(smem), 1);  // the items' copy barrier
         a = atomicAdd(P.queue, 1);
         b = atomicAdd(P.queue, 1);
-        if (a < P.nitems) {
-            mbar_expect_tx(&rbar[0], (unsigned)sizeof(ItemRec));
-            bulk_g2s(&rbuf[0], P.recs + a, (unsigned)sizeof(ItemRec), &rbar[0]);
-            hook.inflight = 1u;
+        c = atomicAdd(P.queue, 1);
+        for (int j = 0; j < 2; ++j) {
+            const int q = j == 0 ? a : b;
+            if (q < N) {
+                mbar_expect_tx(&hbar[j], (unsigned)sizeof(ItemHead));
+                bulk_g2s(&hbuf[j], P.heads + q, (unsigned)sizeof(ItemHead), &hbar[j]);
+                inflight |= 1u << j;
+            }
+        }
+        // the first item's table, once its head has landed
+        if (a < N && mbar_wait_bounded(&hbar[0], 0)) {
+            par ^= 1u;
+            inflight &= ~1u;
+            if (hbuf[0].item.pass >= 0) {
+                mbar_expect_tx(&tbar[0], (unsigned)kTopRecBytes);
+                bulk_g2s(tbuf, P.tables + (int64_t)hbuf[0].item.pad * kTopRecInts,
+                         (unsigned)kTopRecBytes, &tbar[0]);
+                inflight |= 1u << 3;
+            }
+        } else if (a < N) {
+            atomicOr(P.bottom.status, kDevTimeout);
+            a = N;
         }
     }
     for (;;) {
-        // thread 0 alone waits for the item's record and, for a stage s > 0, for all items of
-        // stage s - 1 of its transform; the barrier then hands both to the CTA.  slot[0] is
-        // rewritten only after the barrier at the end of the item, when every thread has
-        // read it.
+        // thread 0 alone waits for the item's table (a top pass) and for the counter it
+        // depends on; the barrier then hands both to the CTA.  slot[0] is rewritten only
+        // after the barrier at the end of the item, when every thread has read it.
         if (tid == 0) {
-            int q = (stat & kDevTimeout) ? P.nitems : a;
-            if (q < P.nitems) {
-                if (!mbar_wait_bounded(&rbar[rb], (rpar >> rb) & 1u)) {
-                    atomicOr(P.bottom.status, kDevTimeout);
-                    q = P.nitems;
-                } else {
-                    rpar ^= 1u << rb;
-                    hook.inflight &= ~(1u << rb);
-                    const ItemRec& R = rbuf[rb];
-                    const int stage = R.item.pass < 0 ? 0 : R.item.pass + 1;
-                    if (stage > 0) {
-                        if (hook.pend) {  // release before waiting on anyone
-                            release_count(hook.pend);
-                            hook.pend = nullptr;
-                        }
-                        const int* cnt = P.done + R.item.tr * kMaxStages + stage - 1;
+            int q = (stat & kDevTimeout) ? N : a;
+            if (q < N) {
+                const ItemHead& H = hbuf[ha];
+                bool ok = true;
+                if (H.item.pass >= 0) {
+                    ok = mbar_wait_bounded(&tbar[ta], (par >> (3 + ta)) & 1u);
+                    par ^= 1u << (3 + ta);
+                    inflight &= ~(1u << (3 + ta));
+                }
+                if (ok && H.wait >= 0) {
+                    const int* cnt = P.done + H.wait;
+                    int seen;
+                    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(seen) : "l"(cnt) : "memory");
+                    if (seen < H.need) {
+                        hook.release();  // before waiting on anyone
                         const long long t0 = clock64();
                         for (;;) {
-                            int seen;
+                            __nanosleep(256);
                             asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(seen) : "l"(cnt) : "memory");
-                            if (seen >= R.need) break;
+                            if (seen >= H.need) break;
                             if (clock64() - t0 > (1LL << 31)) {
-                                atomicOr(P.bottom.status, kDevTimeout);
-                                q = P.nitems;
+                                ok = false;
                                 break;
                             }
-                            __nanosleep(256);
                         }
-                        asm volatile("fence.proxy.async.global;" ::: "memory");
                     }
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
+                if (!ok) {
+                    atomicOr(P.bottom.status, kDevTimeout);
+                    q = N;
                 }
             }
             slot[0] = q;
+            reinterpret_cast<int*>(smem)[2] = 0;  // a sub-tree's register-stage node count
+            reinterpret_cast<int*>(smem)[3] = 1;  // and largest node
         }
         __syncthreads();
         const int q = slot[0];
-        if (q >= P.nitems) break;
-        const ItemRec& R = rbuf[rb];
-        const WorkItem item = R.item;
-        const TransformDesc tr = R.tr;
-        const int stage = item.pass < 0 ? 0 : item.pass + 1;
+        if (q >= N) break;
+        const ItemHead& H = hbuf[ha];
+        const WorkItem item = H.item;
+        const TransformDesc tr = H.tr;
         if (tid == 0) {
-            c = atomicAdd(P.queue, 1);
+            d = atomicAdd(P.queue, 1);
             asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(stat) : "l"(P.bottom.status) : "memory");
-            // the next item's record goes to the other buffer
+            // during the item: release the item before, fetch the next item's table and
+            // the head of the one after it
+            const int hb = ha == 2 ? 0 : ha + 1, hc = hb == 2 ? 0 : hb + 1;
             hook.armed = true;
-            hook.src = b < P.nitems ? P.recs + b : nullptr;
-            hook.dst = &rbuf[rb ^ 1];
-            hook.bar = &rbar[rb ^ 1];
-            hook.bit = 1u << (rb ^ 1);
+            hook.issued = 0;
+            hook.timed_out = false;
+            hook.next = b < N ? &hbuf[hb] : nullptr;
+            hook.next_bar = &hbar[hb];
+            hook.next_par = (par >> hb) & 1u;
+            hook.table_src = P.tables;
+            hook.table_dst = tbuf + (ta ^ 1) * kTopRecInts;
+            hook.table_bar = &tbar[ta ^ 1];
+            hook.head_src = c < N ? P.heads + c : nullptr;
+            hook.head_dst = &hbuf[hc];
+            hook.head_bar = &hbar[hc];
         }
-        bool signal = false;
         if (item.pass == -2) bottom_item<true>(P.bottom_snr, item, tr, smem, hook);
-        else if (item.pass == -1) {
-            bottom_item<false>(P.bottom, item, tr, smem, hook);
-            signal = true;
-        } else {
-            signal = top_item(P.top, item, tr, R.top, smem, hook);
-        }
+        else if (item.pass == -1) bottom_item<false>(P.bottom, item, tr, smem, hook);
+        else top_item(P.top, item, tr, tbuf + ta * kTopRecInts, smem, hook);
         __syncthreads();
         if (hook.failed) break;  // a copy wait ran out (uniform)
         if (tid == 0) {
             hook.run();  // an item that returned before its copy wait
-            if (signal) hook.pend = P.done + item.tr * kMaxStages + stage;
+            const int hb = ha == 2 ? 0 : ha + 1, hc = hb == 2 ? 0 : hb + 1;
+            if (hook.next && !hook.timed_out) {  // the next item's head was consumed by the hook
+                par ^= 1u << hb;
+                inflight &= ~(1u << hb);
+            }
+            if (hook.issued & 1u) inflight |= 1u << (3 + (ta ^ 1));
+            if (hook.issued & 2u) inflight |= 1u << hc;
+            if (hook.timed_out) {
+                atomicOr(P.bottom.status, kDevTimeout);
+                stat |= kDevTimeout;
+            }
+            hook.pend[0] = H.rel[0];
+            hook.pend[1] = H.rel[1];
         }
-        rb ^= 1;
+        ha = ha == 2 ? 0 : ha + 1;
+        ta ^= 1;
         a = b;
         b = c;
+        c = d;
     }
     if (tid == 0) {
-        if (hook.pend) release_count(hook.pend);
-        // a record fetch still in flight lands before the CTA exits
-        for (int j = 0; j < 2; ++j)
-            if ((hook.inflight >> j) & 1u) mbar_wait_bounded(&rbar[j], (rpar >> j) & 1u);
+        hook.release();
+        // copies still in flight land before the CTA exits
+        for (int j = 0; j < 5; ++j)
+            if ((inflight >> j) & 1u) mbar_wait_bounded(&hbar[j], (par >> j) & 1u);
     }
 }
 
@@ -1406,12 +1529,10 @@ cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_item_recs(const TopParams& P, const int* stage_count, int nitems, ItemRec* recs,
-                             cudaStream_t s) {
-    if (nitems <= 0) return cudaSuccess;
-    LaunchScope ls(kItemRecs, (16.0 + sizeof(TransformDesc) + sizeof(ItemRec)) * nitems, s);
-    item_rec_kernel<<<(unsigned)((nitems + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(
-        P, stage_count, nitems, recs);
+cudaError_t launch_item_recs(const RecParams& R, cudaStream_t s) {
+    if (R.nitems <= 0) return cudaSuccess;
+    LaunchScope ls(kItemRecs, (16.0 + sizeof(TransformDesc) + sizeof(ItemHead)) * R.nitems, s);
+    item_rec_kernel<<<(unsigned)((R.nitems + kPrepThreads - 1) / kPrepThreads), kPrepThreads, 0, s>>>(R);
     return cudaGetLastError();
 }
 
