@@ -103,18 +103,24 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu record, or
-    None if there is none or the kernel source changed since it was taken."""
+def recorded_profile(kernel, workload):
+    """The committed ncu record of `kernel` on `workload` (DRAM bytes per launch, shared-
+    memory and issue utilisation), or None if there is none or the kernel source changed
+    since it was taken."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
         if kernel_source_sha() != rec["kernel_source_sha256_prefix"]:
             return None
         if rec["kernel"] != kernel or rec.get("workload", workload) != workload:
             return None
-        return rec["dram_bytes_per_launch"]
+        return rec
     except Exception:
         return None
+
+
+def recorded_traffic(kernel, workload):
+    rec = recorded_profile(kernel, workload)
+    return rec["dram_bytes_per_launch"] if rec else None
 
 
 def measured_peaks():
@@ -264,7 +270,7 @@ def oracle_rate(job, stride, offset=0, full_ds=True):
     checks = [(series index or None, sampled trial rows, oracle periodogram of them)]."""
     if job.batch is None:
         w = job.single
-        if job.store != "f32":
+        if job.prepared:
             w = synth.Workload(w.name, job.dequantised(0), w.tsamp, w.pmin, w.pmax, w.bmin,
                                w.bmax, w.widths)
         est, desc, chk = oracle_sample_time(w, stride, offset, full_ds)
@@ -275,7 +281,7 @@ def oracle_rate(job, stride, offset=0, full_ds=True):
     for i in pick:
         s = b.series[i]
         x = b.series_x(i)
-        if job.store != "f32":
+        if job.prepared:
             x = job.dequantised(i)
         w = synth.Workload("s%d" % i, x, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax, b.widths)
         est, desc, chk = oracle_sample_time(w, stride, offset, full_ds)
@@ -415,6 +421,12 @@ class Job:
     def dequantised(self, i):
         return self._deq[i]
 
+    @property
+    def prepared(self):
+        """Whether the searched values differ from the generated ones (stored at reduced
+        precision, or de-reddened and normalised): the oracle then searches them."""
+        return bool(self._deq)
+
     # ------------------------------------------------------------------ device side
     def to_device(self, ffa, torch, dev, ws_budget):
         self.ffa, self.torch, self.dev = ffa, torch, dev
@@ -455,18 +467,20 @@ class Job:
 
     def _store(self, x32):
         """Normalised storage of the input (Sec. 3.1): FP16 or int8 (q/16) by the
-        library's own normalise call, whole series (each series of a batch alone)."""
-        if self.store == "f32":
+        library's own normalise call, whole series (each series of a batch alone).  Red
+        noise series (the int8 stress batch) are first de-reddened by the library's
+        running median of about 1 s (Sec. 5.2).  Input preparation: not timed."""
+        red = self.batch is not None and any(s.red for s in self.batch.series)
+        if self.store == "f32" and not red:
             return x32
         ffa, torch = self.ffa, self.torch
-        out = torch.empty(x32.numel(), dtype=torch.float16 if self.store == "f16" else torch.int8,
-                          device=x32.device)
+        dt = {"f32": torch.float32, "f16": torch.float16, "i8": torch.int8}[self.store]
         segs = [(0, x32.numel())] if self.batch is None else \
             [(s.offset, s.n) for s in self.batch.series]
-        for i, (o, n) in enumerate(segs):
-            out[o:o + n] = ffa.normalise(x32[o:o + n], dtype=out.dtype)[0]
+        width = ffa.median_width(synth.DEREDDEN_SECONDS, self.batch.series[0].tsamp) if red else None
+        out = ffa.prepare_batch(x32, segs, width, dt)
         torch.cuda.synchronize()
-        host = out.cpu().numpy()  # host copies of the dequantised series the oracle checks
+        host = out.cpu().numpy()  # host copies of the searched (dequantised) series the oracle checks
         for i in sorted({0, len(segs) // 2, len(segs) - 1}):
             o, n = segs[i]
             v = host[o:o + n].astype(np.float32)
@@ -499,6 +513,28 @@ class Job:
     @property
     def ntrials(self):
         return self.searcher.info.ntrials
+
+    def method_counts(self):
+        """(FP32 operations of the method, whole-step B_ref bytes) of one step: per series
+        the plan's merge adds and S/N operations, and per octave the raw series read plus
+        the octave written, plus the FFA + S/N term (4 m p + 4 n_w kept per transform)."""
+        ffa = self.ffa
+        es = self.x.element_size()
+        series = [self.single] if self.batch is None else self.batch.series
+        memo = {}
+        ops = b_ref = 0.0
+        for s in series:
+            key = (s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax)
+            if key not in memo:
+                i = ffa.periodogram_plan(s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax,
+                                         self.widths, zero_mean=ZERO_MEAN)
+                ffa_term = 4.0 * i.folded_samples + 4.0 * len(self.widths) * i.ntrials
+                memo[key] = (i.ffa_adds + i.snr_ops,
+                             i.noctaves * es * s.n + 4.0 * i.downsampled_samples + ffa_term)
+            o, b = memo[key]
+            ops += o
+            b_ref += b
+        return ops, b_ref
 
     def config(self):
         c = self._config()
@@ -983,34 +1019,44 @@ def run_ffa(a):
     bytes_per_launch = kq["alg_bytes"] / kq["launches"]
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / avg_s / 1e9
-    traffic = recorded_traffic(top, job.config()["workload"])
-    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+    wl = job.config()["workload"]
+    traffic = recorded_traffic(top, wl)
+    prof = recorded_profile(top, wl)
+    roofline = {"bound": "smem" if top == "ffa_persistent" else "hbm", "kernel": top,
+                "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "frac_of": "the measured HBM copy bandwidth (the metric's % of HBM peak)",
+                "hbm_frac": achieved / peak,
                 "alg_bytes_per_launch": bytes_per_launch,
                 "alg_bytes_def": "B_ref FFA+S/N term: sum over transforms of 4 m p + 4 n_w kept",
                 "peak_source": peak_kind,
                 "dram_frac": (traffic / avg_s / 1e9 / peak) if traffic else None,
                 "share_of_step": kq["ms"] / tot_ms if tot_ms else None,
                 "launches_per_step": kq["launches"] / a.steps}
-    if job.batch is None and top == "ffa_persistent":
+    if top == "ffa_persistent":
+        roofline["bound_note"] = ("shared-memory pipe and instruction issue (merge levels, "
+                                  "boxcar S/N); neither HBM nor the FP32 ALU is near its roof")
+        # shared-memory and issue utilisation from the recorded ncu capture of this kernel
+        # source (null once the kernel has changed since the capture)
+        roofline["smem_frac"] = prof["l1tex_throughput_pct"] / 100.0 if prof and "l1tex_throughput_pct" in prof else None
+        roofline["issue_frac"] = prof["issue_active_pct"] / 100.0 if prof and "issue_active_pct" in prof else None
         # the same kernel against the FP32 ALU: the method's adds, subtracts and maxima
         # over 128 FP32 lanes per SM at the maximum SM clock
-        i = s.info
-        ops = i.ffa_adds + i.snr_ops
+        ops, b_ref = job.method_counts()
+        launches = kq["launches"] / a.steps
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = (clk or {}).get("sm_max_mhz") or 2070.0
         alu_peak = sms * 128 * mhz * 1e6 / 1e12
-        alu = ops / avg_s / 1e12
-        roofline["alu"] = {"ops_per_launch": ops, "achieved": alu, "peak": alu_peak,
+        alu = ops / launches / avg_s / 1e12
+        roofline["alu_frac"] = alu / alu_peak
+        roofline["alu"] = {"ops_per_launch": ops / launches, "achieved": alu, "peak": alu_peak,
                            "unit": "TFLOP/s", "frac": alu / alu_peak,
                            "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz" % (sms, mhz)}
-        # whole-step effective fraction: B_ref = sum_k (read the raw series + write
-        # octave k) + the FFA + S/N term, over the device time of one step
-        i = s.info
-        es = job.x.element_size()
-        b_ref = i.noctaves * es * job.n + 4.0 * i.downsampled_samples + bytes_per_launch
+        # whole-step effective fraction: B_ref = per octave the raw series read and the
+        # octave written, plus the FFA + S/N term, over the device time of one step (an
+        # effective figure: the prefix-sum downsampler does not re-read the raw series)
         roofline["step_b_ref_bytes"] = b_ref
-        roofline["step_b_ref_frac"] = b_ref / (t_step * 1e-3) / 1e9 / peak
+        roofline["step_b_ref_effective_frac"] = b_ref / (t_step * 1e-3) / 1e9 / peak
 
     # ---- end to end from pinned host buffers (copies inside the timed region)
     e2e = None
@@ -1027,7 +1073,7 @@ def run_ffa(a):
         if job.batch is None:
             _log("CPU oracle on all host cores")
             w = job.single
-            if job.store != "f32":
+            if job.prepared:
                 w = synth.Workload(w.name, job.dequantised(0), w.tsamp, w.pmin, w.pmax, w.bmin,
                                    w.bmax, w.widths)
             prate, pdesc, pthreads = oracle_parallel_rate(w, 4, os.cpu_count() or 1)

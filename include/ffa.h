@@ -61,6 +61,9 @@ const char* ffa_version(void);
  *         FFA_ERR_CAPACITY (out_cap < n_out or workspace too small).
  * ---------------------------------------------------------------------------- */
 ffa_status ffa_downsample_workspace(int64_t n, size_t* bytes);
+/* n_out = floor(n / factor) of a downsampling (host only), to size d_out before the
+ * call.  Errors: FFA_ERR_ARG (null n_out, n <= 0, factor < 1 or not finite). */
+ffa_status ffa_downsample_length(int64_t n, double factor, int64_t* n_out);
 ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_out,
                           int64_t out_cap, int64_t* n_out, void* d_ws, size_t ws_bytes,
                           void* stream);
@@ -91,9 +94,12 @@ ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d
  * Scratch: a fixed 4 MiB array inside the library (per device, held by every GPU that
  * loads the library until the process exits).  Blocks that need sub-trees may have
  * rows * cols <= 1048512 floats; larger ones return FFA_ERR_CAPACITY before anything is
- * launched.  Allocates nothing (no cudaMalloc, cudaFree, events or library allocator).
+ * launched.  Calls no cudaMalloc, cudaFree, event creation or library allocator.
  * The first call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.
+ * with that device current).  With CUDA's lazy module loading that first call also
+ * loads the library module holding the array, which is when the runtime allocates its
+ * 4 MiB on the device: make that first call before the caller's no-allocation phase
+ * (and before any stream capture).  Later calls allocate nothing.
  * All calls share the one array: calls that overlap on the GPU (other streams, other
  * threads) race and must be serialised by the caller.
  * ---------------------------------------------------------------------------- */
@@ -377,6 +383,20 @@ ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, doubl
  * device-side check failed, else FFA_ERR_TIMEOUT or FFA_ERR_DEVICE (the message names
  * the failed checks). */
 ffa_status ffa_check(void* d_ws, void* stream);
+
+/* Limit of every device-side wait of a periodogram launch (a CTA waiting for the items
+ * an item depends on, or for its own bulk copies), in milliseconds of SM clock at the
+ * maximum clock; default 1000.  A wait that runs out sets FFA_ERR_TIMEOUT in the status
+ * word and the launch ends early (its outputs are then incomplete).  Process-wide; takes
+ * effect from the next call.  Errors: FFA_ERR_ARG (ms <= 0 or ms > 60000).
+ *
+ * Fault injection for tests: the environment variable FFA_FAULT, read at every call,
+ * makes calls fail on purpose, always without a device fault: "plan" (plan building:
+ * FFA_ERR_UNSUPPORTED), "alloc" (the page-locked table allocation: FFA_ERR_CUDA),
+ * "launch" (the launch sequence, before any CUDA call: FFA_ERR_CUDA), "stage" (one
+ * transform's second stage waits for one item more than exist: the wait runs out after
+ * the wait limit and ffa_check reports FFA_ERR_TIMEOUT). */
+ffa_status ffa_set_wait_limit_ms(double ms);
 
 /* ------------------------------------------------------------------------------
  * Launch accounting and per-kernel timing (for benchmarks).  When enabled, every

@@ -33,7 +33,7 @@ __all__ = [
     "Tiles", "tile_candidates", "tune", "tune_periodogram", "SegmentSearcher",
     "check", "plan_cache_clear", "launch_count", "kernel_names", "profile_enable", "profile_reset",
     "profile_query", "RunningMedian", "running_median", "deredden", "median_width",
-    "PeakFinder", "find_peaks", "PEAK_DTYPE",
+    "PeakFinder", "find_peaks", "PEAK_DTYPE", "prepare_batch", "set_wait_limit_ms",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -109,6 +109,7 @@ def library() -> ctypes.CDLL:
     L.ffa_version.restype = ctypes.c_char_p
     L.ffa_downsample_workspace.argtypes = [i64, ctypes.POINTER(sz)]
     L.ffa_downsample.argtypes = [vp, i64, dbl, vp, i64, ctypes.POINTER(i64), vp, sz, vp]
+    L.ffa_downsample_length.argtypes = [i64, dbl, ctypes.POINTER(i64)]
     L.ffa_transform_workspace.argtypes = [i32, i32, ctypes.POINTER(sz)]
     L.ffa_transform.argtypes = [vp, i32, i32, vp, vp, sz, vp]
     L.ffa_boxcar_snr.argtypes = [vp, i32, i32, vp, i32, dbl, vp, vp]
@@ -127,6 +128,7 @@ def library() -> ctypes.CDLL:
     L.ffa_periodogram_host.argtypes = [vp, i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp,
                                        i64, vp, sz, vp]
     L.ffa_check.argtypes = [vp, vp]
+    L.ffa_set_wait_limit_ms.argtypes = [dbl]
     L.ffa_batch_plan.argtypes = [vp, i32, vp, i32, sz, vp, ctypes.POINTER(_BatchInfo)]
     L.ffa_periodogram_batch.argtypes = [vp, i32, vp, i32, vp, i32, sz, vp, vp, vp, i64, vp,
                                         sz, vp]
@@ -146,7 +148,8 @@ def library() -> ctypes.CDLL:
     L.ffa_profile_enable.argtypes = [i32]
     L.ffa_profile_query.argtypes = [i32, ctypes.POINTER(i64), ctypes.POINTER(dbl),
                                     ctypes.POINTER(dbl)]
-    for f in ("ffa_downsample_workspace", "ffa_downsample", "ffa_transform_workspace",
+    for f in ("ffa_downsample_workspace", "ffa_downsample", "ffa_downsample_length",
+              "ffa_transform_workspace",
               "ffa_transform", "ffa_boxcar_snr", "ffa_periodogram_plan", "ffa_periodogram",
               "ffa_periodogram_host", "ffa_check", "ffa_profile_enable", "ffa_profile_reset",
               "ffa_normalise_workspace", "ffa_normalise", "ffa_batch_plan",
@@ -154,7 +157,7 @@ def library() -> ctypes.CDLL:
               "ffa_periodogram_opts", "ffa_batch_plan_opts", "ffa_periodogram_batch_opts",
               "ffa_boxcar_snr_template", "ffa_running_median_workspace",
               "ffa_running_median", "ffa_find_peaks_workspace", "ffa_find_peaks",
-              "ffa_profile_query"):
+              "ffa_profile_query", "ffa_set_wait_limit_ms"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -174,6 +177,25 @@ def _stream_handle(stream=None) -> ctypes.c_void_p:
     torch = _torch()
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def _on(stream):
+    """Context of a one-shot call on `stream`: its workspace and outputs are allocated on
+    the stream its kernels run on, so that torch's caching allocator never hands that
+    memory to work on another stream while the kernels may still use it (and reads such
+    as tolist() are ordered after them)."""
+    import contextlib
+    return _torch().cuda.stream(stream) if stream is not None else contextlib.nullcontext()
+
+
+def _keep(stream, *tensors):
+    """A long-lived object's buffers used on `stream`: the allocator waits for that
+    stream's work before it reuses them once they are freed."""
+    if stream is None:
+        return
+    for t in tensors:
+        if t is not None:
+            t.record_stream(stream)
 
 
 def _dev_tensor(t, name: str):
@@ -215,12 +237,13 @@ def normalise(x, dtype=None, stream=None):
     L = library()
     need = ctypes.c_size_t()
     _check(L.ffa_normalise_workspace(x.numel(), ctypes.byref(need)))
-    ws = _workspace(need.value, x.device)
-    out = torch.empty(x.numel(), dtype=dtype, device=x.device)
-    stats = torch.empty(2, dtype=torch.float64, device=x.device)
-    _check(L.ffa_normalise(_vp(x), x.numel(), _vp(out), code, _vp(stats), _vp(ws), ws.numel(),
-                           _stream_handle(stream)))
-    m, s = stats.tolist()
+    with _on(stream):
+        ws = _workspace(need.value, x.device)
+        out = torch.empty(x.numel(), dtype=dtype, device=x.device)
+        stats = torch.empty(2, dtype=torch.float64, device=x.device)
+        _check(L.ffa_normalise(_vp(x), x.numel(), _vp(out), code, _vp(stats), _vp(ws),
+                               ws.numel(), _stream_handle(stream)))
+        m, s = stats.tolist()
     return out, m, s
 
 
@@ -261,21 +284,45 @@ class RunningMedian:
             _vp(x), self.n, self.width, _vp(med) if med is not None else None,
             _vp(y) if y is not None else None, _vp(self.ws), self.ws.numel(),
             _stream_handle(stream)))
+        _keep(stream, self.ws)
         return med, y
+
+
+def prepare_batch(x, spans, width: Optional[int], dtype=None, stream=None):
+    """The steps before the search of a batch of series (Sec. 5.2), each series on its
+    own: de-redden x in place by a running median of `width` samples (None: skip), then
+    normalise into a new buffer of `dtype` (float32, float16 or int8 holding q with value
+    q/16).  `spans`: (offset, n) of every series in the float32 CUDA buffer x."""
+    torch = _torch()
+    _dev_tensor(x, "x")
+    with _on(stream):
+        out = torch.empty(x.numel(), dtype=torch.float32 if dtype is None else dtype,
+                          device=x.device)
+        med = {}
+        for o, n in spans:
+            v = x[o:o + n]
+            if width is not None:
+                if n not in med:
+                    med[n] = RunningMedian(n, width, x.device)
+                med[n](v, y=v)
+            out[o:o + n] = normalise(v, dtype=out.dtype)[0]
+    return out
 
 
 def running_median(x, width: int, stream=None):
     """The running median of a float32 CUDA series (Sec. 5.2), a new tensor."""
-    med = _torch().empty_like(x)
-    RunningMedian(x.numel(), width, x.device)(x, med=med, stream=stream)
+    with _on(stream):
+        med = _torch().empty_like(x)
+        RunningMedian(x.numel(), width, x.device)(x, med=med)
     return med
 
 
 def deredden(x, width: int, inplace: bool = False, stream=None):
     """x minus its running median over `width` samples (Sec. 5.2): the red-noise removal
     that precedes `normalise`.  In place if `inplace`."""
-    y = x if inplace else _torch().empty_like(x)
-    RunningMedian(x.numel(), width, x.device)(x, y=y, stream=stream)
+    with _on(stream):
+        y = x if inplace else _torch().empty_like(x)
+        RunningMedian(x.numel(), width, x.device)(x, y=y)
     return y
 
 
@@ -319,6 +366,7 @@ class PeakFinder:
             _vp(periods), _vp(snr), self.ntrials, self.nw, self.tobs, ctypes.byref(self.opts),
             _vp(self.peaks), self.cap, _vp(self.npeaks), _vp(self.ws), self.ws.numel(),
             _stream_handle(stream)))
+        _keep(stream, self.ws, self.peaks, self.npeaks)
 
     def check(self, stream=None) -> None:
         _check(library().ffa_check(_vp(self.ws), _stream_handle(stream)))
@@ -349,12 +397,14 @@ def downsample(x, factor: float, stream=None):
     n = x.numel()
     need = ctypes.c_size_t()
     _check(L.ffa_downsample_workspace(n, ctypes.byref(need)))
-    ws = _workspace(need.value, x.device)
-    nout = int(np.floor(n / factor)) if factor >= 1 else 0
-    out = torch.empty(max(nout, 1), dtype=torch.float32, device=x.device)
-    got = ctypes.c_int64()
-    _check(L.ffa_downsample(_vp(x), n, float(factor), _vp(out), out.numel(), ctypes.byref(got),
-                            _vp(ws), ws.numel(), _stream_handle(stream)))
+    nout = ctypes.c_int64()
+    _check(L.ffa_downsample_length(n, float(factor), ctypes.byref(nout)))
+    with _on(stream):
+        ws = _workspace(need.value, x.device)
+        out = torch.empty(max(nout.value, 1), dtype=torch.float32, device=x.device)
+        got = ctypes.c_int64()
+        _check(L.ffa_downsample(_vp(x), n, float(factor), _vp(out), out.numel(),
+                                ctypes.byref(got), _vp(ws), ws.numel(), _stream_handle(stream)))
     return out[: got.value]
 
 
@@ -368,10 +418,11 @@ def ffa_transform(block, stream=None):
     m, p = block.shape
     need = ctypes.c_size_t()
     _check(L.ffa_transform_workspace(m, p, ctypes.byref(need)))
-    ws = _workspace(need.value, block.device)
-    out = torch.empty_like(block)
-    _check(L.ffa_transform(_vp(block), m, p, _vp(out), _vp(ws), ws.numel(),
-                           _stream_handle(stream)))
+    with _on(stream):
+        ws = _workspace(need.value, block.device)
+        out = torch.empty_like(block)
+        _check(L.ffa_transform(_vp(block), m, p, _vp(out), _vp(ws), ws.numel(),
+                               _stream_handle(stream)))
     return out
 
 
@@ -385,11 +436,12 @@ def boxcar_snr(prof, widths: Sequence[int], stdnoise: float, stream=None,
         raise TypeError("prof must be a 2-D float32 tensor")
     w = _widths_array(widths)
     rows, cols = prof.shape
-    out = torch.empty((rows, len(w)), dtype=torch.float32, device=prof.device)
-    _check(library().ffa_boxcar_snr_template(_vp(prof), rows, cols, _vp(w), len(w),
-                                             float(stdnoise),
-                                             BOXCAR_ZERO_MEAN if zero_mean else BOXCAR_PLAIN,
-                                             _vp(out), _stream_handle(stream)))
+    with _on(stream):
+        out = torch.empty((rows, len(w)), dtype=torch.float32, device=prof.device)
+        _check(library().ffa_boxcar_snr_template(_vp(prof), rows, cols, _vp(w), len(w),
+                                                 float(stdnoise),
+                                                 BOXCAR_ZERO_MEAN if zero_mean else BOXCAR_PLAIN,
+                                                 _vp(out), _stream_handle(stream)))
     return out
 
 
@@ -486,6 +538,7 @@ class Searcher:
             _vp(x), _dtype_code(x), n, tsamp, pmin, pmax, bmin, bmax, _vp(self.widths),
             len(self.widths), self._tiles_ptr, _vp(self._per), _vp(self._fb), _vp(self._snr),
             self.periods.numel(), _vp(self.ws), self.ws.numel(), _stream_handle(stream)))
+        _keep(stream, self.ws, self._per, self._fb, self._snr)
         return self.periods, self.foldbins, self.snr
 
     def run_host(self, x_host, periods_h, foldbins_h, snr_h, stream=None):
@@ -513,9 +566,10 @@ def periodogram(x, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,
 
     Returns (periods float64 [T], foldbins int32 [T], snr float32 [T, nw]) on the device.
     """
-    s = Searcher(x.numel(), tsamp, pmin, pmax, bmin, bmax, widths, device=x.device,
-                 zero_mean=zero_mean)
-    return s(x, stream)
+    with _on(stream):
+        s = Searcher(x.numel(), tsamp, pmin, pmax, bmin, bmax, widths, device=x.device,
+                     zero_mean=zero_mean)
+        return s(x)
 
 
 def periodogram_host(x: np.ndarray, tsamp, pmin, pmax, bmin, bmax, widths, device="cuda"):
@@ -617,6 +671,7 @@ class BatchSearcher:
             _vp(self.widths), len(self.widths), self.ws_budget, self._tiles_ptr, _vp(self._per),
             _vp(self._fb), _vp(self._snr), self.periods.numel(), _vp(self.ws), self.ws.numel(),
             _stream_handle(stream)))
+        _keep(stream, self.ws, self._per, self._fb, self._snr)
         return self.periods, self.foldbins, self.snr
 
     def series_result(self, i: int):
@@ -630,8 +685,9 @@ class BatchSearcher:
 def periodogram_batch(x, series: Sequence[Series], widths: Sequence[int],
                       ws_budget: int = DEFAULT_BATCH_BUDGET, stream=None):
     """Batched periodograms; returns (periods, foldbins, snr, trial_offsets)."""
-    s = BatchSearcher(series, widths, ws_budget, device=x.device)
-    per, fb, snr = s(x, stream)
+    with _on(stream):
+        s = BatchSearcher(series, widths, ws_budget, device=x.device)
+        per, fb, snr = s(x)
     return per, fb, snr, s.trial_offsets
 
 
@@ -726,6 +782,12 @@ def shard_series(costs: Sequence[float], rank: int, world: int):
 def plan_cache_clear() -> None:
     """Release every cached plan (only when no call or captured graph still uses one)."""
     _check(library().ffa_plan_cache_clear())
+
+
+def set_wait_limit_ms(ms: float) -> None:
+    """Limit of every device-side wait of a periodogram launch (default 1000 ms); a wait
+    that runs out makes the search report FFA_ERR_TIMEOUT (see ffa_set_wait_limit_ms)."""
+    _check(library().ffa_set_wait_limit_ms(float(ms)))
 
 
 def check(ws, stream=None) -> None:

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -38,6 +39,21 @@ ffa_status fail(ffa_status st, const char* fmt, ...) {
 ffa_status cuda_fail(cudaError_t e, const char* what) {
     return fail(FFA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
+
+// Fault injection for tests, by the environment variable FFA_FAULT: "plan" makes plan
+// building fail, "alloc" the page-locked table allocation and "launch" the start of the
+// launch sequence (each before any CUDA call of the call); "stage" makes the second stage of one transform
+// wait for one item more than exist, so that the wait runs out on the device and the
+// call reports FFA_ERR_TIMEOUT through ffa_check.
+bool fault(const char* what) {
+    const char* f = std::getenv("FFA_FAULT");
+    return f && std::strcmp(f, what) == 0;
+}
+
+// Limit of every device-side wait of the persistent launch, in milliseconds of SM clock
+// (at the maximum clock; a wait at a lower clock lasts proportionally longer).
+std::atomic<double> g_wait_ms{1000.0};
+constexpr double kCyclesPerMs = 2.1e6;
 
 #define FFA_CUDA(call, what)                      \
     do {                                          \
@@ -547,6 +563,8 @@ ffa_status build_plan(Plan& pl) {
 // Page-locked copy of the plan's tables, made on first execution (planning alone needs
 // no CUDA device).  Copied into the workspace on every call.
 ffa_status ensure_pinned(Plan& pl) {
+    if (fault("alloc")) return fail(FFA_ERR_CUDA, "injected fault: alloc");
+    if (fault("launch")) return fail(FFA_ERR_CUDA, "injected fault: launch");
     std::lock_guard<std::mutex> lk(g_plan_mu);
     if (pl.pinned) return FFA_OK;
     void* p = nullptr;
@@ -611,6 +629,7 @@ std::map<PlanKey, std::unique_ptr<Plan>> g_plans;
 
 ffa_status get_plan_series(const std::vector<SeriesSpec>& series, const int32_t* h_widths,
                            int32_t nw, const Tiles& tiles, Plan** out) {
+    if (fault("plan")) return fail(FFA_ERR_UNSUPPORTED, "injected fault: plan");
     if (nw > 0 && !h_widths) return fail(FFA_ERR_ARG, "widths is null");
     PlanKey key{series, std::vector<int>(h_widths, h_widths + std::max(nw, 0)), tiles};
     {
@@ -656,6 +675,7 @@ std::map<BatchKey, std::unique_ptr<Batch>> g_batches;
 
 ffa_status get_batch(const ffa_series* h_series, int32_t nseries, const int32_t* h_widths,
                      int32_t nw, size_t budget, const Tiles& tiles, Batch** out) {
+    if (fault("plan")) return fail(FFA_ERR_UNSUPPORTED, "injected fault: plan");
     if (!h_series || nseries < 1) return fail(FFA_ERR_ARG, "no series");
     if (nw > 0 && !h_widths) return fail(FFA_ERR_ARG, "widths is null");
     std::vector<SeriesSpec> all(nseries);
@@ -744,11 +764,12 @@ struct SideStream {
     cudaEvent_t fork = nullptr, join = nullptr;
 };
 
+constexpr int kMaxDevices = 64;
 SideStream* side_stream() {
-    thread_local SideStream t;
+    thread_local SideStream t[kMaxDevices];  // one per device, made once per (thread, device)
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
-    if (t.dev == dev) return &t;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    if (t[dev].dev == dev) return &t[dev];
     SideStream n;
     n.dev = dev;
     if (cudaStreamCreateWithFlags(&n.s, cudaStreamNonBlocking) != cudaSuccess ||
@@ -757,8 +778,8 @@ SideStream* side_stream() {
         cudaGetLastError();  // clear; fall back to the caller's stream
         return nullptr;
     }
-    t = n;  // the previous device's stream and events stay (a thread rarely switches)
-    return &t;
+    t[dev] = n;
+    return &t[dev];
 }
 
 ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d_periods,
@@ -817,6 +838,7 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     pp.queue = counters;
     pp.done = counters + 1;
     pp.smem_floats = pl.smem_floats;
+    pp.wait_cycles = (long long)(g_wait_ms.load() * kCyclesPerMs);
     RecParams rp{};
     rp.top = tp;
     rp.stage_count = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt);
@@ -825,6 +847,10 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     rp.ring = pl.ring;
     rp.nbatches = pl.nbatches;
     rp.batch_base = (int)(pl.trs.size() * kMaxStages);
+    rp.inject_tr = -1;
+    if (fault("stage"))  // the first transform with a top pass
+        for (size_t t = 0; t < pl.trs.size() && rp.inject_tr < 0; ++t)
+            if (pl.trs[t].depth > 0) rp.inject_tr = (int)t;
     rp.heads = heads;
     rp.tables = toptab;
 
@@ -913,6 +939,11 @@ const char* ffa_last_error(void) { return g_err.c_str(); }
 const char* ffa_version(void) { return "libffa 0.1 (sm_103a)"; }
 
 int64_t ffa_launch_count(void) { return g_launches.load(); }
+ffa_status ffa_set_wait_limit_ms(double ms) {
+    if (!(ms > 0.0) || ms > 60000.0) return fail(FFA_ERR_ARG, "wait limit must be in (0, 60000] ms");
+    g_wait_ms.store(ms);
+    return FFA_OK;
+}
 int32_t ffa_kernel_kinds(void) { return kAllKinds; }
 const char* ffa_kernel_name(int32_t kind) {
     return (kind >= 0 && kind < kAllKinds) ? kKindNames[kind] : "";
@@ -948,16 +979,23 @@ ffa_status ffa_downsample_workspace(int64_t n, size_t* bytes) {
     return FFA_OK;
 }
 
+ffa_status ffa_downsample_length(int64_t n, double factor, int64_t* n_out) {
+    if (!n_out) return fail(FFA_ERR_ARG, "null pointer");
+    if (n <= 0) return fail(FFA_ERR_ARG, "n must be positive");
+    if (!(factor >= 1.0) || !std::isfinite(factor) || factor >= 4294967296.0)
+        return fail(FFA_ERR_ARG, "factor must be a finite number >= 1");
+    *n_out = (int64_t)std::floor((double)n / factor);  // complete windows only
+    return FFA_OK;
+}
+
 ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_out,
                           int64_t out_cap, int64_t* n_out, void* d_ws, size_t ws_bytes,
                           void* stream) {
     if (!d_x || !d_out || !n_out || !d_ws) return fail(FFA_ERR_ARG, "null pointer");
-    if (n <= 0) return fail(FFA_ERR_ARG, "n must be positive");
-    if (!(factor >= 1.0) || !std::isfinite(factor) || factor >= 4294967296.0)
-        return fail(FFA_ERR_ARG, "factor must be a finite number >= 1");
+    ffa_status st0 = ffa_downsample_length(n, factor, n_out);
+    if (st0 != FFA_OK) return st0;
     if (!aligned256(d_ws)) return fail(FFA_ERR_ARG, "workspace must be 256-byte aligned");
-    const int64_t nk = (int64_t)std::floor((double)n / factor);
-    *n_out = nk;
+    const int64_t nk = *n_out;
     if (out_cap < nk) return fail(FFA_ERR_CAPACITY, "out_cap %lld < %lld", (long long)out_cap,
                                   (long long)nk);
     size_t need = 0;

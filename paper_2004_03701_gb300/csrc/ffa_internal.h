@@ -381,6 +381,7 @@ struct PersistentParams {
     int* queue;                     // dispatch counter, zero at launch
     int* done;                      // completion counters, zero at launch
     int smem_floats;                // dynamic shared floats before the queue slot (a multiple of 4)
+    long long wait_cycles;          // limit of every wait of a CTA, SM clock cycles
 };
 
 // The per-item records of a queue, made on the device before the FFA launch.
@@ -392,6 +393,8 @@ struct RecParams {
     int ring;                       // scratch ring slots (a batch reuses slot batch % ring)
     int nbatches;
     int batch_base;                 // index of batch 0's counter among the counters
+    int inject_tr;                  // fault injection (tests): this transform's stage 1 waits
+                                    // for one item more than exist (-1: none)
     ItemHead* heads;
     int* tables;
 };

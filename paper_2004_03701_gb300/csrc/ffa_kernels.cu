@@ -318,17 +318,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
-// Spins on the mbarrier for at most ~1 s of SM clock; false if it ran out.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+// Spins on the mbarrier for at most `limit` SM clock cycles (by default 2^31, about 1 s);
+// false if it ran out.
+constexpr long long kWaitCycles = 1LL << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
 
 struct QueueHook {
     static constexpr bool kInitEachItem = false;  // the copy barrier is made once per CTA
+    long long wait = kWaitCycles;   // limit of every wait, SM clock cycles (all threads)
     unsigned cpar = 0;              // parity of the copy barrier's next phase (all threads)
     bool failed = false;            // a copy wait of the item ran out (all threads)
     // thread 0 only:
@@ -360,7 +364,7 @@ struct QueueHook {
         // (the buffers were last read by earlier items, whose reads had all returned
         // before the barrier that ended them, so the copies may overwrite them)
         if (next) {  // the next item's head (fetched one item ago) says whether it has a table
-            if (!mbar_wait_bounded(next_bar, next_par)) {
+            if (!mbar_wait_bounded(next_bar, next_par, wait)) {
                 timed_out = true;
             } else if (next->item.pass >= 0) {
                 mbar_expect_tx(table_bar, (unsigned)kTopRecBytes);
@@ -381,6 +385,7 @@ struct QueueHook {
         asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
     __device__ __forceinline__ unsigned parity() const { return cpar; }
+    __device__ __forceinline__ long long limit() const { return wait; }
     __device__ __forceinline__ void copied() { cpar ^= 1u; }
     __device__ __forceinline__ void fail() { failed = true; }
 };
@@ -391,6 +396,7 @@ struct NoHook {
     __device__ __forceinline__ void run() {}
     __device__ __forceinline__ void store_wait() { bulk_store_wait(); }
     __device__ __forceinline__ unsigned parity() const { return 0u; }
+    __device__ __forceinline__ long long limit() const { return kWaitCycles; }
     __device__ __forceinline__ void copied() {}
     __device__ __forceinline__ void fail() {}
 };
@@ -811,11 +817,11 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
             desc[l * P.nmax + r] = bottom_desc(n, kRegLevels + 1 + l, r, p);
         }
     }
-    const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity());
+    const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity(), hook.limit());
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
             atomicOr(P.status, kDevTimeout);
-            mbar_wait_bounded(bar, hook.parity());  // let a late copy land before the CTA exits
+            mbar_wait_bounded(bar, hook.parity(), hook.limit());  // a late copy lands before the CTA exits
         }
         hook.fail();
         return;
@@ -992,6 +998,7 @@ __global__ void __launch_bounds__(kPrepThreads) item_rec_kernel(RecParams R) {
     if (stage > 0) {  // every item of the stage before, in this transform
         h.wait = item.tr * kMaxStages + stage - 1;
         h.need = R.stage_count[h.wait];
+        if (item.tr == R.inject_tr && stage == 1) h.need += 1;  // fault injection (tests)
     } else if (item.pass == -1 && tr.batch >= R.ring) {
         // a sub-tree writes its batch's ring slot once the batch that used it before has
         // finished reading it: all of that batch's last-pass items
@@ -1107,11 +1114,11 @@ __device__ __forceinline__ bool top_item(const TopParams& P, const WorkItem item
         }
     }
 
-    const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity());
+    const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity(), hook.limit());
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
             atomicOr(P.status, kDevTimeout);
-            mbar_wait_bounded(bar, hook.parity());
+            mbar_wait_bounded(bar, hook.parity(), hook.limit());
         }
         hook.fail();
         return !last;
@@ -1209,6 +1216,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
     unsigned stat = 0, par = 0, inflight = 0;
     int ha = 0, ta = 0;
     QueueHook hook;
+    hook.wait = P.wait_cycles;
     if (tid == 0) {
         hook.done = P.done;
         for (int j = 0; j < 5; ++j) mbar_init(&hbar[j], 1);
@@ -1225,7 +1233,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
             }
         }
         // the first item's table, once its head has landed
-        if (a < N && mbar_wait_bounded(&hbar[0], 0)) {
+        if (a < N && mbar_wait_bounded(&hbar[0], 0, P.wait_cycles)) {
             par ^= 1u;
             inflight &= ~1u;
             if (hbuf[0].item.pass >= 0) {
@@ -1249,7 +1257,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
                 const ItemHead& H = hbuf[ha];
                 bool ok = true;
                 if (H.item.pass >= 0) {
-                    ok = mbar_wait_bounded(&tbar[ta], (par >> (3 + ta)) & 1u);
+                    ok = mbar_wait_bounded(&tbar[ta], (par >> (3 + ta)) & 1u, P.wait_cycles);
                     par ^= 1u << (3 + ta);
                     inflight &= ~(1u << (3 + ta));
                 }
@@ -1264,7 +1272,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
                             __nanosleep(256);
                             asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(seen) : "l"(cnt) : "memory");
                             if (seen >= H.need) break;
-                            if (clock64() - t0 > (1LL << 31)) {
+                            if (clock64() - t0 > P.wait_cycles) {
                                 ok = false;
                                 break;
                             }
@@ -1337,7 +1345,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
         hook.release();
         // copies still in flight land before the CTA exits
         for (int j = 0; j < 5; ++j)
-            if ((inflight >> j) & 1u) mbar_wait_bounded(&hbar[j], (par >> j) & 1u);
+            if ((inflight >> j) & 1u) mbar_wait_bounded(&hbar[j], (par >> j) & 1u, P.wait_cycles);
     }
 }
 

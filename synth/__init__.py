@@ -82,12 +82,15 @@ def pulse_train(n: int, tsamp: float, pulse: Pulse) -> np.ndarray:
     ph = np.mod(t / pulse.period - pulse.phase + 0.5, 1.0) - 0.5   # in [-0.5, 0.5)
     sigma = pulse.duty / (2.0 * np.sqrt(2.0 * np.log(2.0)))
     s = np.exp(-0.5 * (ph / sigma) ** 2)
-    s /= np.sqrt(np.sum(s * s))
-    return pulse.amplitude * s
+    norm = np.sqrt(np.sum(s * s))
+    if not norm > 0.0:  # no sample near any pulse (a very narrow, sparse train): no signal
+        return np.zeros(n, np.float64)
+    return pulse.amplitude * (s / norm)
 
 
-def make_series(n: int, tsamp: float, seed: int, pulses=()) -> np.ndarray:
-    x = white_noise(n, seed)
+def make_series(n: int, tsamp: float, seed: int, pulses=(), red: bool = False) -> np.ndarray:
+    """N(0, 1) noise (plus 1/f red noise if `red`) and the pulse trains, float32."""
+    x = red_noise(n, tsamp, seed).astype(np.float64) if red else white_noise(n, seed)
     for p in pulses:
         x = x + pulse_train(n, tsamp, p)
     return x.astype(np.float32)
@@ -160,6 +163,7 @@ class SeriesParams:
     bmin: int
     bmax: int
     pulses: List[Pulse] = field(default_factory=list)
+    red: bool = False  # N(0,1) plus 1/f red noise (to be de-reddened before the search)
 
 
 @dataclass
@@ -191,7 +195,7 @@ def _fill_batch(series: Sequence[SeriesParams], seeds: Sequence[int], threads: i
 
     def one(k):
         s = series[k]
-        x[s.offset:s.offset + s.n] = make_series(s.n, s.tsamp, seeds[k], s.pulses)
+        x[s.offset:s.offset + s.n] = make_series(s.n, s.tsamp, seeds[k], s.pulses, s.red)
 
     with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
         list(ex.map(one, range(len(series))))
@@ -201,17 +205,19 @@ def _fill_batch(series: Sequence[SeriesParams], seeds: Sequence[int], threads: i
 def batch_uneven(nseries: int = 256, nmin: int = 2 ** 20, nmax: int = 2 ** 23,
                  seed: Optional[int] = None, threads: int = 16) -> BatchWorkload:
     """Series of uneven length n ~ U[nmin, nmax] at 64 us, each N(0,1) noise plus one
-    Gaussian pulse train, each with its own period range inside 0.1-30 s (log-uniform
-    Pmin in [0.1, 3] s, Pmax/Pmin log-uniform in [3, 100], capped at 30 s); bins
-    240-260, 11 widths.  Series are stored back to back in one buffer."""
+    Gaussian pulse train, each with its own period range inside 0.1-30 s: two
+    log-uniform draws in [0.1, 30] s, sorted, with Pmax raised to at least 2 Pmin
+    (capped at 30 s); bins 240-260, 11 widths.  Series are stored back to back in one
+    buffer."""
     seed = SEED_BASE + 3 if seed is None else seed
     r = rng(seed)
     tsamp = 64e-6
     series, seeds, off = [], [], 0
     for i in range(nseries):
         n = int(r.integers(nmin, nmax + 1))
-        pmin = float(np.exp(r.uniform(np.log(0.1), np.log(3.0))))
-        pmax = min(30.0, pmin * float(np.exp(r.uniform(np.log(3.0), np.log(100.0)))))
+        lo, hi = sorted(float(v) for v in np.exp(r.uniform(np.log(0.1), np.log(30.0), 2)))
+        pmin = lo
+        pmax = min(30.0, max(hi, 2.0 * lo))
         per = float(np.exp(r.uniform(np.log(pmin), np.log(pmax))))
         pulse = Pulse(per, float(r.uniform(0.01, 0.05)), float(r.uniform(8.0, 20.0)),
                       float(r.uniform()))
@@ -225,10 +231,11 @@ def batch_uneven(nseries: int = 256, nmin: int = 2 ** 20, nmax: int = 2 ** 23,
 
 def batch_int8_stress(nseries: int = 1024, n: int = 2 ** 21, seed: Optional[int] = None,
                       threads: int = 16) -> BatchWorkload:
-    """nseries series of n samples at 64 us, N(0,1) noise (the white series left after
-    red-noise removal), one Gaussian pulse train in every tenth series; periods
-    0.1-10 s, bins 480-520, the 16-width set.  Meant to be normalised and stored as
-    int8 before the search."""
+    """nseries series of n samples at 64 us, N(0,1) noise plus 1/f red noise
+    (`red_noise`), one Gaussian pulse train in every tenth series; periods 0.1-10 s,
+    bins 480-520, the 16-width set.  Meant to be de-reddened by a running median of
+    about 1 s (Sec. 5.2), normalised and stored as int8 before the search, all on the
+    device by the library (`deredden_normalise_batch` in the benchmark and tests)."""
     seed = SEED_BASE + 5 if seed is None else seed
     r = rng(seed)
     tsamp = 64e-6
@@ -239,7 +246,11 @@ def batch_int8_stress(nseries: int = 1024, n: int = 2 ** 21, seed: Optional[int]
             pulses = [Pulse(float(np.exp(r.uniform(np.log(0.1), np.log(10.0)))),
                             float(r.uniform(0.01, 0.05)), float(r.uniform(8.0, 20.0)),
                             float(r.uniform()))]
-        series.append(SeriesParams(i * n, n, tsamp, 0.1, 10.0, 480, 520, pulses))
+        series.append(SeriesParams(i * n, n, tsamp, 0.1, 10.0, 480, 520, pulses, red=True))
         seeds.append(seed * 7919 + i)
     return BatchWorkload("batch_int8_%dx2^21_64us" % nseries, _fill_batch(series, seeds, threads),
                          series, WIDTHS_16)
+
+
+# Running-median window of the batch_int8 stress series (Sec. 5.2: about 1 s): odd samples
+DEREDDEN_SECONDS = 1.0

@@ -277,3 +277,16 @@ def test_plan_options_boxcar_template(lib):
                                        ctypes.cast(ctypes.byref(opts), ctypes.c_void_p),
                                        ctypes.byref(info))
     assert st == 1 and b"boxcar" in lib.ffa_last_error()
+
+
+def test_downsample_length(lib):
+    """The output length query: floor(n / f) complete windows (reading c5), for the
+    binding to size its output; bad arguments rejected."""
+    n_out = ctypes.c_int64()
+    for n, f in [(1000, 1.0), (1000, 3.0), (1000, 3.7), (2 ** 23, 13.02), (5, 6.0)]:
+        assert lib.ffa_downsample_length(n, f, ctypes.byref(n_out)) == 0
+        assert n_out.value == int(np.floor(n / f)), (n, f)
+    assert lib.ffa_downsample_length(0, 2.0, ctypes.byref(n_out)) == 1
+    assert lib.ffa_downsample_length(10, 0.5, ctypes.byref(n_out)) == 1
+    assert lib.ffa_downsample_length(10, float("nan"), ctypes.byref(n_out)) == 1
+    assert lib.ffa_downsample_length(10, 2.0, None) == 1

@@ -3,8 +3,9 @@ that bench.py times (one BatchSearcher over the whole batch, 48 GB workspace bud
 chunk), checked on sampled outputs that the oracle computes one by one:
 
   * batch_uneven: 256 FP32 series of U[2^20, 2^23] samples, own period ranges;
-  * batch_int8: 1024 series of 2^21 samples normalised by the library and stored as
-    int8 (the oracle searches the same dequantised values: pure accumulation error).
+  * batch_int8: 1024 series of 2^21 samples of white plus red noise, de-reddened by the
+    library's running median (1 s) and normalised and stored as int8 by the library (the
+    oracle searches the same dequantised values: pure accumulation error).
 
 For three series of each batch (first, middle, last) a spread of transforms is
 compared: periods and fold bins exactly, S/N within 1e-4 of the FP64 oracle."""
@@ -73,10 +74,9 @@ def test_batch_uneven_full_size(F):
 def test_batch_int8_full_size(F):
     b = synth.batch_int8_stress()
     x32 = torch.from_numpy(b.x).cuda()
-    q = torch.empty(x32.numel(), dtype=torch.int8, device="cuda")
-    for s in b.series:
-        q[s.offset:s.offset + s.n] = F.normalise(x32[s.offset:s.offset + s.n],
-                                                 dtype=torch.int8)[0]
+    # red noise removed by the library's running median (1 s), then int8 storage
+    width = F.median_width(synth.DEREDDEN_SECONDS, b.series[0].tsamp)
+    q = F.prepare_batch(x32, [(s.offset, s.n) for s in b.series], width, torch.int8)
     del x32
     S = F.BatchSearcher(_series(F, b), b.widths, ws_budget=BUDGET)
     S(q)

@@ -55,3 +55,31 @@ def test_rejects_blocks_above_the_fixed_scratch(lib):
     st, _ = _noalloc(L, X)
     assert st == 2  # FFA_ERR_CAPACITY
     assert b"4 MiB" in L.ffa_last_error()
+
+
+def test_allocates_nothing_after_the_first_call(lib):
+    """After the first call on a device (which looks the array up, loading the library's
+    module with it under lazy loading), a call changes no device allocation and records
+    no profiling events (the launch counter still counts its kernels)."""
+    ffa, L = lib
+    X = torch.from_numpy(synth.normal_block(1000, 250, seed=7)).cuda()
+    st, out = _noalloc(L, X)
+    assert st == 0, L.ffa_last_error()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream().cuda_stream
+    ffa.profile_enable(True)
+    ffa.profile_reset()
+    free0 = torch.cuda.mem_get_info()[0]
+    launches0 = ffa.launch_count()
+    st = L.ffa_transform_noalloc(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1],
+                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    assert st == 0, L.ffa_last_error()
+    assert free1 == free0
+    assert ffa.launch_count() > launches0
+    for kind in ("ffa_bottom", "ffa_top"):
+        assert ffa.profile_query(kind)["launches"] == 0, kind
+    ffa.profile_enable(False)
+    ffa.profile_reset()
+    assert torch.equal(out, ffa.ffa_transform(X))
