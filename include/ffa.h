@@ -155,7 +155,8 @@ ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out
  * series: every output is a range-quantile query), for any width.
  * d_x: n floats (device), finite (NaN has no order).  d_med, d_y: n floats (device),
  * either may be NULL but not both; either may equal d_x (in place), not each other.
- * Workspace: ffa_running_median_workspace(n) bytes (about 16 n).  Deterministic.
+ * Workspace: ffa_running_median_workspace(n) bytes (about 16 n), a status word first
+ * (ffa_check reads it).  Deterministic.
  * Errors: FFA_ERR_ARG (null pointers, n outside [1, 2^31 - 1], even or non-positive
  *         width, d_med == d_y), FFA_ERR_CAPACITY (workspace too small).
  * ---------------------------------------------------------------------------- */
@@ -215,6 +216,18 @@ ffa_status ffa_find_peaks(const double* d_periods, const float* d_snr, int64_t n
                           int32_t nw, double tobs, const ffa_peak_opts* opts,
                           ffa_peak* d_peaks, int64_t peak_cap, int64_t* d_npeaks, void* d_ws,
                           size_t ws_bytes, void* stream);
+/* The intermediate results of the last ffa_find_peaks on a workspace (same ntrials, nw
+ * and opts), for inspection: synchronises `stream`, then copies to host memory
+ *   h_nseg: the segment count;
+ *   h_ctrl: min(nseg, ctrl_cap) x nw x 2 doubles {nu_j, s_j} per segment and width,
+ *           s_j NaN where the segment gave no control point;
+ *   h_fits: nw x 10 doubles per width {xbar, xscale, valid, c_0 .. c_6}: where valid
+ *           is 1, the threshold at frequency nu is sum_a c_a u^a with
+ *           u = (ln nu - xbar) / xscale (c_a is 0 past the degree).
+ * Errors: FFA_ERR_ARG (null pointers, bad sizes or options), FFA_ERR_CUDA. */
+ffa_status ffa_find_peaks_fits(const void* d_ws, int64_t ntrials, int32_t nw,
+                               const ffa_peak_opts* opts, int64_t* h_nseg, double* h_ctrl,
+                               int64_t ctrl_cap, double* h_fits, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Periodogram search plan (paper Sec. 5.3, Fig. 4; Sec. 5.6 for the first factor).
@@ -379,10 +392,22 @@ ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, doubl
                                 void* d_ws, size_t ws_bytes, void* stream);
 
 /* Synchronises `stream`, reads and clears the device status word of a workspace used
- * by ffa_periodogram / ffa_transform / ffa_downsample / ffa_find_peaks.  FFA_OK if no
+ * by ffa_periodogram / ffa_transform / ffa_downsample / ffa_running_median /
+ * ffa_find_peaks.  FFA_OK if no
  * device-side check failed, else FFA_ERR_TIMEOUT or FFA_ERR_DEVICE (the message names
  * the failed checks). */
 ffa_status ffa_check(void* d_ws, void* stream);
+
+/* Bounds-checked debug build.  The library compiled with FFA_CHECKED (built beside the
+ * normal one as libffa_checked.so; same entry points, same results) checks every
+ * shared-memory range and global index its kernels compute from runtime data before
+ * use: a violation skips the access (or the whole work item) and sets bit 32 in the
+ * status word, which ffa_check reports as FFA_ERR_DEVICE ("an index out of range").
+ * *checked: 1 in that build, 0 in the normal one.  *bits: synchronises the device and
+ * returns (and clears) bit 32 if any kernel of the library found a violation since the
+ * last call, whatever workspace (or none, as for the standalone boxcar S/N) the launch
+ * had; always 0 in the normal build.  Errors: FFA_ERR_ARG (null pointer), FFA_ERR_CUDA. */
+ffa_status ffa_checked_status(int32_t* checked, uint32_t* bits);
 
 /* Limit of every device-side wait of a periodogram launch (a CTA waiting for the items
  * an item depends on, or for its own bulk copies), in milliseconds of SM clock at the

@@ -38,6 +38,13 @@ __all__ = [
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libffa.so")
+# The bounds-checked debug build (same entry points); loaded instead of libffa.so when the
+# environment has FFA_LIBRARY=checked at the first call.
+LIB_CHECKED_PATH = os.path.join(_PKG, "libffa_checked.so")
+
+
+def _lib_path() -> str:
+    return LIB_CHECKED_PATH if os.environ.get("FFA_LIBRARY") == "checked" else LIB_PATH
 
 FFA_F32, FFA_F16, FFA_I8 = 0, 1, 2
 _STATUS = {0: "FFA_OK", 1: "FFA_ERR_ARG", 2: "FFA_ERR_CAPACITY", 3: "FFA_ERR_CUDA",
@@ -95,14 +102,16 @@ def build(force: bool = False) -> str:
 
 
 def library() -> ctypes.CDLL:
-    """The loaded libffa.so.  Raises if it has not been built."""
+    """The loaded libffa.so (libffa_checked.so with FFA_LIBRARY=checked).  Raises if it
+    has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError("libffa.so is not built (run __graft_entry__.build()); "
-                           "there is no CPU fallback")
-    L = ctypes.CDLL(LIB_PATH)
+    path = _lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built (run __graft_entry__.build()); "
+                           "there is no CPU fallback" % os.path.basename(path))
+    L = ctypes.CDLL(path)
     i32, i64, dbl, vp, sz = (ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p,
                              ctypes.c_size_t)
     L.ffa_last_error.restype = ctypes.c_char_p
@@ -129,6 +138,7 @@ def library() -> ctypes.CDLL:
                                        i64, vp, sz, vp]
     L.ffa_check.argtypes = [vp, vp]
     L.ffa_set_wait_limit_ms.argtypes = [dbl]
+    L.ffa_checked_status.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint32)]
     L.ffa_batch_plan.argtypes = [vp, i32, vp, i32, sz, vp, ctypes.POINTER(_BatchInfo)]
     L.ffa_periodogram_batch.argtypes = [vp, i32, vp, i32, vp, i32, sz, vp, vp, vp, i64, vp,
                                         sz, vp]
@@ -139,6 +149,8 @@ def library() -> ctypes.CDLL:
     L.ffa_find_peaks_workspace.argtypes = [i64, i32, ctypes.POINTER(_PeakOpts), ctypes.POINTER(sz)]
     L.ffa_find_peaks.argtypes = [vp, vp, i64, i32, dbl, ctypes.POINTER(_PeakOpts), vp, i64, vp,
                                  vp, sz, vp]
+    L.ffa_find_peaks_fits.argtypes = [vp, i64, i32, ctypes.POINTER(_PeakOpts),
+                                      ctypes.POINTER(i64), vp, i64, vp, vp]
     L.ffa_running_median_workspace.argtypes = [i64, ctypes.POINTER(sz)]
     L.ffa_running_median.argtypes = [vp, i64, i64, vp, vp, vp, sz, vp]
     L.ffa_launch_count.restype = i64
@@ -157,7 +169,8 @@ def library() -> ctypes.CDLL:
               "ffa_periodogram_opts", "ffa_batch_plan_opts", "ffa_periodogram_batch_opts",
               "ffa_boxcar_snr_template", "ffa_running_median_workspace",
               "ffa_running_median", "ffa_find_peaks_workspace", "ffa_find_peaks",
-              "ffa_profile_query", "ffa_set_wait_limit_ms"):
+              "ffa_profile_query", "ffa_set_wait_limit_ms", "ffa_find_peaks_fits",
+              "ffa_checked_status"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -370,6 +383,19 @@ class PeakFinder:
 
     def check(self, stream=None) -> None:
         _check(library().ffa_check(_vp(self.ws), _stream_handle(stream)))
+
+    def fits(self, stream=None):
+        """The last search's control points and threshold fits (see ffa_find_peaks_fits):
+        (ctrl [segments, nw, 2] {nu_j, s_j, NaN s_j without a point}, fits [nw, 10]
+        {xbar, xscale, valid, c_0 .. c_6})."""
+        nseg = ctypes.c_int64()
+        cap = int(self.opts.max_segments)
+        ctrl = np.empty((cap, self.nw, 2), np.float64)
+        fits = np.empty((self.nw, 10), np.float64)
+        _check(library().ffa_find_peaks_fits(_vp(self.ws), self.ntrials, self.nw,
+                                             ctypes.byref(self.opts), ctypes.byref(nseg),
+                                             _vp(ctrl), cap, _vp(fits), _stream_handle(stream)))
+        return ctrl[:min(nseg.value, cap)].copy(), fits
 
     def result(self):
         counts = self.npeaks.cpu().numpy()
@@ -793,6 +819,14 @@ def set_wait_limit_ms(ms: float) -> None:
 def check(ws, stream=None) -> None:
     """Raises FFAError if a device-side check of the last calls on `ws` failed."""
     _check(library().ffa_check(_vp(ws), _stream_handle(stream)))
+
+
+def checked_status() -> Tuple[bool, int]:
+    """(whether the loaded library is the bounds-checked build, the violation bits its
+    kernels recorded since the last call; synchronises the device in that build)."""
+    c, bits = ctypes.c_int32(), ctypes.c_uint32()
+    _check(library().ffa_checked_status(ctypes.byref(c), ctypes.byref(bits)))
+    return bool(c.value), int(bits.value)
 
 
 def launch_count() -> int:

@@ -815,6 +815,9 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     bp.status = status;
     bp.nmax = pl.bottom_nmax;
     bp.elems_max = pl.bottom_elems;
+    bp.src_cap = pl.ds_floats;
+    bp.dst_cap = pl.scratch_floats;
+    bp.ntrials = pl.ntrials;
     pp.bottom_snr = bp;
     pp.bottom_snr.nmax = pl.bottom0_nmax;
     pp.bottom_snr.elems_max = pl.bottom0_elems;
@@ -830,6 +833,8 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     tp.snr = d_snr;
     tp.status = status;
     tp.items = d_items;
+    tp.buf_cap = pl.scratch_floats;
+    tp.ntrials = pl.ntrials;
     ItemHead* heads = reinterpret_cast<ItemHead*>(ws + pl.o_heads);
     int* toptab = reinterpret_cast<int*>(ws + pl.o_toptab);
     pp.heads = heads;
@@ -839,6 +844,8 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     pp.done = counters + 1;
     pp.smem_floats = pl.smem_floats;
     pp.wait_cycles = (long long)(g_wait_ms.load() * kCyclesPerMs);
+    pp.ncounters = (int)(pl.counter_bytes / sizeof(int)) - 1;
+    pp.ntables = pl.ntop;
     RecParams rp{};
     rp.top = tp;
     rp.stage_count = reinterpret_cast<const int*>(ws + pl.o_tables + pl.o_stcnt);
@@ -853,6 +860,8 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
             if (pl.trs[t].depth > 0) rp.inject_tr = (int)t;
     rp.heads = heads;
     rp.tables = toptab;
+    rp.ntables = pl.ntop;
+    rp.status = status;
 
     // ---- item records on a side stream, concurrent with prefix sums and
     //      downsampling (they need only the tables); joined before the FFA launch
@@ -878,6 +887,9 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     xp.prefix = prefix;
     xp.nchunks = pl.nchunks;
     xp.total = pl.input_total;
+    xp.x_cap = pl.n;
+    xp.prefix_cap = pl.prefix_len;
+    xp.status = status;
     FFA_CUDA(launch_prefix(xp, st), "prefix launch");
     DownsampleParams dp{};
     dp.x = d_x;
@@ -889,6 +901,10 @@ ffa_status run_periodogram(const Plan& pl, const void* d_x, int dtype, double* d
     dp.nblocks = (int)pl.ds_blocks.size();
     dp.total = pl.ds_total;
     dp.out = ds;
+    dp.x_cap = pl.n;
+    dp.prefix_cap = pl.prefix_len;
+    dp.out_cap = pl.ds_floats;
+    dp.status = status;
     FFA_CUDA(launch_downsample(dp, st), "downsample launch");
 
     // ---- all FFA work: one persistent launch over the plan's queue
@@ -1018,6 +1034,9 @@ ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_o
     pp.prefix = prefix;
     pp.nchunks = nch;
     pp.total = n;
+    pp.x_cap = n;
+    pp.prefix_cap = n + 1;
+    pp.status = reinterpret_cast<unsigned*>(ws);
     FFA_CUDA(launch_prefix(pp, st), "prefix launch");
     DownsampleParams dp{};
     dp.x = d_x;
@@ -1035,6 +1054,10 @@ ffa_status ffa_downsample(const float* d_x, int64_t n, double factor, float* d_o
     dp.single.x_off = 0;
     dp.single.x_n = n;
     dp.single.pre_off = 0;
+    dp.x_cap = n;
+    dp.prefix_cap = n + 1;
+    dp.out_cap = out_cap;
+    dp.status = reinterpret_cast<unsigned*>(ws);
     fixed_point(factor, &dp.single.f_int, &dp.single.f_frac);
     FFA_CUDA(launch_downsample(dp, st), "downsample launch");
     return FFA_OK;
@@ -1087,6 +1110,8 @@ ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d
     const int rows_d = (rows + (1 << D) - 1) >> D;
     bp.nmax = rows_d;
     bp.elems_max = rows_d * cols;
+    bp.src_cap = (long long)rows * cols;
+    bp.dst_cap = (long long)rows * cols;
     const int smem = bottom_layout(bp.nmax, bp.elems_max, 0).total * 4;
     {
         LaunchScope ls(kFfaBottom, 8.0 * rows * cols, st);
@@ -1106,6 +1131,7 @@ ffa_status ffa_transform(const float* d_in, int32_t rows, int32_t cols, float* d
         tp.status = status;
         tp.single_pass = j;
         tp.single_rows = K;
+        tp.buf_cap = (long long)rows * cols;
         LaunchScope ls(kFfaTop, 8.0 * rows * cols, st);
         FFA_CUDA(launch_top(tp, (1 << dout) * nb, top_layout(K, L, cols, 0, false).total * 4, st),
                  "ffa_top launch");
@@ -1356,6 +1382,21 @@ ffa_status ffa_periodogram_host(const float* h_x, int64_t n, double tsamp, doubl
     return FFA_OK;
 }
 
+ffa_status ffa_checked_status(int32_t* checked, uint32_t* bits) {
+    if (!checked || !bits) return fail(FFA_ERR_ARG, "null pointer");
+    *checked = kChecked ? 1 : 0;
+    *bits = 0;
+    if (kChecked) {
+        FFA_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize");
+        unsigned v[3] = {0, 0, 0};
+        FFA_CUDA(bounds_seen_kernels(&v[0]), "read status");
+        FFA_CUDA(bounds_seen_median(&v[1]), "read status");
+        FFA_CUDA(bounds_seen_peaks(&v[2]), "read status");
+        *bits = v[0] | v[1] | v[2];
+    }
+    return FFA_OK;
+}
+
 ffa_status ffa_check(void* d_ws, void* stream) {
     if (!d_ws) return fail(FFA_ERR_ARG, "null workspace");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1366,11 +1407,12 @@ ffa_status ffa_check(void* d_ws, void* stream) {
     if (v & kDevTimeout) return fail(FFA_ERR_TIMEOUT, "a device-side wait ran out of time");
     if (v) {
         // bits 4, 8, 16: the peak finder's input checks (ffa_peaks.cu)
-        return fail(FFA_ERR_DEVICE, "device status 0x%x%s%s%s%s", v,
+        return fail(FFA_ERR_DEVICE, "device status 0x%x%s%s%s%s%s", v,
                     (v & 2u) ? "; a work item out of range" : "",
                     (v & 4u) ? "; peak finding: more segments than max_segments" : "",
                     (v & 8u) ? "; peak finding: a segment above 16384 trials" : "",
-                    (v & 16u) ? "; peak finding: periods not positive and non-decreasing" : "");
+                    (v & 16u) ? "; peak finding: periods not positive and non-decreasing" : "",
+                    (v & kDevBounds) ? "; an index out of range (checked build)" : "");
     }
     return FFA_OK;
 }

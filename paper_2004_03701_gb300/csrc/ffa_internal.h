@@ -44,6 +44,40 @@ constexpr int kTopMaxRows = 128;     // output rows per top CTA
 // Device status word bits (first word of every workspace).
 constexpr unsigned kDevTimeout = 1u;
 constexpr unsigned kDevBadItem = 2u;
+constexpr unsigned kDevBounds = 32u;  // a checked build found an index out of range
+
+// Checked build (compiled with FFA_CHECKED): every shared-memory range and global index
+// the kernels compute from runtime data is checked before use; a violation sets
+// kDevBounds in the status word and the access (or the whole work item) is skipped.
+#ifdef FFA_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+#ifdef __CUDACC__
+// Checked builds also record every violation here, one word per translation unit, so
+// that it is seen whatever status word (or none) the launch had; bounds_seen_*() read
+// and clear it.
+static __device__ unsigned g_bounds_seen;
+__device__ __forceinline__ void bounds_violation(unsigned* status) {
+    if (status) atomicOr(status, kDevBounds);
+    atomicOr(&g_bounds_seen, kDevBounds);
+}
+// [i, i + len) inside [0, cap); in an unchecked build always true.
+__device__ __forceinline__ bool in_range(long long i, long long len, long long cap,
+                                         unsigned* status) {
+    if (!kChecked) return true;
+    if (i >= 0 && len >= 0 && i + len <= cap) return true;
+    bounds_violation(status);
+    return false;
+}
+// Floats of the launch's dynamic shared memory.
+__device__ __forceinline__ long long dyn_smem_floats() {
+    unsigned r;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+    return (long long)(r / 4);
+}
+#endif
 
 // nint(a / d), ties up, for a >= 0, d > 0 (Sec. 2.2: i and j of the merge rule).
 __host__ __device__ inline int nint_div(long long a, long long d) {
@@ -298,6 +332,8 @@ struct PrefixParams {
     float2* prefix;         // double-float exclusive prefix sums
     int64_t nchunks;        // chunks over all series
     int64_t total;          // samples over all series
+    int64_t x_cap, prefix_cap;  // elements of x and of prefix (checks)
+    unsigned* status;
 };
 
 constexpr int kDownsampleThreads = 256;
@@ -314,6 +350,8 @@ struct DownsampleParams {
     int nblocks;
     int64_t total;        // sum of nk (algorithmic accounting)
     float* out;           // series buffer
+    int64_t x_cap, prefix_cap, out_cap;  // elements of x, prefix and out (checks)
+    unsigned* status;
 };
 
 struct BottomParams {
@@ -332,6 +370,8 @@ struct BottomParams {
     int elems_max;                  // largest sub-tree (floats) of the launch
     int snr_warps;                  // warps that score rows (fused S/N mode)
     int snr_floats;                 // shared floats those warps need (0 otherwise)
+    long long src_cap, dst_cap;     // floats of src and of each of dst, dst_odd (checks)
+    long long ntrials;              // trials of the S/N outputs (checks)
 };
 
 struct TopParams {
@@ -347,6 +387,8 @@ struct TopParams {
     unsigned* status;
     int single_pass;                // pass and rows per block when items is null
     int single_rows;
+    long long buf_cap;              // floats of each of buf0, buf1 (checks)
+    long long ntrials;              // trials of the S/N outputs (checks)
 };
 
 constexpr int kMaxStages = 16;  // sub-trees + up to 15 top passes per transform
@@ -382,6 +424,8 @@ struct PersistentParams {
     int* done;                      // completion counters, zero at launch
     int smem_floats;                // dynamic shared floats before the queue slot (a multiple of 4)
     long long wait_cycles;          // limit of every wait of a CTA, SM clock cycles
+    int ncounters;                  // completion counters (checks)
+    int ntables;                    // top-pass tables (checks)
 };
 
 // The per-item records of a queue, made on the device before the FFA launch.
@@ -397,6 +441,8 @@ struct RecParams {
                                     // for one item more than exist (-1: none)
     ItemHead* heads;
     int* tables;
+    int ntables;                    // top-pass tables (checks)
+    unsigned* status;
 };
 
 struct SnrParams {
@@ -407,6 +453,7 @@ struct SnrParams {
     float inv_std;
     float* snr;
     int warp_floats;
+    unsigned* status;     // (checks; may be null)
 };
 
 struct NormaliseParams {
@@ -426,6 +473,11 @@ cudaError_t launch_bottom(const BottomParams& P, int nblocks, int smem_bytes, bo
                           cudaStream_t s);
 cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStream_t s);
 cudaError_t launch_persistent(const PersistentParams& P, int smem_bytes, cudaStream_t s);
+// Read and clear the violations recorded by the kernels of ffa_kernels.cu, ffa_median.cu
+// and ffa_peaks.cu (checked builds).
+cudaError_t bounds_seen_kernels(unsigned* bits);
+cudaError_t bounds_seen_median(unsigned* bits);
+cudaError_t bounds_seen_peaks(unsigned* bits);
 cudaError_t launch_item_recs(const RecParams& R, cudaStream_t s);
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s);
 cudaError_t launch_normalise(const NormaliseParams& P, cudaStream_t s);

@@ -123,6 +123,9 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_partial_kernel(PrefixPa
     __shared__ float sh[kPrefixThreads * 17];
     __shared__ float2 wt[kPrefixThreads / 32];
     const PrefixSeg sg = prefix_seg(P, blockIdx.x);
+    if (kChecked && !(in_range(sg.x_off, sg.n, P.x_cap, threadIdx.x ? nullptr : P.status) &&
+                      in_range(blockIdx.x, 1, P.nchunks, threadIdx.x ? nullptr : P.status)))
+        return;  // uniform
     float v[kPrefixPerThread];
     prefix_load(P, sg.x_off + ((int64_t)blockIdx.x - sg.blk0) * kPrefixChunk, sg.x_off + sg.n, sh,
                 v);
@@ -140,6 +143,7 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_top_kernel(PrefixParams
     __shared__ float2 wt[kPrefixThreads / 32];
     const PrefixSeg sg = P.segs ? P.segs[blockIdx.x] : P.single;
     const int64_t nb = (sg.n + kPrefixChunk - 1) / kPrefixChunk;
+    if (kChecked && !in_range(sg.blk0, nb, P.nchunks, threadIdx.x ? nullptr : P.status)) return;
     float2* part = P.partial + sg.blk0;
     float2 carry = make_float2(0.f, 0.f);
     for (int64_t b0 = 0; b0 < nb; b0 += kPrefixThreads * kTopPerThread) {
@@ -168,6 +172,10 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_final_kernel(PrefixPara
     __shared__ float2 wt[kPrefixThreads / 32];
     const PrefixSeg sg = prefix_seg(P, blockIdx.x);
     const int64_t local0 = ((int64_t)blockIdx.x - sg.blk0) * kPrefixChunk;  // in the series
+    if (kChecked && !(in_range(sg.x_off, sg.n, P.x_cap, threadIdx.x ? nullptr : P.status) &&
+                      in_range(sg.pre_off, sg.n + 1, P.prefix_cap, threadIdx.x ? nullptr : P.status) &&
+                      in_range(blockIdx.x, 1, P.nchunks, threadIdx.x ? nullptr : P.status)))
+        return;  // uniform
     float v[kPrefixPerThread];
     prefix_load(P, sg.x_off + local0, sg.x_off + sg.n, sh, v);
     float2 acc = make_float2(0.f, 0.f);
@@ -194,6 +202,13 @@ __global__ void __launch_bounds__(kDownsampleThreads) downsample_kernel(Downsamp
     const int2 bi = P.blocks ? P.blocks[blockIdx.x]
                              : make_int2(0, (int)blockIdx.x * kDownsamplePerBlock);
     const OctaveDesc od = P.oct ? P.oct[bi.x] : P.single;
+    if (kChecked) {  // the octave's ranges (uniform)
+        unsigned* st = threadIdx.x ? nullptr : P.status;
+        if (!(in_range(od.x_off, od.x_n, P.x_cap, st) && in_range(od.out_off, od.nk, P.out_cap, st) &&
+              (od.f_int == 1 && od.f_frac == 0 ? od.nk <= od.x_n
+                                               : in_range(od.pre_off, od.x_n + 1, P.prefix_cap, st))))
+            return;
+    }
 #pragma unroll
     for (int q = 0; q < kDownsamplePerBlock / kDownsampleThreads; ++q) {
         const int64_t i64 = (int64_t)bi.y + q * kDownsampleThreads + threadIdx.x;
@@ -214,6 +229,12 @@ __global__ void __launch_bounds__(kDownsampleThreads) downsample_kernel(Downsamp
                 b_frac = 0;
             }
             const float2* pre = P.prefix + od.pre_off;
+            if (kChecked && !(a_int <= b_int && b_int <= (uint64_t)od.x_n &&
+                              (a_frac == 0 || a_int < (uint64_t)od.x_n) &&
+                              (b_frac == 0 || b_int < (uint64_t)od.x_n))) {
+                bounds_violation(P.status);
+                continue;
+            }
             out = df_sub_to_float(pre[(int64_t)b_int], pre[(int64_t)a_int]);
             if (a_frac != 0) {
                 float al = __ull2float_rn(a_frac) * 5.42101086242752217e-20f;  // 2^-64
@@ -348,6 +369,7 @@ struct QueueHook {
     ItemHead* head_dst = nullptr;
     uint64_t* head_bar = nullptr;
     unsigned issued = 0;            // set: the table copy was issued (bit 0), the head copy (bit 1)
+    int ntables = 0;                // top-pass tables (checks)
     bool armed = false;
     bool timed_out = false;
     __device__ __forceinline__ void release() {
@@ -366,7 +388,8 @@ struct QueueHook {
         if (next) {  // the next item's head (fetched one item ago) says whether it has a table
             if (!mbar_wait_bounded(next_bar, next_par, wait)) {
                 timed_out = true;
-            } else if (next->item.pass >= 0) {
+            } else if (next->item.pass >= 0 &&
+                       (!kChecked || (next->item.pad >= 0 && next->item.pad < ntables))) {
                 mbar_expect_tx(table_bar, (unsigned)kTopRecBytes);
                 bulk_g2s(table_dst, table_src + (int64_t)next->item.pad * kTopRecInts,
                          (unsigned)kTopRecBytes, table_bar);
@@ -529,28 +552,35 @@ __device__ __forceinline__ void snr_pair(const float* A, const float* B, int k, 
 }
 
 // Boxcar S/N of one long profile (p > kSnrHalfMaxP) by one warp: sequential per-lane
-// chunks of the prefix sums, then strided phases per width.
+// chunks of the prefix sums, then strided phases per width.  The prefix sums are
+// compensated (double-float two-sum accumulation, the lane totals scanned the same way)
+// and rounded to float once each, so a long profile's boxcar sums carry one rounding of
+// each prefix sum instead of the error of ~p/32 sequential float adds.
 __device__ __noinline__ void snr_row_any(const float* prof, int p, float* S, const Widths& W,
                                          float inv_std, float* out, int lane) {
     const int L = p + W.wmax;
     const int c = (L + 31) >> 5;
     const int i0 = lane * c;
     const int i1 = min(i0 + c, L);
-    float acc = 0.f;
-    for (int i = i0; i < i1; ++i) acc += prof[i < p ? i : i - p];
-    float inc = acc;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int i = i0; i < i1; ++i) acc = df_add(acc, make_float2(prof[i < p ? i : i - p], 0.f));
+    float2 inc = acc;
     for (int o = 1; o < 32; o <<= 1) {
-        float u = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += u;
+        float2 u;
+        u.x = __shfl_up_sync(kFull, inc.x, o);
+        u.y = __shfl_up_sync(kFull, inc.y, o);
+        if (lane >= o) inc = df_add(u, inc);
     }
-    float run = __shfl_up_sync(kFull, inc, 1);
+    float2 run;
+    run.x = __shfl_up_sync(kFull, inc.x, 1);
+    run.y = __shfl_up_sync(kFull, inc.y, 1);
     if (lane == 0) {
-        run = 0.f;
+        run = make_float2(0.f, 0.f);
         S[0] = 0.f;
     }
     for (int i = i0; i < i1; ++i) {
-        run += prof[i < p ? i : i - p];
-        S[i + 1] = run;
+        run = df_add(run, make_float2(prof[i < p ? i : i - p], 0.f));
+        S[i + 1] = __fadd_rn(run.x, run.y);
     }
     __syncwarp();
     for (int iw = 0; iw < W.nw; ++iw) {
@@ -785,12 +815,31 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     }
     const unsigned bytes = bulk_bytes(src, total);
     const int H = tree_height(n);
+    bool skip = false;  // checked builds: a bad item is skipped (the queue hook still runs)
+    if constexpr (kChecked) {  // the item's ranges, alike in every thread
+        unsigned* st = tid == 0 ? P.status : nullptr;
+        const long long dyn = dyn_smem_floats();
+        const int nw = P.widths.nw;
+        const long long sw = (long long)P.snr_warps * snr_warp_floats(p, P.widths.wmax);
+        bool ok = n >= 1 && n <= P.nmax && total + 4 <= lay.buf_floats &&
+                  in_range(tr.src_off + (long long)start * p, total, P.src_cap, st) &&
+                  in_range(lay.buf_b, lay.buf_floats, dyn, st) &&
+                  in_range(lay.desc, 2LL * (H > kRegLevels ? H - kRegLevels : 0) * P.nmax,
+                           lay.nodes, st) &&
+                  in_range(lay.nodes, P.nmax, lay.buf_a, st);
+        if (kSnr)
+            ok = ok && tr.kept <= n && in_range(tr.trial0, tr.kept, P.ntrials, st) &&
+                 in_range(lay.buf_a, sw, dyn, st) && in_range(lay.buf_b, sw, dyn, st) && nw >= 1;
+        else
+            ok = ok && in_range(tr.scratch_off + (long long)start * p, total, P.dst_cap, st);
+        skip = !ok;
+    }
     // Warp 0 runs the hook (thread 0: release the item before, fetch the next records)
     // while warps 1.. issue the copy and make the item's tables (the persistent loop has
     // reset nreg and regmax before its claim barrier).
     if (warp == 0) {
         hook.run();
-    } else {
+    } else if (!skip) {
         const int t = tid - 32, nt = kBottomThreads - 32;
         if (t == 0 && bytes) {
             mbar_expect_tx(bar, bytes);  // the single arrival of this barrier phase
@@ -806,7 +855,7 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
             }
             if (r == st) {
                 const int q = atomicAdd(&nreg, 1);
-                rnodes[q] = st | (sz << 16);
+                if (in_range(q, 1, P.nmax, P.status)) rnodes[q] = st | (sz << 16);
                 atomicMax(&regmax, sz);
             }
         }
@@ -817,13 +866,17 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
             desc[l * P.nmax + r] = bottom_desc(n, kRegLevels + 1 + l, r, p);
         }
     }
-    const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity(), hook.limit());
+    const bool landed = skip || bytes == 0 || mbar_wait_bounded(bar, hook.parity(), hook.limit());
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
             atomicOr(P.status, kDevTimeout);
             mbar_wait_bounded(bar, hook.parity(), hook.limit());  // a late copy lands before the CTA exits
         }
         hook.fail();
+        return;
+    }
+    if (skip) {
+        if (Hook::kInitEachItem && tid == 0) mbar_inval(bar);
         return;
     }
     if (bytes) hook.copied();
@@ -844,6 +897,9 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
         for (int w = warp; w < nwork; w += nwarps) {
             const int q = w / nstrip, c = w - q * nstrip;
             const int nd = rnodes[q];
+            if (kChecked && !((nd >> 16) >= 1 && (nd >> 16) <= 16 &&
+                              in_range(nd & 0xffff, nd >> 16, n, lane == 0 ? P.status : nullptr)))
+                continue;
             reg_strip_any(smem, a0, in, nd & 0xffff, nd >> 16, p, c * vstep, vstep, lane);
         }
         __syncthreads();
@@ -855,6 +911,10 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
         for (int r = warp; r < n; r += nwarps) {
             const int2 d = dc[r];
             const int ha = d.x & 0xffff, tb = (d.x >> 16) & 0xffff;
+            if (kChecked && !(in_range(ha, 1, n, lane == 0 ? P.status : nullptr) &&
+                              (tb == 0xffff || in_range(tb, 1, n, lane == 0 ? P.status : nullptr)) &&
+                              d.y >= 0 && d.y < p))
+                continue;
             if (tb != 0xffff) merge_row(smem, out + r * p, in + ha * p, in + tb * p, d.y, p, lane);
             else copy_row(smem, out + r * p, in + r * p, p, lane);
         }
@@ -1016,7 +1076,8 @@ __global__ void __launch_bounds__(kPrepThreads) item_rec_kernel(RecParams R) {
         }
     }
     R.heads[q] = h;
-    if (item.pass >= 0) top_record(R.top, tr, item, R.tables + (int64_t)item.pad * kTopRecInts);
+    if (item.pass >= 0 && in_range(item.pad, 1, R.ntables, R.status))
+        top_record(R.top, tr, item, R.tables + (int64_t)item.pad * kTopRecInts);
 }
 
 // Returns whether a later stage of the transform waits for this item (not the last pass).
@@ -1059,6 +1120,31 @@ __device__ __forceinline__ bool top_item(const TopParams& P, const WorkItem item
         if (Hook::kInitEachItem && tid == 0) mbar_inval(bar);
         return !last;
     }
+    bool skip = false;  // checked builds: a bad item is skipped (the queue hook still runs)
+    if constexpr (kChecked) {  // the item's table, alike in every thread
+        unsigned* st = tid == 0 ? P.status : nullptr;
+        const long long dyn = dyn_smem_floats();
+        bool ok = L >= 1 && L <= kTopMaxLevels;
+        // every node: its rows inside the transform, the needed interval inside the node,
+        // its rows in shared memory inside the launch's; the gathered ones in the scratch
+        for (int e = 0; ok && e < (2 << L) - 1; ++e) {
+            const int* t = tab + 8 * e;
+            const int rows = t[3] - t[2] + 1;
+            ok = rows >= 1 && in_range(t[0], t[1], m, st) && in_range(t[2], rows, t[1], st) &&
+                 in_range(t[4], (long long)rows * p, dyn, st);
+            if (ok && e >= (1 << L) - 1)
+                ok = in_range(tr.scratch_off + (long long)(t[0] + t[2]) * p, (long long)rows * p,
+                              P.buf_cap, st);
+        }
+        ok = ok && lvl_desc[L] <= lay.desc_cap && in_range(lay.desc, 4LL * lvl_desc[L], dyn, st);
+        if (score)
+            ok = ok && hi0 < tr.kept && in_range(tr.trial0 + lo0, hi0 - lo0 + 1, P.ntrials, st) &&
+                 in_range(lay.sbuf, (long long)nwarps * lay.sbuf_warp, dyn, st);
+        else
+            ok = ok && in_range(tr.scratch_off + (long long)(st0 + lo0) * p,
+                                (long long)(hi0 - lo0 + 1) * p, P.buf_cap, st);
+        skip = !ok;
+    }
 
     // ---- gather the needed rows of the depth-d_in transforms: one bulk copy per interval,
     //      all counted by a single arrival on the barrier; the unaligned ends of all
@@ -1068,7 +1154,7 @@ __device__ __forceinline__ bool top_item(const TopParams& P, const WorkItem item
     int4* desc = reinterpret_cast<int4*>(smem + lay.desc);
     if (warp == 0) {
         hook.run();
-    } else {
+    } else if (!skip) {
         const int t = tid - 32, nt = kTopThreads - 32;
         if (t == 0 && bytes) {
             mbar_expect_tx(bar, bytes);
@@ -1110,17 +1196,26 @@ __device__ __forceinline__ bool top_item(const TopParams& P, const WorkItem item
             d.y = tab[8 * eh + 4] + (sp.i - tab[8 * eh + 2]) * p;
             d.z = tab[8 * et + 4] + (sp.j - tab[8 * et + 2]) * p;
             d.w = sp.shift % p;
+            if (kChecked && !(in_range(sp.i - tab[8 * eh + 2], 1, tab[8 * eh + 3] - tab[8 * eh + 2] + 1,
+                                       P.status) &&
+                              in_range(sp.j - tab[8 * et + 2], 1, tab[8 * et + 3] - tab[8 * et + 2] + 1,
+                                       P.status)))
+                d = make_int4(d.x, d.x, d.x, 0);  // inside the item's rows; the status tells
             desc[q] = d;
         }
     }
 
-    const bool landed = bytes == 0 || mbar_wait_bounded(bar, hook.parity(), hook.limit());
+    const bool landed = skip || bytes == 0 || mbar_wait_bounded(bar, hook.parity(), hook.limit());
     if (__syncthreads_or(!landed)) {
         if (tid == 0) {
             atomicOr(P.status, kDevTimeout);
             mbar_wait_bounded(bar, hook.parity(), hook.limit());
         }
         hook.fail();
+        return !last;
+    }
+    if (skip) {
+        if (Hook::kInitEachItem && tid == 0) mbar_inval(bar);
         return !last;
     }
     if (bytes) hook.copied();
@@ -1219,6 +1314,7 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
     hook.wait = P.wait_cycles;
     if (tid == 0) {
         hook.done = P.done;
+        hook.ntables = P.ntables;
         for (int j = 0; j < 5; ++j) mbar_init(&hbar[j], 1);
         mbar_init(reinterpret_cast<uint64_t*>(smem), 1);  // the items' copy barrier
         a = atomicAdd(P.queue, 1);
@@ -1236,7 +1332,8 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
         if (a < N && mbar_wait_bounded(&hbar[0], 0, P.wait_cycles)) {
             par ^= 1u;
             inflight &= ~1u;
-            if (hbuf[0].item.pass >= 0) {
+            if (hbuf[0].item.pass >= 0 &&
+                in_range(hbuf[0].item.pad, 1, P.ntables, P.bottom.status)) {
                 mbar_expect_tx(&tbar[0], (unsigned)kTopRecBytes);
                 bulk_g2s(tbuf, P.tables + (int64_t)hbuf[0].item.pad * kTopRecInts,
                          (unsigned)kTopRecBytes, &tbar[0]);
@@ -1256,7 +1353,12 @@ __global__ void __launch_bounds__(kTopThreads, kTopMinBlocks) ffa_persistent_ker
             if (q < N) {
                 const ItemHead& H = hbuf[ha];
                 bool ok = true;
-                if (H.item.pass >= 0) {
+                if (kChecked)
+                    ok = (H.wait < 0 || in_range(H.wait, 1, P.ncounters, P.bottom.status)) &&
+                         (H.rel[0] < 0 || in_range(H.rel[0], 1, P.ncounters, P.bottom.status)) &&
+                         (H.rel[1] < 0 || in_range(H.rel[1], 1, P.ncounters, P.bottom.status)) &&
+                         (H.item.pass < 0 || in_range(H.item.pad, 1, P.ntables, P.bottom.status));
+                if (ok && H.item.pass >= 0) {
                     ok = mbar_wait_bounded(&tbar[ta], (par >> (3 + ta)) & 1u, P.wait_cycles);
                     par ^= 1u << (3 + ta);
                     inflight &= ~(1u << (3 + ta));
@@ -1357,6 +1459,17 @@ __global__ void __launch_bounds__(256) boxcar_snr_kernel(SnrParams P) {
     float* S = smem + warp * P.warp_floats;
     const int64_t nwarps = (int64_t)gridDim.x * 8, gw = (int64_t)blockIdx.x * 8 + warp;
     const int nw = P.widths.nw;
+    if constexpr (kChecked) {  // the warps' prefix-sum rows and the widths (uniform)
+        unsigned* st = threadIdx.x ? nullptr : P.status;
+        bool ok = P.widths.wmax <= P.cols &&
+                  in_range(snr_warp_floats(P.cols, P.widths.wmax), 0, P.warp_floats, st) &&
+                  in_range(0, 8LL * P.warp_floats, dyn_smem_floats(), st);
+        for (int i = 0; ok && i < nw; ++i) ok = P.widths.w[i] >= 1 && P.widths.w[i] <= P.widths.wmax;
+        if (!ok) {
+            if (threadIdx.x == 0) bounds_violation(P.status);
+            return;
+        }
+    }
     if (P.cols <= kSnrHalfMaxP) {
         for (int64_t r0 = 2 * gw; r0 < P.rows; r0 += 2 * nwarps) {
             const int64_t r = min(r0 + (lane >> 4), P.rows - 1);
@@ -1498,6 +1611,15 @@ cudaError_t launch_top(const TopParams& P, int nblocks, int smem_bytes, cudaStre
     allow_max_smem((const void*)ffa_top_kernel, 2);
     ffa_top_kernel<<<nblocks, kTopThreads, smem_bytes, s>>>(P);
     return cudaGetLastError();
+}
+
+cudaError_t bounds_seen_kernels(unsigned* bits) {
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_bounds_seen, sizeof(v));
+    if (e != cudaSuccess) return e;
+    *bits = v;
+    v = 0;
+    return cudaMemcpyToSymbol(g_bounds_seen, &v, sizeof(v));
 }
 
 cudaError_t launch_snr(const SnrParams& P, cudaStream_t s) {

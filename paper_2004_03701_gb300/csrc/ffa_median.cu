@@ -74,6 +74,13 @@ __device__ __forceinline__ uint32_t rank0(const uint2* __restrict__ D, uint32_t 
     return e.x + __popc(~e.y & ((1u << (i & 31)) - 1u));
 }
 
+// Checked builds: false (and the status bit set) when `ok` fails.
+__device__ __forceinline__ bool ck(bool ok, unsigned* status) {
+    if (!ffa::kChecked || ok) return true;
+    ffa::bounds_violation(status);
+    return false;
+}
+
 // Level 0: zero count of the top key bit per tile, the two end keys, and a cleared count
 // buffer for level 1.
 __global__ void __launch_bounds__(kThreads)
@@ -149,7 +156,8 @@ wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xs
                   uint32_t* __restrict__ dst, int64_t n, int bit, int ntiles,
                   const uint32_t* __restrict__ tz, const uint32_t* __restrict__ pre,
                   uint32_t* __restrict__ Zl, uint2* __restrict__ dir,
-                  uint32_t* __restrict__ tz_next, uint32_t* __restrict__ tz_clear) {
+                  uint32_t* __restrict__ tz_next, uint32_t* __restrict__ tz_clear,
+                  unsigned* status) {
     __shared__ uint32_t s_z[kRounds * (kThreads / 32)];  // zeros per (round, warp)
     __shared__ uint32_t s_base[2 * (kThreads / 32)];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -241,7 +249,7 @@ wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xs
         if (v) {
             const uint32_t z = zw + __popc(valid[j] & ~ones[j] & lt);  // zeros before me
             d = one ? Z + (uint32_t)(w0 + lane) - z : z;
-            dst[d] = key[j];
+            if (ck((int64_t)d < n, status)) dst[d] = key[j];
         }
         const bool nz = v && !((key[j] >> (bit - 1)) & 1u);
         const bool second = d / kTile != (one ? to_first : tz_first);
@@ -261,7 +269,7 @@ wm_scatter_kernel(const uint32_t* __restrict__ src, const float* __restrict__ xs
     __syncthreads();
     if (tid < 4 && s_cnt[tid]) {
         const uint32_t tile = ((tid >> 1) ? to_first : tz_first) + (tid & 1);
-        atomicAdd(tz_next + tile, s_cnt[tid]);
+        if (ck(tile < (uint32_t)ntiles, status)) atomicAdd(tz_next + tile, s_cnt[tid]);
     }
 }
 
@@ -269,7 +277,15 @@ struct Matrix {
     const uint2* dir;  // level L's directory at dir + L * nwords
     int64_t nwords;
     const uint32_t* Z;
+    uint32_t n;        // keys per level (checks)
+    unsigned* status;  // (checks)
 };
+
+// Checked builds: a range [l, r) of a level inside [0, n); otherwise set to [0, 0)
+// with the status bit set.
+__device__ __forceinline__ void ck_range(const Matrix& M, uint32_t& l, uint32_t& r) {
+    if (!ck(l <= r && r <= M.n, M.status)) l = r = 0;
+}
 
 // key of the k-th smallest (from 0) of A_0[l, r)
 __device__ __forceinline__ uint32_t wm_select(const Matrix& M, const uint32_t* sZ, uint32_t l,
@@ -278,6 +294,7 @@ __device__ __forceinline__ uint32_t wm_select(const Matrix& M, const uint32_t* s
 #pragma unroll 4
     for (int L = 0; L < kLevels; ++L) {
         const uint2* D = M.dir + L * M.nwords;
+        if (ffa::kChecked) ck_range(M, l, r);
         const uint32_t zl = rank0(D, l), zr = rank0(D, r), zeros = zr - zl;
         key <<= 1;
         if (k < zeros) {
@@ -299,6 +316,7 @@ __device__ __forceinline__ uint32_t wm_count_less(const Matrix& M, const uint32_
     uint32_t cnt = 0;
     for (int L = 0; L < kLevels; ++L) {
         const uint2* D = M.dir + L * M.nwords;
+        if (ffa::kChecked) ck_range(M, l, r);
         const uint32_t zl = rank0(D, l), zr = rank0(D, r);
         if ((v >> (31 - L)) & 1u) {
             cnt += zr - zl;
@@ -338,6 +356,7 @@ __device__ __forceinline__ void median_inner(const float* x, int64_t base, int64
         const uint32_t zL = sZ[L];
 #pragma unroll
         for (int u = 0; u < kQueryILP; ++u) {
+            if (ffa::kChecked) ck_range(M, l[u], r[u]);
             const uint32_t zl = rank0(D, l[u]), zr = rank0(D, r[u]), zeros = zr - zl;
             key[u] <<= 1;
             if (k[u] < zeros) {
@@ -354,7 +373,7 @@ __device__ __forceinline__ void median_inner(const float* x, int64_t base, int64
 #pragma unroll
     for (int u = 0; u < kQueryILP; ++u) {
         const int64_t i = base + u * kQueryThreads;
-        if (i < e1) emit(x, med, y, i, key_float(key[u]));
+        if (i < e1 && ck(i >= 0 && i < (int64_t)M.n, M.status)) emit(x, med, y, i, key_float(key[u]));
     }
 }
 
@@ -388,7 +407,7 @@ __device__ __forceinline__ void median_edge(const float* x, int64_t n, int64_t h
         else
             key = wm_select(M, sZ, l, r, k - c1);
     }
-    emit(x, med, y, i, key_float(key));
+    if (ck(i >= 0 && i < n, M.status)) emit(x, med, y, i, key_float(key));
 }
 
 // One launch for all outputs: the first `edge_blocks` CTAs take the outputs whose window
@@ -411,6 +430,7 @@ wm_median_kernel(const float* x, int64_t n, int64_t h, int64_t e0, int64_t e1,
 }
 
 struct Workspace {
+    unsigned* status;  // device status word (ffa_check)
     uint32_t* keys[2];
     uint2* dir;
     uint32_t* tz[3];
@@ -434,6 +454,7 @@ Workspace layout(int64_t n, char* base) {
         off += up256(b);
         return p;
     };
+    w.status = reinterpret_cast<unsigned*>(take(4));
     w.keys[0] = reinterpret_cast<uint32_t*>(take(4 * (size_t)n));
     w.keys[1] = reinterpret_cast<uint32_t*>(take(4 * (size_t)n));
     w.dir = reinterpret_cast<uint2*>(take(8 * (size_t)w.nwords * kLevels));
@@ -483,6 +504,10 @@ extern "C" ffa_status ffa_running_median(const float* d_x, int64_t n, int64_t wi
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t h = width / 2;
     {
+        const cudaError_t e = cudaMemsetAsync(W.status, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) return cuda_err(e, "cudaMemsetAsync");
+    }
+    {
         // 32 levels: per level, reads and writes of the keys and the directory words
         LaunchScope ls(ffa::kMedianBuild, (double)kLevels * (8.0 * n + 8.0 * W.nwords), st);
         wm_count_kernel<<<W.ntiles, kThreads, 0, st>>>(d_x, n, W.tz[0], W.tz[1], W.ends);
@@ -495,12 +520,12 @@ extern "C" ffa_status ffa_running_median(const float* d_x, int64_t n, int64_t wi
                 L ? W.keys[(L - 1) & 1] : nullptr, L ? nullptr : d_x,
                 last ? nullptr : W.keys[L & 1], n, kLevels - 1 - L, W.ntiles, tz,
                 scan ? W.pre : nullptr, W.Z + L, W.dir + (size_t)L * W.nwords,
-                last ? nullptr : W.tz[(L + 1) % 3], last ? nullptr : W.tz[(L + 2) % 3]);
+                last ? nullptr : W.tz[(L + 1) % 3], last ? nullptr : W.tz[(L + 2) % 3], W.status);
         }
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_err(e, "build launch");
     }
-    const Matrix M{W.dir, W.nwords, W.Z};
+    const Matrix M{W.dir, W.nwords, W.Z, (uint32_t)n, W.status};
     // outputs whose window lies inside the series: [e0, e1) = [h, n - h)
     const int64_t e0 = h < n ? h : n;
     const int64_t e1 = n - h > e0 ? n - h : e0;
@@ -516,4 +541,13 @@ extern "C" ffa_status ffa_running_median(const float* d_x, int64_t n, int64_t wi
         if (e != cudaSuccess) return cuda_err(e, "query launch");
     }
     return FFA_OK;
+}
+
+cudaError_t ffa::bounds_seen_median(unsigned* bits) {
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, ffa::g_bounds_seen, sizeof(v));
+    if (e != cudaSuccess) return e;
+    *bits = v;
+    v = 0;
+    return cudaMemcpyToSymbol(ffa::g_bounds_seen, &v, sizeof(v));
 }

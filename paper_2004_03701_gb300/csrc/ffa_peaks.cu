@@ -33,10 +33,12 @@
 #include "ffa_internal.h"
 #include "ffa_kinds.h"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 namespace ffa {
 ffa_status set_error(ffa_status st, const char* msg);
@@ -96,6 +98,13 @@ struct Params {
     long long* ccount;   // [nw][nchunks]: selected trials per chunk
     long long* coff;     // [nw][nchunks]: their exclusive prefix
 };
+
+// Checked builds: false (and the status bit set) when `ok` fails.
+__device__ __forceinline__ bool ck(bool ok, unsigned* status) {
+    if (!ffa::kChecked || ok) return true;
+    ffa::bounds_violation(status);
+    return false;
+}
 
 __device__ __forceinline__ long long seg_of(double nu, const Hdr& h) {
     const long long j = (long long)floor(__ddiv_rn(__dsub_rn(nu, h.nu_lo), h.width));
@@ -209,7 +218,7 @@ __global__ void __launch_bounds__(256) pk_bounds_kernel(Params p) {
             else
                 a = m + 1;
         }
-        p.first[j] = a;
+        if (ck(j < p.max_segments, p.status)) p.first[j] = a;
     }
 }
 
@@ -229,6 +238,9 @@ __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
         const int wb = wa + kGroupW < nw ? wa + kGroupW : nw;
         const long long t0 = p.first[j], t1 = j ? p.first[j - 1] : p.ntrials;
         const long long c = t1 - t0;
+        if (ffa::kChecked &&  // uniform
+            !ck(j < p.max_segments && t0 >= 0 && t0 <= t1 && t1 <= p.ntrials, threadIdx.x ? nullptr : p.status))
+            continue;
         const double nu_c = __dadd_rn(h.nu_lo, __dmul_rn((double)j + 0.5, h.width));
         if (c < p.min_seg || c > kSortCap) {
             if (threadIdx.x == 0 && c > kSortCap) atomicOr(p.status, kPkSegmentTooLarge);
@@ -240,6 +252,9 @@ __global__ void __launch_bounds__(kSegThreads) pk_segment_kernel(Params p) {
         while ((1LL << lm) < c) ++lm;
         const int m = 1 << lm;
         const int G = kSortCap >> lm;  // widths per pass
+        if (ffa::kChecked &&
+            !ck((long long)G * m <= ffa::dyn_smem_floats(), threadIdx.x ? nullptr : p.status))
+            continue;
         for (int w0 = wa; w0 < wb; w0 += G) {
             const int gn = wb - w0 < G ? wb - w0 : G;
             __syncthreads();  // the previous pass's quartiles are read
@@ -481,7 +496,8 @@ __global__ void __launch_bounds__(kSelThreads) pk_write_kernel(Params p) {
     uint32_t* L = p.list + (size_t)iw * p.ntrials;
 #pragma unroll
     for (int u = 0; u < kSelPer; ++u)
-        if (sel[u]) L[off++] = (uint32_t)((long long)blockIdx.x * kSelTile + threadIdx.x * kSelPer + u);
+        if (sel[u] && ck(off >= 0 && off < p.ntrials, p.status))
+            L[off++] = (uint32_t)((long long)blockIdx.x * kSelTile + threadIdx.x * kSelPer + u);
 }
 
 // Peaks of one width: the selected trials in order (decreasing frequency) split where the
@@ -492,12 +508,15 @@ __global__ void __launch_bounds__(kSelThreads) pk_cluster_kernel(Params p) {
     long long* cnt = p.counts + 2 * iw;
     if (p.hdr->nseg == 0 || !p.fit[iw].valid) return;
     const long long nsel = cnt[0];
+    if (ffa::kChecked && !ck(nsel >= 0 && nsel <= p.ntrials, threadIdx.x ? nullptr : p.status))
+        return;  // uniform
     const uint32_t* L = p.list + (size_t)iw * p.ntrials;
     uint64_t* B = p.best + (size_t)iw * p.ntrials;
     const long long per = (nsel + blockDim.x - 1) / blockDim.x;
     const long long e0 = threadIdx.x * per, e1 = e0 + per < nsel ? e0 + per : nsel;
     auto starts = [&](long long e) {
         if (e == 0) return true;
+        if (ffa::kChecked && !ck(L[e - 1] < p.ntrials && L[e] < p.ntrials, p.status)) return false;
         const double gp = __dsub_rn(p.nu[L[e - 1]], p.nu[L[e]]);
         return gp > p.gap;
     };
@@ -517,6 +536,8 @@ __global__ void __launch_bounds__(kSelThreads) pk_cluster_kernel(Params p) {
             run = 0;
         }
         const long long t = L[e];
+        if (ffa::kChecked && !(ck(t < p.ntrials, p.status) && ck(cid >= 0 && cid < npk, p.status)))
+            continue;
         const uint64_t k = best_key(p.snr[t * p.nw + iw], t);
         run = k > run ? k : run;
     }
@@ -533,6 +554,7 @@ __global__ void __launch_bounds__(1024) pk_output_kernel(Params p, ffa_peak* out
         for (long long c = threadIdx.x; c < np; c += blockDim.x) {
             if (base + c >= cap) break;
             const long long t = (long long)(0xffffffffu - (uint32_t)(B[c] & 0xffffffffu));
+            if (ffa::kChecked && !ck(c < p.ntrials && t < p.ntrials, p.status)) continue;
             ffa_peak pk;
             pk.trial = t;
             pk.period = p.periods[t];
@@ -713,4 +735,58 @@ extern "C" ffa_status ffa_find_peaks(const double* d_periods, const float* d_snr
         return ffa::set_error(FFA_ERR_CUDA, buf);
     }
     return FFA_OK;
+}
+
+extern "C" ffa_status ffa_find_peaks_fits(const void* d_ws, int64_t ntrials, int32_t nw,
+                                          const ffa_peak_opts* opts, int64_t* h_nseg,
+                                          double* h_ctrl, int64_t ctrl_cap, double* h_fits,
+                                          void* stream) {
+    if (!d_ws || !h_nseg || !h_fits || (ctrl_cap > 0 && !h_ctrl) || ctrl_cap < 0)
+        return ffa::set_error(FFA_ERR_ARG, "ffa_find_peaks_fits: null pointer or bad capacity");
+    if (ntrials < 1 || ntrials > 0xffffffffLL || nw < 1 || nw > ffa::kMaxWidths)
+        return ffa::set_error(FFA_ERR_ARG, "ffa_find_peaks_fits: ntrials must be in "
+                                           "[1, 2^32 - 1] and nw in [1, 64]");
+    const ffa_peak_opts o = opts ? *opts : defaults();
+    ffa_status st = check_opts(o);
+    if (st != FFA_OK) return st;
+    const Layout L = layout(ntrials, nw, o.max_segments);
+    const char* ws = static_cast<const char*>(d_ws);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Hdr h{};
+    std::vector<Fit> fits(nw);
+    if (cudaMemcpyAsync(&h, ws + L.hdr, sizeof(Hdr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(fits.data(), ws + L.fit, sizeof(Fit) * nw, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return ffa::set_error(FFA_ERR_CUDA, "ffa_find_peaks_fits: copy");
+    }
+    *h_nseg = h.nseg;
+    const long long nc = std::min<long long>(std::min<long long>(h.nseg, o.max_segments), ctrl_cap);
+    if (nc > 0) {
+        if (cudaMemcpyAsync(h_ctrl, ws + L.ctrl, sizeof(double2) * (size_t)nc * nw,
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return ffa::set_error(FFA_ERR_CUDA, "ffa_find_peaks_fits: copy");
+        }
+    }
+    for (int iw = 0; iw < nw; ++iw) {
+        double* f = h_fits + 10 * iw;
+        f[0] = fits[iw].xbar;
+        f[1] = fits[iw].xscale;
+        f[2] = fits[iw].valid ? 1.0 : 0.0;
+        for (int a = 0; a <= kMaxDegree; ++a)  // 0 past the degree
+            f[3 + a] = fits[iw].valid && a <= o.degree ? fits[iw].c[a] : 0.0;
+    }
+    return FFA_OK;
+}
+
+cudaError_t ffa::bounds_seen_peaks(unsigned* bits) {
+    unsigned v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, ffa::g_bounds_seen, sizeof(v));
+    if (e != cudaSuccess) return e;
+    *bits = v;
+    v = 0;
+    return cudaMemcpyToSymbol(ffa::g_bounds_seen, &v, sizeof(v));
 }

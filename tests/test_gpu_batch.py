@@ -190,3 +190,32 @@ def test_dynamic_duty_cycle_segments(F):
     # the injected 2.345 s pulse is the strongest trial of the segment that holds it
     per, _, snr = (t.cpu().numpy() for t in S.segment_result(0))
     assert abs(per[snr.max(axis=1).argmax()] - 2.345) / 2.345 < 2e-3
+
+
+def test_segments_long_profiles_full_size(F):
+    """The Sec. 5.6 segments of the 2^23-sample survey series at full size, in the
+    bench's launch configuration; the 2-20 s segment folds at 1000-1100 bins (scored one
+    profile per warp with compensated prefix sums).  In every segment the deepest
+    transforms (the most rows) and the first and last are compared with the FP64 oracle:
+    periods and fold bins exactly, S/N within 1e-4, and within 3e-5 at 1000-1100 bins."""
+    b = synth.survey_segments()
+    S = F.SegmentSearcher(b.n, b.series[0].tsamp,
+                          [(t.pmin, t.pmax, t.bmin, t.bmax) for t in b.series], b.widths)
+    S(torch.from_numpy(b.x).cuda())
+    torch.cuda.synchronize()
+    S.batch.check()
+    assert max(t.bmin for t in b.series) >= 1000
+    for k, s in enumerate(b.series):
+        pl = oracle.plan(s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax)
+        sel = np.zeros(pl.n_transforms, bool)
+        sel[np.argsort(-pl.tr_m)[:3]] = True
+        sel[[0, pl.n_transforms - 1]] = True
+        ref = oracle.periodogram(b.x, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax, b.widths,
+                                 select=sel)
+        rows = np.concatenate([np.arange(pl.tr_first_trial[t], pl.tr_first_trial[t] + pl.tr_kept[t])
+                               for t in np.flatnonzero(sel)])
+        per, fb, snr = (t.cpu().numpy() for t in S.segment_result(k))
+        np.testing.assert_array_equal(per[rows], ref.periods)
+        np.testing.assert_array_equal(fb[rows], ref.foldbins)
+        err = np.abs(snr[rows].astype(np.float64) - ref.snr).max()
+        assert err <= (3e-5 if s.bmin >= 1000 else 1e-4), (k, s.bmin, err)

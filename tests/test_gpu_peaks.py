@@ -162,3 +162,53 @@ def test_full_survey_periodogram(F):
     # the two brighter injected trains (1.7 s at S/N 14, 7.9 s at S/N 20) are peaks
     for P0 in (1.7, 7.9):
         assert np.any(np.abs(pk["period"] / P0 - 1.0) < 2e-3), P0
+
+
+def _check_fits(F, P, S, tobs, **opts):
+    """Control points bit-identical to the oracle's; thresholds evaluated from the GPU's
+    fitted polynomial within 1e-9 (relative) of the oracle's per-trial thresholds."""
+    S2 = np.ascontiguousarray(S if S.ndim == 2 else S[:, None], dtype=np.float32)
+    PF = F.PeakFinder(len(P), S2.shape[1], tobs, **opts)
+    PF(torch.from_numpy(np.ascontiguousarray(P)).cuda(), torch.from_numpy(S2).cuda())
+    PF.result()
+    ctrl, fits = PF.fits()
+    ref = oracle.find_peaks(P, S2, tobs, **opts)
+    lnnu = np.log(1.0 / P)
+    for iw, r in enumerate(ref):
+        got = ctrl[:, iw]
+        keep = ~np.isnan(got[:, 1])
+        np.testing.assert_array_equal(got[keep, 0], r.ctrl_nu)
+        np.testing.assert_array_equal(got[keep, 1], r.ctrl_s)
+        xbar, xscale, valid = fits[iw, :3]
+        if r.coef is None:
+            assert valid == 0
+            continue
+        assert valid == 1
+        u = (lnnu - xbar) / xscale
+        thr = np.zeros_like(u)
+        for a in range(6, -1, -1):
+            thr = thr * u + fits[iw, 3 + a]
+        np.testing.assert_allclose(thr, r.threshold, rtol=1e-9, atol=1e-9)
+    return ref
+
+
+def test_control_points_fits_and_thresholds(F):
+    """Not only the selected peaks: the intermediate results that decide them."""
+    tobs = 500.0
+    P, nu = _grid(300, 250, tobs, 0.1)
+    r = synth.rng(18)
+    cols = []
+    for iw in range(3):
+        trend = 2.0 - (1.0 + iw) * np.log(nu) + 0.5 * np.log(nu) ** 2
+        cols.append(trend + r.standard_normal(len(P)))
+    S = np.stack(cols, axis=1).astype(np.float32)
+    ref = _check_fits(F, P, S, tobs)
+    assert all(len(x.ctrl_nu) > 100 for x in ref)
+    for opts in (dict(degree=0), dict(degree=4, nsigma=5.0), dict(dzseg=10.0, min_seg=20)):
+        _check_fits(F, P, S[:, :1], tobs, **opts)
+
+
+def test_fits_without_control_points(F):
+    tobs = 300.0
+    P, nu = _grid(10, 5, tobs, 0.3)          # segments of 5 trials < min_seg 8
+    _check_fits(F, P, np.zeros(len(P), np.float32), tobs)
