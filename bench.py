@@ -75,8 +75,8 @@ def parse():
                     default="survey")
     ap.add_argument("--storage", choices=["f32", "f16", "i8"], default=None,
                     help="input storage (default f32; i8 for batch_int8)")
-    ap.add_argument("--tune", action="store_true",
-                    help="time a small grid of tile shapes first and bench the fastest")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="automatic tiles (default: per-class tiles tuned before the warm-up)")
     ap.add_argument("--ws-budget-gb", type=float, default=48.0,
                     help="workspace budget of one launch chunk of a batch")
     ap.add_argument("--template", choices=["plain", "zero_mean"], default="plain",
@@ -434,7 +434,7 @@ class Job:
         self.x32 = torch.from_numpy(src).to(dev)
         self.x = self._store(self.x32)
         self.ws_budget = ws_budget
-        self.tiles, self.tune_ms = None, None
+        self.tiles, self.tune_log, self.effective = None, None, None
         self.widths = self.single.widths if self.batch is None else self.batch.widths
         self.searcher = self._make(None)
         self.graph = None
@@ -450,19 +450,48 @@ class Job:
         return ffa.BatchSearcher(ser, self.batch.widths, ws_budget=self.ws_budget, device=dev,
                                  tiles=tiles, zero_mean=ZERO_MEAN)
 
-    def tune(self, repeats=2):
-        """Picks the fastest tile shape of a small grid around the automatic one (every
-        shape gives the same periodogram) and rebuilds the searcher with it."""
+    def tune(self, repeats=5):
+        """Per-class tiles (classes by transform rows m): each class's candidates timed
+        in turn, the fastest kept (every shape gives the same periodogram), and the
+        searcher rebuilt with the table.  A batch is tuned on its first series up to
+        2^26 samples (the classes are shapes, not series) so that tuning takes seconds."""
         ffa = self.ffa
-        w = self.single if self.batch is None else self.batch.series[0]
-        auto = ffa.periodogram_plan(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax,
-                                    self.widths).tiles
+        if self.batch is None:
+            make, ws = self._make, [self.single]
+        else:
+            sub, tot = [], 0
+            for s in self.batch.series:
+                if sub and tot + s.n > (1 << 26):
+                    break
+                sub.append(s)
+                tot += s.n
+            ser = [ffa.Series(s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax) for s in sub]
+            make = lambda t: ffa.BatchSearcher(ser, self.batch.widths, ws_budget=self.ws_budget,
+                                               device=self.dev, tiles=t, zero_mean=ZERO_MEAN)
+            ws = sub
+
+        def plan_tiles(t):
+            # effective per-class tiles over the tuned series: the largest of each field
+            eff = [ffa.periodogram_plan(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax,
+                                        self.widths, tiles=t, zero_mean=ZERO_MEAN).tiles
+                   for w in {(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax): w
+                             for w in ws}.values()]
+            cls = tuple(ffa.TileClass(c[0].m_max, c[0].p_max,
+                                      max(x.subtree_rows for x in c),
+                                      max(x.top_levels for x in c),
+                                      max(x.top_rows for x in c))
+                        for c in zip(*(e.classes for e in eff)))
+            return ffa.Tiles(classes=cls)
+
         self.searcher = None
-        best, timings = ffa.tune(self._make, lambda s: s(self.x), ffa.tile_candidates(auto),
-                                 repeats)
+        t0 = time.perf_counter()
+        best, log = ffa.tune_classes(make, lambda s: s(self.x), plan_tiles, repeats=repeats)
         self.tiles = best
-        self.tune_ms = [[t.subtree_rows, t.top_levels, t.top_rows, round(ms, 4)]
-                        for t, ms in timings]
+        self.tune_log = {"seconds": round(time.perf_counter() - t0, 2),
+                         "automatic_ms": round(log[0][2], 4),
+                         "tuned_ms": round(min(ms for _, _, ms in log), 4),
+                         "tuned_on_series": len(ws), "trials": len(log)}
+        self.effective = plan_tiles(best)
         self.searcher = self._make(best)
 
     def _store(self, x32):
@@ -539,9 +568,14 @@ class Job:
     def config(self):
         c = self._config()
         if self.tiles is not None:
-            t = self.tiles
-            c["tiles"] = {"subtree_rows": t.subtree_rows, "top_levels": t.top_levels,
-                          "top_rows": t.top_rows, "tuned_ms": self.tune_ms}
+            c["tiles"] = {
+                "classes": [{"m_max": k.m_max or None, "subtree_rows": k.subtree_rows or "auto",
+                             "top_levels": k.top_levels or "auto",
+                             "top_rows": k.top_rows or "auto",
+                             "effective": [e.subtree_rows, e.top_levels, e.top_rows]}
+                            for k, e in zip(self.tiles.classes, self.effective.classes)
+                            if e.subtree_rows],
+                "tuning": self.tune_log}
         else:
             c["tiles"] = "automatic (largest that fits shared memory)"
         return c
@@ -945,8 +979,8 @@ def run_ffa(a):
     _log("inputs to the device, plan")
     job.to_device(ffa, torch, dev, int(a.ws_budget_gb * (1 << 30)))
     _log("planned")
-    if a.tune:
-        _log("tuning tiles")
+    if not a.no_tune:
+        _log("tuning tiles per class")
         job.tune()
     s = job.searcher
     stream = torch.cuda.current_stream()

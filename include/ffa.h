@@ -258,11 +258,30 @@ ffa_status ffa_find_peaks_fits(const void* d_ws, int64_t ntrials, int32_t nw,
  * CPU code recurses depth first). */
 enum { FFA_BOXCAR_PLAIN = 0, FFA_BOXCAR_ZERO_MEAN = 1 };
 
+/* Tile classes: transforms of different shapes may take different tiles.  A transform
+ * (m rows of p bins) takes the first class in table order with m <= m_max and
+ * p <= p_max (a 0 bound admits any value); each non-zero tile field of that class
+ * replaces the plan-wide one for that transform (subtree_rows stays a cap: the smaller
+ * of the class's and the plan's).  Transforms that match no class keep the plan-wide
+ * tiles.  In ffa_plan_info.opts the table comes back with its bounds as given and, per
+ * class, the largest sub-tree, levels per top pass and rows per top item that its
+ * transforms got (all 0: no transform of the plan fell in the class). */
+#define FFA_MAX_TILE_CLASSES 8
+typedef struct ffa_tile_class {
+    int32_t m_max;
+    int32_t p_max;
+    int32_t subtree_rows;
+    int32_t top_levels;
+    int32_t top_rows;
+} ffa_tile_class;
+
 typedef struct ffa_plan_opts {
     int32_t subtree_rows;
     int32_t top_levels;
     int32_t top_rows;
     int32_t boxcar;
+    int32_t nclasses;                              /* 0 .. FFA_MAX_TILE_CLASSES */
+    ffa_tile_class classes[FFA_MAX_TILE_CLASSES];  /* the first nclasses are used */
 } ffa_plan_opts;
 
 typedef struct ffa_plan_info {

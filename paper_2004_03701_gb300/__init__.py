@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass
+from dataclasses import dataclass, replace
 from typing import Optional, Sequence, Tuple
 
 import numpy as np
@@ -39,12 +39,16 @@ __all__ = [
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libffa.so")
 # The bounds-checked debug build (same entry points); loaded instead of libffa.so when the
-# environment has FFA_LIBRARY=checked at the first call.
+# environment has FFA_LIBRARY=checked at the first call (FFA_LIBRARY=<path to a .so>
+# loads another build of the same sources).
 LIB_CHECKED_PATH = os.path.join(_PKG, "libffa_checked.so")
 
 
 def _lib_path() -> str:
-    return LIB_CHECKED_PATH if os.environ.get("FFA_LIBRARY") == "checked" else LIB_PATH
+    v = os.environ.get("FFA_LIBRARY", "")
+    if v == "checked":
+        return LIB_CHECKED_PATH
+    return v if v.endswith(".so") else LIB_PATH
 
 FFA_F32, FFA_F16, FFA_I8 = 0, 1, 2
 _STATUS = {0: "FFA_OK", 1: "FFA_ERR_ARG", 2: "FFA_ERR_CAPACITY", 3: "FFA_ERR_CUDA",
@@ -57,9 +61,19 @@ class FFAError(RuntimeError):
         self.status = status
 
 
+MAX_TILE_CLASSES = 8  # FFA_MAX_TILE_CLASSES
+
+
+class _TileClass(ctypes.Structure):
+    _fields_ = [("m_max", ctypes.c_int32), ("p_max", ctypes.c_int32),
+                ("subtree_rows", ctypes.c_int32), ("top_levels", ctypes.c_int32),
+                ("top_rows", ctypes.c_int32)]
+
+
 class _PlanOpts(ctypes.Structure):
     _fields_ = [("subtree_rows", ctypes.c_int32), ("top_levels", ctypes.c_int32),
-                ("top_rows", ctypes.c_int32), ("boxcar", ctypes.c_int32)]
+                ("top_rows", ctypes.c_int32), ("boxcar", ctypes.c_int32),
+                ("nclasses", ctypes.c_int32), ("classes", _TileClass * MAX_TILE_CLASSES)]
 
 
 class _PlanInfo(ctypes.Structure):
@@ -488,11 +502,30 @@ class PlanInfo:
 
 
 @dataclass(frozen=True)
-class Tiles:
-    """Tile shape of a plan (0 = the largest that fits shared memory); see ffa_tiles."""
+class TileClass:
+    """Transforms with m <= m_max and p <= p_max (0: any) and their own tiles (0: the
+    plan-wide value); see ffa_tile_class."""
+    m_max: int = 0
+    p_max: int = 0
     subtree_rows: int = 0
     top_levels: int = 0
     top_rows: int = 0
+
+
+@dataclass(frozen=True)
+class Tiles:
+    """Tile shape of a plan (0 = the largest that fits shared memory), plus an optional
+    table of per-class shapes (the first matching class of a transform wins); see
+    ffa_plan_opts."""
+    subtree_rows: int = 0
+    top_levels: int = 0
+    top_rows: int = 0
+    classes: Tuple[TileClass, ...] = ()
+
+    def with_class(self, i: int, **fields) -> "Tiles":
+        cl = list(self.classes)
+        cl[i] = replace(cl[i], **fields)
+        return replace(self, classes=tuple(cl))
 
 
 BOXCAR_PLAIN, BOXCAR_ZERO_MEAN = 0, 1
@@ -503,9 +536,20 @@ def _tiles_arg(tiles: Optional[Tiles], zero_mean: bool = False):
     if tiles is None and not zero_mean:
         return None, ctypes.c_void_p(None)
     t = tiles or Tiles()
+    if len(t.classes) > MAX_TILE_CLASSES:
+        raise ValueError("at most %d tile classes" % MAX_TILE_CLASSES)
     o = _PlanOpts(int(t.subtree_rows), int(t.top_levels), int(t.top_rows),
-                  BOXCAR_ZERO_MEAN if zero_mean else BOXCAR_PLAIN)
+                  BOXCAR_ZERO_MEAN if zero_mean else BOXCAR_PLAIN, len(t.classes))
+    for i, c in enumerate(t.classes):
+        o.classes[i] = _TileClass(int(c.m_max), int(c.p_max), int(c.subtree_rows),
+                                  int(c.top_levels), int(c.top_rows))
     return o, ctypes.cast(ctypes.byref(o), ctypes.c_void_p)
+
+
+def _tiles_of(o: _PlanOpts) -> Tiles:
+    return Tiles(o.subtree_rows, o.top_levels, o.top_rows,
+                 tuple(TileClass(c.m_max, c.p_max, c.subtree_rows, c.top_levels, c.top_rows)
+                       for c in o.classes[:o.nclasses]))
 
 
 def periodogram_plan(n: int, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,
@@ -517,9 +561,7 @@ def periodogram_plan(n: int, tsamp: float, pmin: float, pmax: float, bmin: int, 
     _check(library().ffa_periodogram_plan_opts(n, tsamp, pmin, pmax, bmin, bmax, _vp(w), len(w),
                                                tp, ctypes.byref(info)))
     vals = [getattr(info, f) for f, _ in _PlanInfo._fields_[:-3]]
-    t = info.opts
-    return PlanInfo(*vals, Tiles(t.subtree_rows, t.top_levels, t.top_rows), info.ffa_adds,
-                    info.snr_ops)
+    return PlanInfo(*vals, _tiles_of(info.opts), info.ffa_adds, info.snr_ops)
 
 
 def _dtype_code(t) -> int:
@@ -784,6 +826,79 @@ def tune_periodogram(x, tsamp, pmin, pmax, bmin, bmax, widths, candidates=None, 
         candidates = tile_candidates(periodogram_plan(*args).tiles)
     return tune(lambda t: Searcher(*args, device=x.device, tiles=t), lambda s: s(x),
                 candidates, repeats)
+
+
+# Tile classes by transform rows m: the FFA's cost per element grows with log2 m and the
+# split between sub-tree and top-pass levels changes with m (Sec. 5.6 cost model), so
+# each octave of m may prefer its own tiles.  0: every larger m.
+CLASS_M_BOUNDS = (64, 128, 256, 512, 1024, 2048, 4096, 0)
+
+
+def tile_classes(bounds: Sequence[int] = CLASS_M_BOUNDS, p_max: int = 0) -> Tiles:
+    """A class table by m (all classes automatic), the starting point of `tune_classes`."""
+    return Tiles(classes=tuple(TileClass(int(b), int(p_max)) for b in bounds))
+
+
+def class_candidates(eff: TileClass):
+    """Tile choices to try for one class whose transforms got the effective tiles `eff`
+    (as a plan reports them): sub-tree rows as is, halved or quartered, one merge level
+    fewer per top pass, top-pass rows halved; 0 keeps the automatic value."""
+    rows = [0] + [r for r in (eff.subtree_rows // 2, eff.subtree_rows // 4) if r >= 8]
+    levels = [0] + ([eff.top_levels - 1] if eff.top_levels > 1 else [])
+    krows = [0] + ([eff.top_rows // 2] if eff.top_rows >= 8 else [])
+    return [dict(subtree_rows=r, top_levels=l, top_rows=k) for r in rows for l in levels
+            for k in krows if (r, l, k) != (0, 0, 0)]
+
+
+def _min_ms(run, searcher, repeats, stream):
+    torch = _torch()
+    run(searcher)  # warm-up: plan tables pinned, caches filled
+    best = float("inf")
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run(searcher)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def tune_classes(make, run, plan_tiles, start: Optional[Tiles] = None, repeats: int = 5,
+                 min_gain: float = 0.005, stream=None):
+    """Per-class tile tuning: for each class of `start` (default `tile_classes()`) in
+    turn, times `run(make(tiles))` with each of `class_candidates` for that class (the
+    other classes at their best so far) and keeps a choice only if it is faster than the
+    current one by more than `min_gain`.  `plan_tiles(tiles)` returns the effective tiles
+    that a plan with `tiles` reports (empty classes: all zero; they are skipped).
+    Returns (tiles, log) with log = [(class index, fields, min ms of `repeats` calls)];
+    every shape gives bit-identical results, so only time decides."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    cur = start if start is not None else tile_classes()
+    cur_ms = _min_ms(run, make(cur), repeats, s)
+    log = [(-1, {}, cur_ms)]
+    for i in range(len(cur.classes)):
+        eff = plan_tiles(cur).classes[i]
+        if eff.subtree_rows == 0:
+            continue  # no transform in this class
+        best, best_ms = None, cur_ms
+        for f in class_candidates(eff):
+            t = cur.with_class(i, **f)
+            ms = _min_ms(run, make(t), repeats, s)
+            log.append((i, f, ms))
+            if ms < best_ms * (1.0 - min_gain):
+                best, best_ms = t, ms
+        if best is not None:
+            cur, cur_ms = best, best_ms
+    return cur, log
+
+
+def tune_periodogram_classes(x, tsamp, pmin, pmax, bmin, bmax, widths, repeats=5):
+    """Per-class tiles for periodograms of series like `x` (see `tune_classes`)."""
+    args = (x.numel(), tsamp, pmin, pmax, bmin, bmax, widths)
+    return tune_classes(lambda t: Searcher(*args, device=x.device, tiles=t), lambda s: s(x),
+                        lambda t: periodogram_plan(*args, tiles=t).tiles, repeats=repeats)
 
 
 def shard_series(costs: Sequence[float], rank: int, world: int):

@@ -5,6 +5,8 @@
 #include "ffa_internal.h"
 #include "ffa_kinds.h"
 
+#include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -131,11 +133,31 @@ struct SeriesSpec {
 
 // Options of a plan: tile shape (0 = the largest that fits shared memory) and the boxcar
 // template of the S/N.
+// A class of transforms (m <= m_max, p <= p_max; 0: any) with its own tiles (0: the
+// plan-wide value).
+struct TileClass {
+    int m_max = 0, p_max = 0, subtree_rows = 0, top_levels = 0, top_rows = 0;
+    std::array<int, 5> key() const { return {m_max, p_max, subtree_rows, top_levels, top_rows}; }
+};
 struct Tiles {
     int subtree_rows = 0, top_levels = 0, top_rows = 0, boxcar = 0;
+    std::vector<TileClass> classes;
     bool operator<(const Tiles& o) const {
-        return std::tie(subtree_rows, top_levels, top_rows, boxcar) <
-               std::tie(o.subtree_rows, o.top_levels, o.top_rows, o.boxcar);
+        if (std::tie(subtree_rows, top_levels, top_rows, boxcar) !=
+            std::tie(o.subtree_rows, o.top_levels, o.top_rows, o.boxcar))
+            return std::tie(subtree_rows, top_levels, top_rows, boxcar) <
+                   std::tie(o.subtree_rows, o.top_levels, o.top_rows, o.boxcar);
+        return std::lexicographical_compare(
+            classes.begin(), classes.end(), o.classes.begin(), o.classes.end(),
+            [](const TileClass& a, const TileClass& b) { return a.key() < b.key(); });
+    }
+    // the class of a transform of m rows and p bins, or -1
+    int class_of(int m, int p) const {
+        for (size_t c = 0; c < classes.size(); ++c)
+            if ((!classes[c].m_max || m <= classes[c].m_max) &&
+                (!classes[c].p_max || p <= classes[c].p_max))
+                return (int)c;
+        return -1;
     }
 };
 
@@ -150,7 +172,20 @@ ffa_status read_tiles(const ffa_plan_opts* t, Tiles* out) {
         return fail(FFA_ERR_ARG, "top_rows must be 0..%d", kTopMaxRows);
     if (t->boxcar != FFA_BOXCAR_PLAIN && t->boxcar != FFA_BOXCAR_ZERO_MEAN)
         return fail(FFA_ERR_ARG, "boxcar must be FFA_BOXCAR_PLAIN or FFA_BOXCAR_ZERO_MEAN");
-    *out = Tiles{t->subtree_rows, t->top_levels, t->top_rows, t->boxcar};
+    if (t->nclasses < 0 || t->nclasses > FFA_MAX_TILE_CLASSES)
+        return fail(FFA_ERR_ARG, "nclasses must be 0..%d", FFA_MAX_TILE_CLASSES);
+    *out = Tiles{t->subtree_rows, t->top_levels, t->top_rows, t->boxcar, {}};
+    for (int c = 0; c < t->nclasses; ++c) {
+        const ffa_tile_class& k = t->classes[c];
+        if (k.m_max < 0 || k.p_max < 0) return fail(FFA_ERR_ARG, "class %d: negative bound", c);
+        if (k.subtree_rows < 0 || k.subtree_rows == 1 || k.subtree_rows > kBottomMaxRows)
+            return fail(FFA_ERR_ARG, "class %d: subtree_rows must be 0 or 2..%d", c, kBottomMaxRows);
+        if (k.top_levels < 0 || k.top_levels > kTopMaxLevels)
+            return fail(FFA_ERR_ARG, "class %d: top_levels must be 0..%d", c, kTopMaxLevels);
+        if (k.top_rows < 0 || k.top_rows > kTopMaxRows)
+            return fail(FFA_ERR_ARG, "class %d: top_rows must be 0..%d", c, kTopMaxRows);
+        out->classes.push_back(TileClass{k.m_max, k.p_max, k.subtree_rows, k.top_levels, k.top_rows});
+    }
     return FFA_OK;
 }
 
@@ -173,6 +208,7 @@ struct Plan {
     int bottom0_snr_floats = 0;
     int row_cap = kBottomMaxRows;  // sub-tree row limit (lowered if a launch's mix overflows)
     std::vector<int> stage_count;
+    std::vector<int> tr_class;    // tile class of each transform (-1: none)
     std::vector<int> batch_top;   // per scratch batch: its last-pass items
     int ring = 1, nbatches = 0;   // scratch ring slots; batch b uses slot b % ring
     int64_t slot_floats = 0;      // floats of one ring slot (per scratch buffer)
@@ -359,9 +395,16 @@ ffa_status build_plan(Plan& pl) {
                 t.p = p;
                 t.m = m;
                 t.kept = (int)kept;
-                t.depth = depth_for(m, p, pl.row_cap);
+                // tiles: the transform's class, else the plan-wide values
+                const int ci = pl.tiles.class_of(m, p);
+                const TileClass* tc = ci >= 0 ? &pl.tiles.classes[ci] : nullptr;
+                const int rcap = tc && tc->subtree_rows ? std::min(pl.row_cap, tc->subtree_rows)
+                                                        : pl.row_cap;
+                const int lv = tc && tc->top_levels ? tc->top_levels : pl.tiles.top_levels;
+                t.depth = depth_for(m, p, rcap);
                 t.chunk = top_chunk(p, pl.W.wmax, true);
-                if (pl.tiles.top_levels) t.chunk = std::min(t.chunk, pl.tiles.top_levels);
+                if (lv) t.chunk = std::min(t.chunk, lv);
+                pl.tr_class.push_back(ci);
                 if (t.chunk < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
                 t.inv_std = (float)(1.0 / std::sqrt((double)m * var));
                 pl.trs.push_back(t);
@@ -461,7 +504,10 @@ ffa_status build_plan(Plan& pl) {
                 const int L = top_pass_in_depth(d.depth, d.chunk, j) - dout;
                 const bool score = j == np - 1;
                 int K = top_rows(d.p, L, score, wmax);
-                if (pl.tiles.top_rows) K = std::min(K, pl.tiles.top_rows);
+                const int ci = pl.tr_class[t];
+                const int kr = ci >= 0 && pl.tiles.classes[ci].top_rows ? pl.tiles.classes[ci].top_rows
+                                                                         : pl.tiles.top_rows;
+                if (kr) K = std::min(K, kr);
                 if (K < 1) return fail(FFA_ERR_UNSUPPORTED, "profile too long");
                 pl.smem_floats = std::max(pl.smem_floats, top_layout(K, L, d.p, wmax, score).total);
                 const int nmax = (d.m + (1 << dout) - 1) >> dout;
@@ -1203,6 +1249,35 @@ ffa_status ffa_normalise(const float* d_x, int64_t n, void* d_out, ffa_dtype out
 }
 
 // ---------------------------------------------------------------------------------
+// The tiles a plan's transforms got: plan-wide maxima, and the same per class.
+void effective_tiles(const Plan& pl, ffa_plan_opts* o) {
+    std::memset(o, 0, sizeof(*o));
+    o->boxcar = pl.W.boxcar;
+    o->nclasses = (int32_t)pl.tiles.classes.size();
+    for (int c = 0; c < o->nclasses; ++c) {
+        o->classes[c].m_max = pl.tiles.classes[c].m_max;
+        o->classes[c].p_max = pl.tiles.classes[c].p_max;
+    }
+    auto bump = [](int32_t& v, int x) { v = std::max(v, (int32_t)x); };
+    for (size_t t = 0; t < pl.trs.size(); ++t) {
+        const TransformDesc& d = pl.trs[t];
+        const int rows = (d.m + (1 << d.depth) - 1) >> d.depth;
+        const int ci = pl.tr_class[t];
+        bump(o->subtree_rows, rows);
+        if (d.depth > 0) bump(o->top_levels, d.chunk);
+        if (ci >= 0) {
+            bump(o->classes[ci].subtree_rows, rows);
+            if (d.depth > 0) bump(o->classes[ci].top_levels, d.chunk);
+        }
+    }
+    for (const WorkItem& it : pl.items) {
+        if (it.pass < 0) continue;
+        bump(o->top_rows, it.rows);
+        const int ci = pl.tr_class[it.tr];
+        if (ci >= 0) bump(o->classes[ci].top_rows, it.rows);
+    }
+}
+
 ffa_status ffa_periodogram_plan_opts(int64_t n, double tsamp, double pmin, double pmax,
                                       int32_t bmin, int32_t bmax, const int32_t* h_widths,
                                       int32_t nw, const ffa_plan_opts* opts, ffa_plan_info* out) {
@@ -1225,11 +1300,7 @@ ffa_status ffa_periodogram_plan_opts(int64_t n, double tsamp, double pmin, doubl
     out->snr_ops = pl->snr_ops;
     out->workspace_bytes = pl->ws_bytes;
     out->host_workspace_bytes = pl->ws_host_bytes;
-    out->opts = ffa_plan_opts{std::max(pl->bottom_nmax, pl->bottom0_nmax), 0, 0, pl->W.boxcar};
-    for (const TransformDesc& t : pl->trs)
-        if (t.depth > 0) out->opts.top_levels = std::max(out->opts.top_levels, (int32_t)t.chunk);
-    for (const WorkItem& it : pl->items)
-        if (it.pass >= 0) out->opts.top_rows = std::max(out->opts.top_rows, (int32_t)it.rows);
+    effective_tiles(*pl, &out->opts);
     return FFA_OK;
 }
 

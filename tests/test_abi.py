@@ -238,6 +238,46 @@ def test_tiles_rejected(lib, bad):
     assert e.value.status == 1
 
 
+def test_tile_classes_apply_per_transform(lib):
+    """A class table changes only the work items of the transforms it admits: the first
+    matching class wins, its sizes cap that class's tiles, other classes keep theirs."""
+    args = (2 ** 23, 64e-6, 0.2, 20.0, 240, 260, (1, 2, 3, 4, 6, 9, 13, 19, 28, 42, 63))
+    auto = ffa.periodogram_plan(*args)
+    base = ffa.periodogram_plan(*args, tiles=ffa.tile_classes())
+    assert (base.ntrials, base.folded_samples) == (auto.ntrials, auto.folded_samples)
+    # all-automatic classes: each class's effective tiles are within the plan-wide ones
+    nonempty = [c for c in base.tiles.classes if c.subtree_rows]
+    assert len(nonempty) >= 4
+    for c in nonempty:
+        assert c.subtree_rows <= auto.tiles.subtree_rows and c.top_levels <= auto.tiles.top_levels
+    t = ffa.tile_classes().with_class(3, subtree_rows=16, top_levels=1, top_rows=8)
+    info = ffa.periodogram_plan(*args, tiles=t)
+    assert (info.ntrials, info.folded_samples) == (auto.ntrials, auto.folded_samples)
+    c3 = info.tiles.classes[3]
+    assert (c3.subtree_rows, c3.top_levels, c3.top_rows) == (16, 1, 8)
+    for i, (a, b) in enumerate(zip(base.tiles.classes, info.tiles.classes)):
+        if i != 3:
+            assert a == b
+    # a transform matches the first class that admits it: an earlier catch-all wins
+    first = ffa.Tiles(classes=(ffa.TileClass(0, 0, 16, 1, 8),) + ffa.tile_classes().classes[:7])
+    info = ffa.periodogram_plan(*args, tiles=first)
+    assert info.tiles.classes[0].subtree_rows == 16
+    assert all(c.subtree_rows == 0 for c in info.tiles.classes[1:])
+
+
+@pytest.mark.parametrize("bad", [ffa.TileClass(-1, 0, 0, 0, 0), ffa.TileClass(0, -5, 0, 0, 0),
+                                 ffa.TileClass(0, 0, 1, 0, 0), ffa.TileClass(0, 0, 0, 4, 0),
+                                 ffa.TileClass(0, 0, 0, 0, 200)])
+def test_tile_classes_rejected(lib, bad):
+    with pytest.raises(ffa.FFAError) as e:
+        ffa.periodogram_plan(262144, 1e-3, 1.0, 10.0, 240, 260, (1, 2, 4),
+                             tiles=ffa.Tiles(classes=(bad,)))
+    assert e.value.status == 1
+    with pytest.raises(ValueError):
+        ffa.periodogram_plan(262144, 1e-3, 1.0, 10.0, 240, 260, (1, 2, 4),
+                             tiles=ffa.Tiles(classes=(ffa.TileClass(),) * 9))
+
+
 def test_batch_tiles_rejected_and_accepted(lib):
     b, ser = _batch_series(2)
     with pytest.raises(ffa.FFAError):
