@@ -716,11 +716,15 @@ __device__ __forceinline__ int2 bottom_desc(int n, int lev, int r, int p) {
 
 // ---------------------------------------------------------------------------------
 // Register stage: the transform of a node of S <= 16 rows (its whole sub-tree, up to
-// four merge levels) on a strip of 32 consecutive columns held one per lane.  The
-// rotation T[(x + k) mod p] is a shuffle down by k within the strip; an output column
-// depends on input columns x .. x + S - 1 only, so lanes 0 .. 32 - S are exact and the
-// strips advance by 33 - S columns.  The merge schedule of each S is a compile-time
-// table, so every operand is a fixed register.
+// four merge levels) on a strip of 64 consecutive columns, two per lane: lane L holds
+// strip columns L and L + 32 of every row.  The rotation T[(x + k) mod p] reads strip
+// column u + k: for u = L that is lane L + k's first column, or once L + k passes 31,
+// lane L + k - 32's second one, so one shuffle (each lane sending the column its
+// receiver needs) serves the first column and one the second.  An output column depends
+// on input columns x .. x + S - 1 only, so strip columns 0 .. 64 - S are exact and the
+// strips advance by 65 - S columns (a single column per lane would keep 33 - S of 32).
+// The merge schedule of each S is a compile-time table, so every operand is a fixed
+// register.
 // ---------------------------------------------------------------------------------
 template <int S>
 struct RegSched {
@@ -736,34 +740,55 @@ struct RegSched {
 };
 
 template <int OFF, int S, int N>
-__device__ __forceinline__ void reg_ffa(float (&v)[N]) {
+__device__ __forceinline__ void reg_ffa(float (&v0)[N], float (&v1)[N], int lane) {
     if constexpr (S > 1) {
         constexpr int nh = S / 2;
-        reg_ffa<OFF, nh, N>(v);
-        reg_ffa<OFF + nh, S - nh, N>(v);
+        reg_ffa<OFF, nh, N>(v0, v1, lane);
+        reg_ffa<OFF + nh, S - nh, N>(v0, v1, lane);
         constexpr RegSched<S> sc{};
-        float o[S];
+        float o0[S], o1[S];
 #pragma unroll
-        for (int s = 0; s < S; ++s)
-            o[s] = __fadd_rn(v[OFF + sc.i[s]], __shfl_down_sync(kFull, v[OFF + nh + sc.j[s]], sc.sh[s]));
+        for (int s = 0; s < S; ++s) {
+            const int h = OFF + sc.i[s], t = OFF + nh + sc.j[s], k = sc.sh[s];
+            if (k == 0) {
+                o0[s] = __fadd_rn(v0[h], v0[t]);
+                o1[s] = __fadd_rn(v1[h], v1[t]);
+            } else {
+                const float send = lane >= k ? v0[t] : v1[t];  // for receiver lane - k (mod 32)
+                o0[s] = __fadd_rn(v0[h], __shfl_sync(kFull, send, lane + k));
+                o1[s] = __fadd_rn(v1[h], __shfl_sync(kFull, v1[t], lane + k));
+            }
+        }
 #pragma unroll
-        for (int s = 0; s < S; ++s) v[OFF + s] = o[s];
+        for (int s = 0; s < S; ++s) {
+            v0[OFF + s] = o0[s];
+            v1[OFF + s] = o1[s];
+        }
     }
 }
 
-// One strip of one node: rows [st, st + S) of `in`, columns from c0, into `out`.
+// One strip of one node: rows [st, st + S) of `in`, strip columns from c0, into `out`;
+// vstep <= 65 - S (the exact columns).
 template <int S>
 __device__ __forceinline__ void reg_strip(float* sm, int in, int out, int st, int p, int c0,
                                           int vstep, int lane) {
-    int x = c0 + lane;
-    if (x >= p) x %= p;
-    float v[S];
+    int x0 = c0 + lane, x1 = c0 + lane + 32;
+    if (x0 >= p) x0 %= p;
+    if (x1 >= p) x1 %= p;
+    float v0[S], v1[S];
 #pragma unroll
-    for (int r = 0; r < S; ++r) v[r] = sm[in + (st + r) * p + x];
-    reg_ffa<0, S, S>(v);
-    if (lane < vstep && c0 + lane < p) {  // vstep <= 33 - S: exact lanes only
+    for (int r = 0; r < S; ++r) {
+        v0[r] = sm[in + (st + r) * p + x0];
+        v1[r] = sm[in + (st + r) * p + x1];
+    }
+    reg_ffa<0, S, S>(v0, v1, lane);
+    if (lane < vstep && c0 + lane < p) {
 #pragma unroll
-        for (int r = 0; r < S; ++r) sm[out + (st + r) * p + x] = v[r];
+        for (int r = 0; r < S; ++r) sm[out + (st + r) * p + x0] = v0[r];
+    }
+    if (lane + 32 < vstep && c0 + lane + 32 < p) {
+#pragma unroll
+        for (int r = 0; r < S; ++r) sm[out + (st + r) * p + x1] = v1[r];
     }
 }
 
@@ -891,7 +916,7 @@ __device__ __forceinline__ void bottom_item(const BottomParams& P, const WorkIte
     const int hd = kSnr ? 0 : (int)((reinterpret_cast<uintptr_t>(dst_g) >> 2) & 3);
     int in = lay.buf_b + hd, out = lay.buf_a + hd;
     {
-        const int vstep = 33 - regmax;
+        const int vstep = 65 - regmax;
         const int nstrip = (p + vstep - 1) / vstep;
         const int nwork = nreg * nstrip;
         for (int w = warp; w < nwork; w += nwarps) {
