@@ -453,6 +453,22 @@ __device__ __forceinline__ float snr_scale(float cmax, float total, const Widths
     return __fmaf_rn(amb, cmax, b * total) * inv_std;
 }
 
+// max(a, b, c) in one instruction
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+// two float subtractions (round to nearest) in one instruction
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 template <int Q>
 __device__ __forceinline__ void snr_half(const float* A, const float* B, int k, int p, float* S,
                                          const Widths& W, float inv_std, float* out, bool write,
@@ -503,8 +519,14 @@ __device__ __forceinline__ void snr_half(const float* A, const float* B, int k, 
             b[iw] = -INFINITY;
             if (w0 + iw < W.nw) {
                 const float* Sw = S + x0 + W.w[w0 + iw];
+                // two phases per step (Q is odd): a paired subtraction and a three-input
+                // max (max is exact, so the order of the maxima does not matter)
 #pragma unroll
-                for (int i = 0; i < Q; ++i) b[iw] = fmaxf(b[iw], __fsub_rn(Sw[i], sk[i]));
+                for (int i = 0; i + 1 < Q; i += 2) {
+                    const float2 d = fsub2(make_float2(Sw[i], Sw[i + 1]), make_float2(sk[i], sk[i + 1]));
+                    b[iw] = fmax3(b[iw], d.x, d.y);
+                }
+                b[iw] = fmaxf(b[iw], __fsub_rn(Sw[Q - 1], sk[Q - 1]));
             }
         }
         const bool h8 = h & 8, h4 = h & 4, h2 = h & 2, h1 = h & 1;
