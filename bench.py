@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--template", choices=["plain", "zero_mean"], default="plain",
                     help="boxcar template of the S/N (Sec. 5.4; zero-mean: the unit-square-sum "
                          "template with zero sum)")
+    ap.add_argument("--series", type=int, default=None,
+                    help="series of a batch workload (default 256 for batch_uneven, 1024 for "
+                         "batch_int8): a smaller batch of the same shape, e.g. for profiling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-stride", type=int, default=8)
@@ -104,23 +107,36 @@ def kernel_source_sha():
 
 
 def recorded_profile(kernel, workload):
-    """The committed ncu record of `kernel` on `workload` (DRAM bytes per launch, shared-
+    """The committed ncu record of `kernel` on `workload` (DRAM bytes per launch, or per
+    algorithmic byte when the capture was of a smaller batch of the same family; shared-
     memory and issue utilisation), or None if there is none or the kernel source changed
     since it was taken."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "roofline_traffic.json")))
         if kernel_source_sha() != rec["kernel_source_sha256_prefix"]:
             return None
-        if rec["kernel"] != kernel or rec.get("workload", workload) != workload:
-            return None
-        return rec
+        for r in rec["records"]:
+            if r["kernel"] != kernel:
+                continue
+            if r.get("workload") == workload or (
+                    "workload_family" in r and workload.startswith(r["workload_family"])):
+                return r
+        return None
     except Exception:
         return None
 
 
-def recorded_traffic(kernel, workload):
+def recorded_traffic(kernel, workload, alg_bytes_per_launch=None):
+    """DRAM bytes per launch: recorded for this workload, or scaled from a smaller
+    capture by the algorithmic bytes of this launch."""
     rec = recorded_profile(kernel, workload)
-    return rec["dram_bytes_per_launch"] if rec else None
+    if not rec:
+        return None
+    if "dram_bytes_per_launch" in rec:
+        return rec["dram_bytes_per_launch"]
+    if alg_bytes_per_launch and "dram_bytes_per_alg_byte" in rec:
+        return rec["dram_bytes_per_alg_byte"] * alg_bytes_per_launch
+    return None
 
 
 def measured_peaks():
@@ -377,7 +393,7 @@ class Job:
     """One benchmark workload: its inputs on the host and (after `to_device`) the
     searcher, the device input and the step."""
 
-    def __init__(self, name, store, rank=0, world=1):
+    def __init__(self, name, store, rank=0, world=1, nseries=None):
         self.name = name
         self.store = store
         self.single = None
@@ -387,9 +403,9 @@ class Job:
         elif name == "plain_small":
             self.single = synth.plain_small()
         elif name == "batch_uneven":
-            self.batch = self._shard(synth.batch_uneven, 256, rank, world)
+            self.batch = self._shard(synth.batch_uneven, nseries or 256, rank, world)
         elif name == "batch_int8":
-            self.batch = self._shard(synth.batch_int8_stress, 1024, rank, world)
+            self.batch = self._shard(synth.batch_int8_stress, nseries or 1024, rank, world)
         elif name == "segments":
             self.batch = synth.survey_segments()
         else:
@@ -604,7 +620,7 @@ def run_reference(a):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    job = Job(a.workload, "f32")
+    job = Job(a.workload, "f32", nseries=a.series)
     # each step a rotating sample sized so that the whole run takes about 2-3 minutes:
     # ~0.15 s per sampled transform of a 2^23-sample series on one core
     import oracle
@@ -975,7 +991,7 @@ def run_ffa(a):
 
     store = a.storage or ("i8" if a.workload == "batch_int8" else "f32")
     _log("generating %s" % a.workload)
-    job = Job(a.workload, store, rank, world)
+    job = Job(a.workload, store, rank, world, a.series)
     _log("inputs to the device, plan")
     job.to_device(ffa, torch, dev, int(a.ws_budget_gb * (1 << 30)))
     _log("planned")
@@ -1054,7 +1070,7 @@ def run_ffa(a):
     peak, peak_kind = measured_peaks()
     achieved = bytes_per_launch / avg_s / 1e9
     wl = job.config()["workload"]
-    traffic = recorded_traffic(top, wl)
+    traffic = recorded_traffic(top, wl, bytes_per_launch)
     prof = recorded_profile(top, wl)
     roofline = {"bound": "smem" if top == "ffa_persistent" else "hbm", "kernel": top,
                 "achieved": achieved, "peak": peak,
@@ -1065,6 +1081,10 @@ def run_ffa(a):
                 "alg_bytes_def": "B_ref FFA+S/N term: sum over transforms of 4 m p + 4 n_w kept",
                 "peak_source": peak_kind,
                 "dram_frac": (traffic / avg_s / 1e9 / peak) if traffic else None,
+                "traffic_source": (None if not traffic else
+                                   "ncu capture of this workload" if "dram_bytes_per_launch" in prof
+                                   else "scaled from the ncu capture of %s by algorithmic bytes"
+                                   % prof.get("captured_workload")),
                 "share_of_step": kq["ms"] / tot_ms if tot_ms else None,
                 "launches_per_step": kq["launches"] / a.steps}
     if top == "ffa_persistent":
@@ -1077,13 +1097,13 @@ def run_ffa(a):
         # the same kernel against the FP32 ALU: the method's adds, subtracts and maxima
         # over 128 FP32 lanes per SM at the maximum SM clock
         ops, b_ref = job.method_counts()
-        launches = kq["launches"] / a.steps
+        top_per_step = kq["launches"] / a.steps
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         mhz = (clk or {}).get("sm_max_mhz") or 2070.0
         alu_peak = sms * 128 * mhz * 1e6 / 1e12
-        alu = ops / launches / avg_s / 1e12
+        alu = ops / top_per_step / avg_s / 1e12
         roofline["alu_frac"] = alu / alu_peak
-        roofline["alu"] = {"ops_per_launch": ops / launches, "achieved": alu, "peak": alu_peak,
+        roofline["alu"] = {"ops_per_launch": ops / top_per_step, "achieved": alu, "peak": alu_peak,
                            "unit": "TFLOP/s", "frac": alu / alu_peak,
                            "peak_source": "%d SMs x 128 FP32 lanes x %.0f MHz" % (sms, mhz)}
         # whole-step effective fraction: B_ref = per octave the raw series read and the
