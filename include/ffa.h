@@ -343,6 +343,20 @@ ffa_status ffa_periodogram_opts(const void* d_x, ffa_dtype dtype, int64_t n, dou
                                 const int32_t* h_widths, int32_t nw, const ffa_plan_opts* opts,
                                 double* d_periods, int32_t* d_foldbins, float* d_snr,
                                 int64_t ntrials_cap, void* d_ws, size_t ws_bytes, void* stream);
+/* Diagnostics of the persistent FFA launch (the paper has no counterpart): synchronises
+ * `stream` and copies to host memory the work-item records that the last
+ * ffa_periodogram[_opts] call with the same search and options made in d_ws, one per
+ * queue position in queue order, 8 int32 each: {transform, node or block index, pass
+ * (-2 whole tree, -1 sub-tree, >= 0 top pass), scratch batch (-1: none), counter waited
+ * for (-1: none), count needed, counter released on completion (-1: none), sub-tree
+ * depth}.  min(cap, items) records are written; *nitems receives the item count.  Every
+ * wait ends if the items releasing a counter come before its waiters in the queue (CTAs
+ * claim positions in order).  Errors: FFA_ERR_ARG, FFA_ERR_CAPACITY (workspace smaller
+ * than the plan's), FFA_ERR_CUDA. */
+ffa_status ffa_periodogram_queue(int64_t n, double tsamp, double pmin, double pmax, int32_t bmin,
+                                 int32_t bmax, const int32_t* h_widths, int32_t nw,
+                                 const ffa_plan_opts* opts, const void* d_ws, size_t ws_bytes,
+                                 int32_t* h_out, int64_t cap, int64_t* nitems, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Batched periodograms (many series, e.g. the dedispersed DM trials of an observation,

@@ -153,6 +153,8 @@ def library() -> ctypes.CDLL:
     L.ffa_check.argtypes = [vp, vp]
     L.ffa_set_wait_limit_ms.argtypes = [dbl]
     L.ffa_checked_status.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint32)]
+    L.ffa_periodogram_queue.argtypes = [i64, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, sz, vp,
+                                        i64, ctypes.POINTER(i64), vp]
     L.ffa_batch_plan.argtypes = [vp, i32, vp, i32, sz, vp, ctypes.POINTER(_BatchInfo)]
     L.ffa_periodogram_batch.argtypes = [vp, i32, vp, i32, vp, i32, sz, vp, vp, vp, i64, vp,
                                         sz, vp]
@@ -184,7 +186,7 @@ def library() -> ctypes.CDLL:
               "ffa_boxcar_snr_template", "ffa_running_median_workspace",
               "ffa_running_median", "ffa_find_peaks_workspace", "ffa_find_peaks",
               "ffa_profile_query", "ffa_set_wait_limit_ms", "ffa_find_peaks_fits",
-              "ffa_checked_status"):
+              "ffa_checked_status", "ffa_periodogram_queue"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -626,6 +628,20 @@ class Searcher:
 
     def check(self, stream=None):
         check(self.ws, stream)
+
+    def queue_records(self, stream=None) -> np.ndarray:
+        """The work-item records of the last search's persistent launch (see
+        ffa_periodogram_queue): an int32 array [items, 8] of {transform, index, pass,
+        batch, wait counter, count needed, released counter, depth}, in queue order."""
+        L = library()
+        n = ctypes.c_int64()
+        args = (*self.args, _vp(self.widths), len(self.widths), self._tiles_ptr, _vp(self.ws),
+                self.ws.numel())
+        _check(L.ffa_periodogram_queue(*args, None, 0, ctypes.byref(n), _stream_handle(stream)))
+        out = np.zeros((max(n.value, 1), 8), np.int32)
+        _check(L.ffa_periodogram_queue(*args, _vp(out), n.value, ctypes.byref(n),
+                                       _stream_handle(stream)))
+        return out[:n.value]
 
 
 def periodogram(x, tsamp: float, pmin: float, pmax: float, bmin: int, bmax: int,

@@ -1334,6 +1334,43 @@ ffa_status ffa_periodogram_opts(const void* d_x, ffa_dtype dtype, int64_t n, dou
                            static_cast<cudaStream_t>(stream));
 }
 
+ffa_status ffa_periodogram_queue(int64_t n, double tsamp, double pmin, double pmax, int32_t bmin,
+                                 int32_t bmax, const int32_t* h_widths, int32_t nw,
+                                 const ffa_plan_opts* opts, const void* d_ws, size_t ws_bytes,
+                                 int32_t* h_out, int64_t cap, int64_t* nitems, void* stream) {
+    if (!d_ws || !nitems || (cap > 0 && !h_out) || cap < 0)
+        return fail(FFA_ERR_ARG, "null pointer or bad capacity");
+    Tiles T;
+    ffa_status st = read_tiles(opts, &T);
+    if (st != FFA_OK) return st;
+    Plan* pl = nullptr;
+    st = get_plan(n, tsamp, pmin, pmax, bmin, bmax, h_widths, nw, T, &pl);
+    if (st != FFA_OK) return st;
+    if (ws_bytes < pl->ws_bytes) return fail(FFA_ERR_CAPACITY, "workspace needs %zu bytes", pl->ws_bytes);
+    *nitems = pl->nitems;
+    const int64_t k = std::min<int64_t>(cap, pl->nitems);
+    if (k <= 0) return FFA_OK;
+    std::vector<ItemHead> heads((size_t)k);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    FFA_CUDA(cudaMemcpyAsync(heads.data(), static_cast<const char*>(d_ws) + pl->o_heads,
+                             (size_t)k * sizeof(ItemHead), cudaMemcpyDeviceToHost, s),
+             "cudaMemcpyAsync(heads)");
+    FFA_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    for (int64_t q = 0; q < k; ++q) {
+        const ItemHead& h = heads[(size_t)q];
+        int32_t* o = h_out + 8 * q;
+        o[0] = h.item.tr;
+        o[1] = h.item.idx;
+        o[2] = h.item.pass;
+        o[3] = h.tr.batch;
+        o[4] = h.wait;
+        o[5] = h.need;
+        o[6] = h.rel[0];
+        o[7] = h.tr.depth;
+    }
+    return FFA_OK;
+}
+
 ffa_status ffa_periodogram(const void* d_x, ffa_dtype dtype, int64_t n, double tsamp, double pmin,
                            double pmax, int32_t bmin, int32_t bmax, const int32_t* h_widths,
                            int32_t nw, double* d_periods, int32_t* d_foldbins, float* d_snr,
