@@ -858,10 +858,13 @@ def tile_classes(bounds: Sequence[int] = CLASS_M_BOUNDS, p_max: int = 0) -> Tile
 def class_candidates(eff: TileClass):
     """Tile choices to try for one class whose transforms got the effective tiles `eff`
     (as a plan reports them): sub-tree rows as is, halved or quartered, one merge level
-    fewer per top pass, top-pass rows halved; 0 keeps the automatic value."""
+    fewer per top pass, top-pass rows halved or cut to a multiple of 32; 0 keeps the
+    automatic value."""
     rows = [0] + [r for r in (eff.subtree_rows // 2, eff.subtree_rows // 4) if r >= 8]
     levels = [0] + ([eff.top_levels - 1] if eff.top_levels > 1 else [])
-    krows = [0] + ([eff.top_rows // 2] if eff.top_rows >= 8 else [])
+    # top-pass rows halved, or cut to a multiple of 32 (the S/N scores 32 rows per round)
+    krows = [0] + sorted({k for k in (eff.top_rows // 2, 32 * (eff.top_rows // 32))
+                          if k >= 8 and k != eff.top_rows}, reverse=True)
     return [dict(subtree_rows=r, top_levels=l, top_rows=k) for r in rows for l in levels
             for k in krows if (r, l, k) != (0, 0, 0)]
 
