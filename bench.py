@@ -604,30 +604,43 @@ class Job:
         return c
 
     def _config(self):
-        if self.batch is None:
-            w = self.single
-            i = self.searcher.info
-            return {"workload": w.name, "n": w.n, "tsamp": w.tsamp, "pmin": w.pmin,
-                    "pmax": w.pmax, "bins": [w.bmin, w.bmax], "widths": list(w.widths),
-                    "ntrials": i.ntrials, "transforms": i.ntransforms, "octaves": i.noctaves,
-                    "storage": self.store}
-        b, i = self.batch, self.searcher.info
-        ns = [s.n for s in b.series]
-        return {"workload": b.name, "series": len(b.series), "n_total": b.n,
-                "n_min": min(ns), "n_max": max(ns), "tsamp": b.series[0].tsamp,
-                "pmin_range": [min(s.pmin for s in b.series), max(s.pmin for s in b.series)],
-                "pmax_range": [min(s.pmax for s in b.series), max(s.pmax for s in b.series)],
-                "bins": [b.series[0].bmin, b.series[0].bmax], "widths": list(b.widths),
-                "ntrials": i.ntrials, "transforms": i.ntransforms, "chunks": i.nchunks,
-                "workspace_gb": round(i.workspace_bytes / 1e9, 2), "storage": self.store,
-                "graph": "one CUDA graph per step (all chunks)"}
+        return workload_config(self, self.ffa if hasattr(self, "ffa") else None,
+                               getattr(self, "ws_budget", None))
+
+
+def workload_config(job, ffa, ws_budget=None):
+    """The workload part of a line's `config`, from the automatic plan (host only, so the
+    reference arm prints the same): sizes, ranges, trials, transforms, storage."""
+    if ffa is None:
+        import paper_2004_03701_gb300 as ffa
+    if job.batch is None:
+        w = job.single
+        i = ffa.periodogram_plan(w.n, w.tsamp, w.pmin, w.pmax, w.bmin, w.bmax, w.widths,
+                                 zero_mean=ZERO_MEAN)
+        return {"workload": w.name, "n": w.n, "tsamp": w.tsamp, "pmin": w.pmin,
+                "pmax": w.pmax, "bins": [w.bmin, w.bmax], "widths": list(w.widths),
+                "ntrials": i.ntrials, "transforms": i.ntransforms, "octaves": i.noctaves,
+                "storage": job.store}
+    b = job.batch
+    ser = [ffa.Series(s.offset, s.n, s.tsamp, s.pmin, s.pmax, s.bmin, s.bmax) for s in b.series]
+    i, _ = ffa.batch_plan(ser, b.widths, ws_budget=ws_budget or (48 << 30), zero_mean=ZERO_MEAN)
+    ns = [s.n for s in b.series]
+    return {"workload": b.name, "series": len(b.series), "n_total": b.n,
+            "n_min": min(ns), "n_max": max(ns), "tsamp": b.series[0].tsamp,
+            "pmin_range": [min(s.pmin for s in b.series), max(s.pmin for s in b.series)],
+            "pmax_range": [min(s.pmax for s in b.series), max(s.pmax for s in b.series)],
+            "bins": [b.series[0].bmin, b.series[0].bmax], "widths": list(b.widths),
+            "ntrials": i.ntrials, "transforms": i.ntransforms, "chunks": i.nchunks,
+            "workspace_gb": round(i.workspace_bytes / 1e9, 2), "storage": job.store,
+            "graph": "one CUDA graph per step (all chunks)"}
 
 
 def run_reference(a):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    job = Job(a.workload, "f32", nseries=a.series)
+    store = a.storage or ("i8" if a.workload == "batch_int8" else "f32")
+    job = Job(a.workload, store, nseries=a.series)
     # each step a rotating sample sized so that the whole run takes about 2-3 minutes:
     # ~0.15 s per sampled transform of a 2^23-sample series on one core
     import oracle
@@ -642,7 +655,13 @@ def run_reference(a):
         if i >= a.warmup:
             rates.append(r)
     value = statistics.mean(rates)
-    cfg = {"workload": job.single.name if job.batch is None else job.batch.name, "n": job.n}
+    # the GPU arm's config: the same workload keys and run conditions; its tiles are the
+    # GPU arm's own work-item shapes, which the oracle (plain recursion) does not have
+    cfg = workload_config(job, None, int(a.ws_budget_gb * (1 << 30)))
+    cfg["tiles"] = "not applicable (the CPU oracle recurses depth first)"
+    cfg["template"] = "zero_mean" if ZERO_MEAN else "plain"
+    cfg["l2"] = "flushed (256 MB write) between steps"
+    cfg["parallelism"] = "replicas" if world > 1 else "single"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": job.n / value * 1e3,
