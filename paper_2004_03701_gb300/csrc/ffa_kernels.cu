@@ -194,7 +194,9 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_final_kernel(PrefixPara
 // ---------------------------------------------------------------------------------
 // Downsampling (Sec. 5.3, App. A.4).  Window [A, B) = [i f, (i+1) f):
 //   out = (S[floor B] - S[floor A]) - frac(A) x[floor A] + frac(B) x[floor B],
-// S the exclusive prefix sum.  A and B are exact in 64.64 fixed point.
+// S the exclusive prefix sum (double-float), x[j] taken as S[j+1] - S[j] rounded to
+// float (the sample itself up to the prefix's ~48-bit precision).  A and B are exact in
+// 64.64 fixed point.
 // ---------------------------------------------------------------------------------
 // Each CTA covers up to kDownsamplePerBlock consecutive outputs of one octave (the plan
 // assigns CTAs to octaves), four per thread at a stride of the CTA size.
@@ -236,13 +238,18 @@ __global__ void __launch_bounds__(kDownsampleThreads) downsample_kernel(Downsamp
                 continue;
             }
             out = df_sub_to_float(pre[(int64_t)b_int], pre[(int64_t)a_int]);
+            // the edge samples as differences of adjacent prefix sums (x[j] = S[j+1] - S[j]):
+            // the next entry shares the cache sector of S[j] three times in four, where a
+            // load of x[j] would be a sector of its own (outputs f samples apart)
             if (a_frac != 0) {
                 float al = __ull2float_rn(a_frac) * 5.42101086242752217e-20f;  // 2^-64
-                out = __fsub_rn(out, __fmul_rn(al, load_sample(P.x, P.dtype, xo + (int64_t)a_int)));
+                const float xa = df_sub_to_float(pre[(int64_t)a_int + 1], pre[(int64_t)a_int]);
+                out = __fsub_rn(out, __fmul_rn(al, xa));
             }
             if (b_frac != 0) {
                 float be = __ull2float_rn(b_frac) * 5.42101086242752217e-20f;
-                out = __fadd_rn(out, __fmul_rn(be, load_sample(P.x, P.dtype, xo + (int64_t)b_int)));
+                const float xb = df_sub_to_float(pre[(int64_t)b_int + 1], pre[(int64_t)b_int]);
+                out = __fadd_rn(out, __fmul_rn(be, xb));
             }
         }
         P.out[od.out_off + i64] = out;
