@@ -168,7 +168,10 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_top_kernel(PrefixParams
 }
 
 __global__ void __launch_bounds__(kPrefixThreads) prefix_final_kernel(PrefixParams P) {
-    __shared__ float sh[kPrefixThreads * 17];
+    // the input transpose (first 17 x 256 floats), then the output staging: thread t's 16
+    // prefixes at 17 t .. 17 t + 15 (padded: a half-warp's 8-byte stores hit 16 bank pairs)
+    __shared__ float2 st2[kPrefixChunk + kPrefixChunk / 16];
+    float* sh = reinterpret_cast<float*>(st2);
     __shared__ float2 wt[kPrefixThreads / 32];
     const PrefixSeg sg = prefix_seg(P, blockIdx.x);
     const int64_t local0 = ((int64_t)blockIdx.x - sg.blk0) * kPrefixChunk;  // in the series
@@ -184,10 +187,17 @@ __global__ void __launch_bounds__(kPrefixThreads) prefix_final_kernel(PrefixPara
     float2 run = df_add(P.partial[blockIdx.x], block_exclusive_df(acc, wt, &tot));
     float2* pre = P.prefix + sg.pre_off;
     if (local0 == 0 && threadIdx.x == 0) pre[0] = make_float2(0.f, 0.f);
-    const int64_t g0 = local0 + (int64_t)threadIdx.x * kPrefixPerThread;
+    // the block's results (the prefix after each sample) staged in shared memory, then
+    // stored as whole lines (each thread's 16 consecutive values would be 16 strided
+    // stores); st2 was last read before the scan's barriers
     for (int q = 0; q < kPrefixPerThread; ++q) {
         run = df_add(run, make_float2(v[q], 0.f));
-        if (g0 + q < sg.n) pre[g0 + q + 1] = run;
+        st2[17 * threadIdx.x + q] = run;
+    }
+    __syncthreads();
+    for (int q = 0; q < kPrefixPerThread; ++q) {
+        const int e = q * kPrefixThreads + threadIdx.x;
+        if (local0 + e < sg.n) pre[local0 + e + 1] = st2[e + (e >> 4)];
     }
 }
 
